@@ -1,0 +1,275 @@
+"""Pins of the oracle's Ising / EA sweep against exact results.
+
+Exact Boltzmann averages by enumeration, the Kaufman torus solution (itself
+pinned to the paper's Tab. rng values and to Onsager), exact transition
+probabilities of one checkerboard sweep, and symmetries of the chain."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from tests.stats import assert_within, binned_mean
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# --------------------------------------------------------------- exact solutions
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("beta", [0.2, 0.4, exact.BETA_C, 0.5, 0.8])
+def test_kaufman_matches_enumeration(L, beta):
+    bf = exact.brute_force(2, L, beta)
+    e, cv = exact.kaufman_torus(L, beta)
+    N = L * L
+    assert abs(e - (-bf["E"] / N)) < 1e-12
+    assert abs(cv - beta * beta * (bf["E2"] - bf["E"] ** 2) / N) < 1e-10
+
+
+def test_kaufman_reproduces_paper_table():
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "tab_rng_exact.txt"))
+            if l.strip() and not l.startswith("#")]
+    for L, beta, e_paper, cv_paper in rows:
+        e, cv = exact.kaufman_torus(int(L), float(beta))
+        # the printed values carry 10 digits; they agree with the closed
+        # forms to about 3e-9 (see the readings listed with the design notes)
+        assert abs(e - float(e_paper)) < 5e-9
+        assert abs(cv - float(cv_paper)) < 5e-9
+
+
+@pytest.mark.parametrize("beta", [0.4, 0.5, 0.6])
+def test_kaufman_large_L_equals_onsager(beta):
+    e, _ = exact.kaufman_torus(512, beta)
+    assert abs(e + exact.onsager_energy(beta)) < 1e-10
+
+
+def test_yang_and_onsager_limits():
+    assert exact.yang_magnetisation(0.4) == 0.0
+    assert abs(exact.yang_magnetisation(2.0) - 1.0) < 1e-6
+    assert abs(exact.onsager_energy(5.0) + 2.0) < 1e-6   # ground state E/N = -2
+
+
+# --------------------------------------------------------------- MC vs exact
+@pytest.mark.parametrize("beta", [0.4, exact.BETA_C, 0.5])
+def test_mc_4x4_matches_enumeration(beta):
+    dim, L = 2, 4
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(dim, L, 11, lid)
+    E, M, _ = oracle.ising_run(dim, L, s, beta, 11, lid, 0, 200000)
+    bf = exact.brute_force(dim, L, beta)
+    e_mc, e_err = binned_mean(E[1000:])
+    m_mc, m_err = binned_mean(np.abs(M[1000:]))
+    assert_within(e_mc, e_err, bf["E"], what="<E>")
+    assert_within(m_mc, m_err, bf["absM"], what="<|M|>")
+
+
+@pytest.mark.parametrize("beta", [0.4, 0.5])
+def test_mc_16x16_matches_kaufman(beta):
+    dim, L = 2, 16
+    lid = oracle.lattice_id(0, 1, 0)
+    s = oracle.ising_init(dim, L, 5, lid)
+    E, M, _ = oracle.ising_run(dim, L, s, beta, 5, lid, 0, 30000)
+    e_exact, _ = exact.kaufman_torus(L, beta)
+    e_mc, e_err = binned_mean(-E[2000:] / (L * L))
+    assert_within(e_mc, e_err, e_exact, what="e")
+
+
+def test_mc_3d_L2_matches_enumeration():
+    dim, L, beta = 3, 2, 0.3
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(dim, L, 3, lid)
+    E, M, _ = oracle.ising_run(dim, L, s, beta, 3, lid, 0, 200000)
+    bf = exact.brute_force(dim, L, beta)
+    e_mc, e_err = binned_mean(E)
+    assert_within(e_mc, e_err, bf["E"], what="<E> 3D")
+
+
+@pytest.mark.parametrize("dim,L,beta", [(2, 4, 0.6), (3, 2, 0.7)])
+def test_mc_ea_matches_enumeration(dim, L, beta):
+    J = oracle.ea_couplings(dim, L, 5, seed=21)
+    assert set(np.unique(J)) <= {-1, 1}
+    lid = oracle.lattice_id(0, 5 >> 5, 0)
+    s = oracle.ising_init(dim, L, 21, lid, bit=5)
+    E, _, _ = oracle.ising_run(dim, L, s, beta, 21, lid, 0, 200000, J=J)
+    bf = exact.brute_force(dim, L, beta, J=J)
+    e_mc, e_err = binned_mean(E)
+    assert_within(e_mc, e_err, bf["E"], what="<E> EA")
+    assert E[-1] == oracle.ising_energy(dim, L, s, J)
+
+
+def test_couplings_are_equiprobable():
+    J = oracle.ea_couplings(3, 16, 7, seed=3)
+    assert abs(J.mean()) < 4.0 / math.sqrt(J.size)
+
+
+# --------------------------------------------------------------- one sweep, exactly
+def _flip_prob(beta, dE):
+    if dE <= 0:
+        return 1.0
+    return oracle.metropolis_threshold(beta, dE) / 2.0 ** 32
+
+
+def _sweep_distribution(s0, beta, L):
+    """Exact distribution of the state after one checkerboard sweep of a 2D
+    L x L ferromagnet started in s0: colour-0 sites flip independently given
+    s0, then colour-1 sites flip independently given the new colour-0 sites."""
+    N = L * L
+    col = np.array([(i % L + i // L) & 1 for i in range(N)])
+    nbrs = [[(i // L) * L + (i % L + 1) % L, (i // L) * L + (i % L - 1) % L,
+             ((i // L + 1) % L) * L + i % L, ((i // L - 1) % L) * L + i % L] for i in range(N)]
+    c0 = [i for i in range(N) if col[i] == 0]
+    c1 = [i for i in range(N) if col[i] == 1]
+    out = {}
+    for f0 in itertools.product([0, 1], repeat=len(c0)):
+        s = s0.astype(int).copy()
+        p = 1.0
+        for i, f in zip(c0, f0):
+            q = _flip_prob(beta, 2 * s0[i] * sum(s0[j] for j in nbrs[i]))
+            p *= q if f else 1 - q
+            if f:
+                s[i] = -s[i]
+        if p == 0.0:
+            continue
+        probs1 = [_flip_prob(beta, 2 * s[i] * sum(s[j] for j in nbrs[i])) for i in c1]
+        for i, q in zip(c1, probs1):
+            out.setdefault(("site", i), 0.0)
+            out[("site", i)] += p * q
+        for i, f in zip(c0, f0):
+            out.setdefault(("site", i), 0.0)
+            out[("site", i)] += p * f
+    return out
+
+
+def test_one_sweep_flip_frequencies_match_exact_probabilities():
+    L, beta = 4, 0.35
+    lid = oracle.lattice_id(0, 3, 0)
+    s0 = oracle.ising_init(2, L, 8, lid)
+    exact_p = _sweep_distribution(s0, beta, L)
+    n = 40000
+    counts = np.zeros(L * L)
+    for k in range(n):  # independent random numbers through the sweep index
+        s = s0.copy()
+        oracle.ising_sweep(2, L, s, beta, 8, lid, k)
+        counts += (s != s0)
+    for i in range(L * L):
+        p = exact_p[("site", i)]
+        sd = math.sqrt(max(p * (1 - p), 1e-12) / n)
+        assert abs(counts[i] / n - p) <= 5 * sd + 1e-9, (i, counts[i] / n, p)
+
+
+def test_half_sweep_detailed_balance():
+    """Each colour half-sweep is reversible w.r.t. exp(-beta E) (Sec. 3.4),
+    with the integer thresholds up to their 2^-32 rounding."""
+    L, beta = 4, 0.45
+    N = L * L
+    E, _ = exact.state_energies(2, L)
+    S = exact.all_states(N).astype(int)
+    col0 = np.array([(i % L + i // L) & 1 == 0 for i in range(N)])
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        a = int(rng.integers(0, 2 ** N))
+        mask = rng.integers(0, 2, N).astype(bool) & col0
+        b = a ^ int(sum(1 << i for i in range(N) if mask[i]))
+
+        def T(x, y):
+            sx, p = S[x], 1.0
+            for i in np.nonzero(col0)[0]:
+                h = sx[(i // L) * L + (i % L + 1) % L] + sx[(i // L) * L + (i % L - 1) % L] + \
+                    sx[((i // L + 1) % L) * L + i % L] + sx[((i // L - 1) % L) * L + i % L]
+                q = _flip_prob(beta, 2 * sx[i] * h)
+                p *= q if S[x][i] != S[y][i] else 1 - q
+            return p
+        lhs = math.exp(-beta * E[a]) * T(a, b)
+        rhs = math.exp(-beta * E[b]) * T(b, a)
+        assert abs(lhs - rhs) <= 1e-8 * max(lhs, rhs) + 1e-300
+
+
+# --------------------------------------------------------------- symmetries / limits
+def test_global_spin_flip_symmetry():
+    dim, L, beta = 2, 12, 0.44
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(dim, L, 4, lid)
+    t = (-s).astype(np.int8)
+    Es, Ms, _ = oracle.ising_run(dim, L, s, beta, 4, lid, 0, 50)
+    Et, Mt, _ = oracle.ising_run(dim, L, t, beta, 4, lid, 0, 50)
+    assert np.array_equal(t, -s) and np.array_equal(Es, Et) and np.array_equal(Ms, -Mt)
+
+
+def test_ferromagnet_equals_ea_with_all_plus_couplings():
+    dim, L, beta = 3, 6, 0.25
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(dim, L, 9, lid)
+    t = s.copy()
+    J = np.ones(dim * L ** dim, np.int8)
+    E1, _, _ = oracle.ising_run(dim, L, s, beta, 9, lid, 0, 20)
+    E2, _, _ = oracle.ising_run(dim, L, t, beta, 9, lid, 0, 20, J=J)
+    assert np.array_equal(s, t) and np.array_equal(E1, E2)
+
+
+def test_ea_gauge_invariance():
+    dim, L, beta = 3, 6, 0.8
+    N = L ** dim
+    J = oracle.ea_couplings(dim, L, 3, seed=2)
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(dim, L, 2, lid, bit=3)
+    eps = np.where(np.random.default_rng(0).integers(0, 2, N) == 1, -1, 1).astype(np.int8)
+    Jg = J.copy()
+    for d in range(dim):
+        for i in range(N):
+            c = [(i // L ** k) % L for k in range(dim)]
+            c[d] = (c[d] + 1) % L
+            j = sum(c[k] * L ** k for k in range(dim))
+            Jg[d * N + i] = J[d * N + i] * eps[i] * eps[j]
+    g = (s * eps).astype(np.int8)
+    E1, _, _ = oracle.ising_run(dim, L, s, beta, 2, lid, 0, 30, J=J)
+    E2, _, _ = oracle.ising_run(dim, L, g, beta, 2, lid, 0, 30, J=Jg)
+    assert np.array_equal(g, s * eps) and np.array_equal(E1, E2)
+
+
+def test_infinite_temperature_flips_every_spin():
+    dim, L = 2, 16
+    lid = oracle.lattice_id(0, 0, 0)
+    s0 = oracle.ising_init(dim, L, 6, lid)
+    s = s0.copy()
+    oracle.ising_sweep(dim, L, s, 0.0, 6, lid, 0)
+    assert np.array_equal(s, -s0)
+
+
+def test_zero_temperature_removes_isolated_defect():
+    L = 8
+    for i0, expect_flips in ((0, 1), (1, 1)):  # colour 0 and colour 1 defect
+        s = np.ones(L * L, np.int8)
+        s[i0] = -1
+        flips = oracle.ising_sweep(2, L, s, 50.0, 1, 0, 0)
+        assert np.all(s == 1) and flips == expect_flips
+
+
+def test_energy_and_magnetisation_definitions():
+    L = 4
+    s = np.ones(L * L, np.int8)
+    assert oracle.ising_energy(2, L, s) == -2 * L * L
+    assert oracle.ising_magnetisation(2, L, s) == L * L
+    s[0] = -1
+    assert oracle.ising_energy(2, L, s) == -2 * L * L + 8
+    chk = np.array([1 if (i % L + i // L) % 2 == 0 else -1 for i in range(L * L)], np.int8)
+    assert oracle.ising_energy(2, L, chk) == 2 * L * L
+
+
+def test_window_sweeps_match_full_lattice():
+    dim, L, beta, seed = 2, 32, 0.42, 13
+    lid = oracle.lattice_id(0, 2, 1)
+    s = oracle.ising_init(dim, L, seed, lid)
+    full = s.copy()
+    oracle.ising_run(dim, L, full, beta, seed, lid, 3, 2, series=False)
+    W, org = 14, (27, 5)
+    gx = (org[0] + np.arange(W)) % L
+    gy = (org[1] + np.arange(W)) % L
+    idx = (gy[:, None] * L + gx[None, :]).ravel()
+    win = oracle.init_sites(idx, seed, lid)
+    assert np.array_equal(win, s[idx])
+    oracle.window_sweeps(dim, L, org, W, win, beta, seed, lid, 3, 2)
+    inner = np.zeros((W, W), bool)
+    inner[4:W - 4, 4:W - 4] = True
+    assert np.array_equal(win.reshape(W, W)[inner], full[idx].reshape(W, W)[inner])

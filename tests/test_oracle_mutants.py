@@ -1,0 +1,50 @@
+"""The pins must catch plausible mistakes in the oracle: each case plants
+one mistake in a copy of the oracle's C source (on the CPU, in a temporary
+directory), builds it, and checks that the named pin tests fail with it."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "spin_oracle.c")
+
+MUTANTS = {
+    "metropolis_sign": ("int dE = 2 * s[i] * h;", "int dE = -2 * s[i] * h;",
+                        "tests/test_oracle_ising.py::test_mc_4x4_matches_enumeration"),
+    "threshold_index": ("(uint32_t)(i >> 1));\n        flip = r < thr[dE / 4];",
+                        "(uint32_t)(i >> 1));\n        flip = r < thr[dE / 4 - (dE > 4)];",
+                        "tests/test_oracle_ising.py::test_mc_4x4_matches_enumeration"),
+    "backward_coupling": ("int j_dn = J ? J[d * n + dn] : 1;", "int j_dn = J ? J[d * n + i] : 1;",
+                          "tests/test_oracle_ising.py::test_mc_ea_matches_enumeration"),
+    "colour_order": ("for (int colour = 0; colour < 2; ++colour) {\n    for (int64_t i = 0; i < n; ++i) {\n      if (or_colour(dim, L, i) != colour) continue;\n      int h = or_local_field",
+                     "for (int colour = 1; colour >= 0; --colour) {\n    for (int64_t i = 0; i < n; ++i) {\n      if (or_colour(dim, L, i) != colour) continue;\n      int h = or_local_field",
+                     "tests/test_oracle_ising.py::test_one_sweep_flip_frequencies_match_exact_probabilities"),
+    "pt_sign": ("if (dbeta * (double)dE >= 0.0) {", "if (dbeta * (double)dE <= 0.0) {",
+                "tests/test_oracle_pt_heis.py::test_pt_slot_marginals_and_swap_rates_match_exact"),
+    "heis_energy_sign": ("dE -= (nv[k] - s[3 * i + k]) * h[k];", "dE += (nv[k] - s[3 * i + k]) * h[k];",
+                         "tests/test_oracle_pt_heis.py::test_heis_chain_correlation_matches_langevin"),
+    "heis_proposal": ("double z = 2.0 * u1 - 1.0;", "double z = u1;",
+                      "tests/test_oracle_pt_heis.py::test_heis_infinite_temperature_gives_uniform_proposals"),
+    "philox_word": ("uint32_t n2 = hi0 ^ c3 ^ k1;", "uint32_t n2 = hi0 ^ c1 ^ k1;",
+                    "tests/test_oracle_rng.py::test_philox_matches_curand_host_generator"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new, target = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                    str(mut), "-o", str(lib), "-lm"], check=True)
+    env = dict(os.environ, SPIN_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        target], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if "skipped" in r.stdout and "failed" not in r.stdout:
+        pytest.skip("pin skipped on this host")
+    assert r.returncode != 0, f"mutant {name} survived:\n{r.stdout[-2000:]}"

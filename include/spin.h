@@ -1,0 +1,183 @@
+/*
+ * spin.h -- C ABI of the GB300 checkerboard Metropolis library.
+ *
+ * The library implements the data-parallel hot path of M. Weigel,
+ * "Performance potential for simulating spin models on GPU"
+ * (arXiv:1101.1427): checkerboard (red-black) Metropolis sweeps for the
+ * 2D/3D Ising ferromagnet (Eq. ising_hamiltonian, Eq. metropolis, Sec. 3.2),
+ * the +-J Edwards-Anderson spin glass (Eq. spinglass_hamiltonian, Sec. 6,
+ * including asynchronous multi-spin coding), the 3D Heisenberg model
+ * (Eq. On_hamiltonian, Sec. 5) and the replica-exchange step of parallel
+ * tempering (Eq. parallel_tempering, Sec. 7), plus the energy,
+ * magnetisation and overlap reductions.
+ *
+ * Conventions (shared with the test oracle, which implements them
+ * independently):
+ *   - a lattice has L^dim sites, x fastest, periodic boundaries, L even;
+ *     site i = (z*L + y)*L + x; colour c = (x + y + z) mod 2; colour 0 is
+ *     swept first; j = i >> 1 indexes a site inside its colour.
+ *   - random words come from Philox4x32-10 with key (seed lo, seed hi) and
+ *     counter (idx >> 2, sweep, lattice_id, tag << 28 | colour << 27 | extra);
+ *     word idx & 3 is used.  lattice_id = a << 24 | rkey << 12 | t for
+ *     replica set a, temperature slot t and realisation key rkey (the
+ *     realisation r for Ising/Heisenberg lattices, the group r >> 5 for EA).
+ *   - Ising/EA acceptance: flip iff dE <= 0 or r < thr(dE), with the integer
+ *     threshold thr(dE) = min(2^32 - 1, floor(exp(-beta dE) 2^32)) computed
+ *     on the host in double precision.  Ising and EA trajectories are
+ *     therefore exact integer functions of (seed, inputs).
+ *
+ * Ownership: every spin, coupling and output buffer is allocated and owned
+ * by the caller; the library only borrows device pointers while the work it
+ * enqueued on the handle's stream runs.  A handle owns small workspaces
+ * (threshold tables, reduction partials, an error word, and for the fused
+ * 2D int8 sweep one lattice-sized ping-pong buffer), allocated by spin_init
+ * and freed by spin_destroy.
+ *
+ * Errors: every entry point returns 0 (SPIN_OK) or a negative SPIN_E* code
+ * and never throws.  Work is asynchronous on the handle's stream; kernel
+ * faults and device-side timeouts surface from spin_sync (or the next call).
+ */
+#ifndef SPIN_GB300_H
+#define SPIN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPIN_OK 0
+#define SPIN_EINVAL (-1)   /* bad argument: odd L, bad layout/model, NaN beta ... */
+#define SPIN_EALIGN (-2)   /* a device pointer is not 16-byte aligned            */
+#define SPIN_ENOMEM (-3)   /* workspace allocation failed                        */
+#define SPIN_ECUDA (-4)    /* a CUDA runtime call or kernel failed               */
+#define SPIN_ETIMEOUT (-5) /* a bounded device-side wait gave up                 */
+
+typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
+
+/* Storage of the spins in device memory (lat = (a * n_temps + t) * n_real + r):
+ *  SPIN_I8     int8 +-1, [n_sets][n_temps][n_real][L^dim].  Ising (2D, 3D) and
+ *              EA (3D, one spin per byte: the per-realisation form).
+ *  SPIN_MSC1   1 bit per spin, bit set <=> s = -1, uint32 words.
+ *              EA (3D, asynchronous coding, Sec. 6): [n_sets][n_real/32]
+ *              [n_temps][L^3]; bit b of a word is realisation 32 g + b.
+ *              Ising 2D ferromagnet (synchronous coding): per lattice
+ *              [2 colours][L rows][L/64 words]; in row y the colour-c sites
+ *              x = 2k + ((c + y) & 1) are grouped in blocks of 128 k's, and
+ *              k = 128 B + 4 l + q is bit l of word 4 B + q.  Needs L % 256 == 0.
+ *  SPIN_F32X4  float4 (x, y, z, 0) unit vectors, [n_sets][n_temps][n_real][L^3].
+ * Couplings (EA only; NULL for the ferromagnet, J = 1):
+ *  SPIN_I8     int8 +-1, [n_real][dim][L^dim]: bond (i, i + e_d).
+ *  SPIN_MSC1   uint32 [n_real/32][dim][L^dim], bit b set <=> J = -1 for
+ *              realisation 32 g + b.
+ * All device buffers must be 16-byte aligned. */
+typedef enum { SPIN_I8 = 0, SPIN_MSC1 = 1, SPIN_F32X4 = 2 } spin_layout;
+
+typedef struct {
+  int32_t model;     /* spin_model                                             */
+  int32_t dim;       /* 2 or 3 (EA and Heisenberg: 3)                          */
+  int32_t L;         /* edge length: even, >= 4                                */
+  int32_t layout;    /* spin_layout                                            */
+  int32_t n_real;    /* lattices per (set, slot): EA disorder realisations     */
+                     /* (multiple of 32 for MSC1) or independent lattices      */
+  int32_t n_temps;   /* temperature slots (>= 1, <= 4096)                      */
+  int32_t n_sets;    /* replica sets (>= 1, <= 255; 2 for the overlap)         */
+  int32_t hot_start; /* 1: random start from the seed; 0: all spins +1 (+z)    */
+  uint64_t seed;     /* Philox key for every random number of this handle      */
+  void *stream;      /* cudaStream_t for all work of this handle; NULL = default */
+} spin_desc;
+
+typedef struct spin_lattice spin_lattice; /* opaque handle */
+
+/* Creates a handle for the caller-owned device buffers `spins` and
+ * `couplings` (NULL for the ferromagnet and Heisenberg) and enqueues their
+ * initialisation: spins from the INIT stream (hot start) or all +1, EA
+ * couplings from the COUPLING stream (bimodal, Eq. spinglass_hamiltonian).
+ * The sweep and exchange counters start at 0. */
+int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *couplings);
+
+/* n_sweeps checkerboard sweeps (Sec. 3.2; all colour-0 sites, then all
+ * colour-1 sites, each with Eq. metropolis or, for the Heisenberg model, a
+ * uniformly drawn new direction accepted with Eq. metropolis).  betas is a
+ * HOST array of n_temps inverse temperatures (beta >= 0, finite); couplings
+ * as in spin_init.  seed must equal the handle's seed (else SPIN_EINVAL).
+ * Sweep k of this call uses sweep counter value (sweeps done so far) + k, so
+ * consecutive calls continue one Markov chain.  Heisenberg spins are
+ * renormalised after every sweep whose 1-based count is a multiple of 100. */
+int spin_sweep(spin_lattice *lat, const void *couplings, const double *betas,
+               int64_t n_sweeps, uint64_t seed);
+
+/* Reductions over the current state (Sec. 4, measurement by binary-tree
+ * reduction; double accumulation for continuous spins, Sec. 5).  Device
+ * outputs, NULL to skip; lat index = (a * n_temps + t) * n_real + r:
+ *   E   int64 [n_lat]  E = -sum_<ij> J_ij s_i s_j        (Ising, EA)
+ *   M   int64 [n_lat]  M = sum_i s_i                     (Ising, EA)
+ *   Q   int64 [n_temps][n_real]  q = sum_i s_i^(0) s_i^(1) between sets 0, 1 (EA)
+ *   Ef  double [n_lat]     E = -sum_<ij> s_i . s_j       (Heisenberg)
+ *   Mf  double [n_lat][3]  M = sum_i s_i                 (Heisenberg) */
+int spin_measure(spin_lattice *lat, const void *couplings, int64_t *E, int64_t *M,
+                 int64_t *Q, double *Ef, double *Mf);
+
+/* One replica-exchange step (Eq. parallel_tempering) for Ising/EA handles:
+ * for every set a and realisation r, the slot pairs (t, t+1) with
+ * t = p (mod 2), p the handle's exchange counter, are tried with
+ * Delta = (beta_{t+1} - beta_t)(E_{t+1} - E_t): accepted iff Delta >= 0 or
+ * the PT word r < floor(exp(Delta) 2^32).  Accepted pairs exchange their
+ * configurations (bitwise for MSC1).  Energies are computed on the device
+ * from the current state.  accepted (device int64 [n_sets][n_temps], may be
+ * NULL) is incremented per accepted pair (t, t+1) at index t.  The exchange
+ * counter then advances by one. */
+int spin_pt_swap(spin_lattice *lat, const void *couplings, const double *betas,
+                 uint64_t seed, int64_t *accepted);
+
+/* A whole simulation on one handle: n_sweeps sweeps; after every sweep whose
+ * 1-based count is a multiple of measure_every (> 0) the measurements of
+ * spin_measure are appended to the series (device buffers, NULL to skip,
+ * row k holds measurement k); after every sweep whose count is a multiple
+ * of pt_every (> 0) one exchange step as in spin_pt_swap follows the
+ * measurement. */
+int spin_run(spin_lattice *lat, const void *couplings, const double *betas, int64_t n_sweeps,
+             int32_t measure_every, int32_t pt_every, int64_t *E_series, int64_t *M_series,
+             int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted);
+
+/* Layout conversion between the handle's layout and one int8 spin per site
+ * ([n_sets][n_temps][n_real][L^dim], +-1), device buffers. */
+int spin_unpack_i8(spin_lattice *lat, int8_t *out);
+int spin_pack_i8(spin_lattice *lat, const int8_t *in);
+
+/* Counter-based random words, exactly as the kernels draw them:
+ * out[k] = word k & 3 of Philox4x32-10(counter (k >> 2, sweep, lattice_id,
+ * tag << 28 | colour << 27 | extra), key (seed lo, seed hi)), k < count.
+ * out is a device buffer; the work runs on `stream`. */
+int spin_rng_fill(uint64_t seed, uint32_t tag, uint32_t colour, uint32_t extra,
+                  uint32_t lattice_id, uint32_t sweep, uint64_t count, uint32_t *out,
+                  void *stream);
+
+/* Generator throughput probe (the paper times its generators alone, Sec. 3.3):
+ * thread k < threads evaluates `calls` Philox4x32-10 blocks with counters
+ * (k + i * threads, 0, 0, 0), i < calls, key (seed lo, seed hi), and writes
+ * the XOR of all their words to out[k] (device buffer of `threads` words).
+ * threads * calls must stay below 2^32. */
+int spin_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out, void *stream);
+
+/* Waits for the handle's stream and reports asynchronous failures
+ * (SPIN_ECUDA, SPIN_ETIMEOUT).  Clears the device error word. */
+int spin_sync(spin_lattice *lat);
+
+/* Counters and tuning of a handle. */
+int64_t spin_sweeps_done(const spin_lattice *lat);
+int64_t spin_pt_steps_done(const spin_lattice *lat);
+int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_done);
+
+/* Selects the 2D int8 sweep kernel: 0 = two in-place colour phases per
+ * sweep, 1 = one fused out-of-place pass per sweep (default).  Both give
+ * identical results. */
+int spin_set_variant(spin_lattice *lat, int32_t variant);
+
+const char *spin_strerror(int code);
+void spin_destroy(spin_lattice *lat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPIN_GB300_H */

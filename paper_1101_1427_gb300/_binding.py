@@ -1,0 +1,167 @@
+"""Thin ctypes binding of the C ABI in include/spin.h.
+
+Argument marshalling only: every step of the sweep, exchange and reduction
+runs in the CUDA kernels of libspin_gb300.so.  There is no CPU fallback: if
+the library is missing or no GPU is present the calls raise.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspin_gb300.so")
+
+SPIN_OK, SPIN_EINVAL, SPIN_EALIGN, SPIN_ENOMEM, SPIN_ECUDA, SPIN_ETIMEOUT = 0, -1, -2, -3, -4, -5
+SPIN_ISING, SPIN_EA, SPIN_HEISENBERG = 0, 1, 2
+SPIN_I8, SPIN_MSC1, SPIN_F32X4 = 0, 1, 2
+TAG_UPDATE, TAG_INIT, TAG_COUPLING, TAG_PT, TAG_HEIS, TAG_HEIS_INIT = range(6)
+
+
+class spin_desc(C.Structure):
+    _fields_ = [("model", C.c_int32), ("dim", C.c_int32), ("L", C.c_int32),
+                ("layout", C.c_int32), ("n_real", C.c_int32), ("n_temps", C.c_int32),
+                ("n_sets", C.c_int32), ("hot_start", C.c_int32), ("seed", C.c_uint64),
+                ("stream", C.c_void_p)]
+
+
+class SpinError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads libspin_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        p, i32, i64, u32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+        L.spin_init.argtypes = [C.POINTER(p), C.POINTER(spin_desc), p, p]
+        L.spin_sweep.argtypes = [p, p, p, i64, u64]
+        L.spin_measure.argtypes = [p, p, p, p, p, p, p]
+        L.spin_pt_swap.argtypes = [p, p, p, u64, p]
+        L.spin_run.argtypes = [p, p, p, i64, i32, i32, p, p, p, p, p, p]
+        L.spin_unpack_i8.argtypes = [p, p]
+        L.spin_pack_i8.argtypes = [p, p]
+        L.spin_rng_fill.argtypes = [u64, u32, u32, u32, u32, u32, u64, p, p]
+        L.spin_rng_probe.argtypes = [u64, u32, u32, p, p]
+        L.spin_sync.argtypes = [p]
+        L.spin_sweeps_done.argtypes = [p]
+        L.spin_sweeps_done.restype = i64
+        L.spin_pt_steps_done.argtypes = [p]
+        L.spin_pt_steps_done.restype = i64
+        L.spin_set_counters.argtypes = [p, i64, i64]
+        L.spin_set_variant.argtypes = [p, i32]
+        L.spin_strerror.argtypes = [C.c_int]
+        L.spin_strerror.restype = C.c_char_p
+        L.spin_destroy.argtypes = [p]
+        L.spin_destroy.restype = None
+        for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
+                     "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
+                     "spin_set_counters", "spin_set_variant"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def spin_strerror(code):
+    return lib().spin_strerror(code).decode()
+
+
+def strerror(code):
+    try:
+        return spin_strerror(code)
+    except RuntimeError:
+        return str(code)
+
+
+def _check(rc, what):
+    if rc != SPIN_OK:
+        raise SpinError(rc, what)
+    return rc
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_doubles(values):
+    arr = (C.c_double * len(values))(*[float(v) for v in values])
+    return arr
+
+
+# ------------------------------------------------------------------ ABI names
+def spin_init(desc, spins, couplings=None):
+    h = C.c_void_p()
+    _check(lib().spin_init(C.byref(h), C.byref(desc), _ptr(spins), _ptr(couplings)), "spin_init")
+    return h
+
+
+def spin_sweep(h, couplings, betas, n_sweeps, seed):
+    return _check(lib().spin_sweep(h, _ptr(couplings), _host_doubles(betas), n_sweeps, seed),
+                  "spin_sweep")
+
+
+def spin_measure(h, couplings=None, E=None, M=None, Q=None, Ef=None, Mf=None):
+    return _check(lib().spin_measure(h, _ptr(couplings), _ptr(E), _ptr(M), _ptr(Q), _ptr(Ef),
+                                     _ptr(Mf)), "spin_measure")
+
+
+def spin_pt_swap(h, couplings, betas, seed, accepted=None):
+    return _check(lib().spin_pt_swap(h, _ptr(couplings), _host_doubles(betas), seed,
+                                     _ptr(accepted)), "spin_pt_swap")
+
+
+def spin_run(h, couplings, betas, n_sweeps, measure_every=0, pt_every=0, E=None, M=None,
+             Q=None, Ef=None, Mf=None, accepted=None):
+    return _check(lib().spin_run(h, _ptr(couplings), _host_doubles(betas), n_sweeps,
+                                 measure_every, pt_every, _ptr(E), _ptr(M), _ptr(Q), _ptr(Ef),
+                                 _ptr(Mf), _ptr(accepted)), "spin_run")
+
+
+def spin_unpack_i8(h, out):
+    return _check(lib().spin_unpack_i8(h, _ptr(out)), "spin_unpack_i8")
+
+
+def spin_pack_i8(h, inp):
+    return _check(lib().spin_pack_i8(h, _ptr(inp)), "spin_pack_i8")
+
+
+def spin_rng_fill(seed, tag, colour, extra, lattice_id, sweep, count, out, stream=None):
+    return _check(lib().spin_rng_fill(seed, tag, colour, extra, lattice_id, sweep, count,
+                                      _ptr(out), stream), "spin_rng_fill")
+
+
+def spin_rng_probe(seed, threads, calls, out, stream=None):
+    return _check(lib().spin_rng_probe(seed, threads, calls, _ptr(out), stream), "spin_rng_probe")
+
+
+def spin_sync(h):
+    return _check(lib().spin_sync(h), "spin_sync")
+
+
+def spin_sweeps_done(h):
+    return int(lib().spin_sweeps_done(h))
+
+
+def spin_pt_steps_done(h):
+    return int(lib().spin_pt_steps_done(h))
+
+
+def spin_set_counters(h, sweeps_done, pt_steps_done):
+    return _check(lib().spin_set_counters(h, sweeps_done, pt_steps_done), "spin_set_counters")
+
+
+def spin_set_variant(h, variant):
+    return _check(lib().spin_set_variant(h, variant), "spin_set_variant")
+
+
+def spin_destroy(h):
+    lib().spin_destroy(h)

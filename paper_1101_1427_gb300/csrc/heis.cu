@@ -1,0 +1,129 @@
+// 3D Heisenberg model (Eq. On_hamiltonian, n = 3) with FP32 unit vectors
+// stored as float4 (x, y, z, 0): hot start, checkerboard Metropolis sweep
+// with a uniformly drawn new direction (Sec. 5), renormalisation.
+#include "internal.h"
+
+namespace spin {
+namespace {
+
+// Uniform unit vector from two uniforms: z = 2 u1 - 1, phi = 2 pi u2.
+__device__ __forceinline__ float4 unit_vector(uint32_t w1, uint32_t w2) {
+  const float z = 2.0f * uniform24(w1) - 1.0f;
+  const float phi = 6.28318530717958647692f * uniform24(w2);
+  const float rho = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+  float sn, cs;
+  sincosf(phi, &sn, &cs);
+  return make_float4(rho * cs, rho * sn, z, 0.0f);
+}
+
+__global__ void heis_init_kernel(float4 *__restrict__ s, Geom g, int64_t n_lat, RoundKeys rk) {
+  const int64_t total = n_lat * g.N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / g.N, i = k - lat * g.N;
+    const uint4 w = philox(make_uint4((uint32_t)i, 0u, lattice_id_of(g, lat), ctr_w(TAG_HEIS_INIT, 0, 0)), rk);
+    s[k] = unit_vector(w.x, w.y);
+  }
+}
+
+__global__ void heis_cold_kernel(float4 *__restrict__ s, int64_t total) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x)
+    s[k] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+}
+
+// One colour phase.  Thread per colour site j (site i = 2j + parity); one
+// Philox call per site: words 0, 1 give the proposal, word 2 the acceptance
+// uniform.  dE = -(n - s) . h with h the sum of the six neighbour spins;
+// accept iff dE <= 0 or u3 < exp(-beta dE).  beta (float) is read from
+// word 0 of the slot's row of the threshold table.
+__global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s, Geom g,
+                                                         int64_t n_lat,
+                                                         const uint32_t *__restrict__ thr,
+                                                         RoundKeys rk, uint32_t sweep,
+                                                         int colour) {
+  const int L = g.L;
+  const int64_t half = g.N / 2;
+  const int64_t total = n_lat * half;
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / half, j = k - lat * half;
+    float4 *sl = s + lat * g.N;
+    const int64_t i0 = 2 * j;
+    const int x0 = (int)(i0 % L);
+    const int y = (int)((i0 / L) % L);
+    const int z = (int)(i0 / LL);
+    const int x = x0 + ((colour + y + z) & 1);
+    const int64_t rowbase = i0 - x0;
+    const int64_t i = rowbase + x;
+    const int64_t ixp = rowbase + (x == L - 1 ? 0 : x + 1);
+    const int64_t ixm = rowbase + (x == 0 ? L - 1 : x - 1);
+    const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * L : i + L;
+    const int64_t iym = y == 0 ? i + (int64_t)(L - 1) * L : i - L;
+    const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
+    const int64_t izm = z == 0 ? i + (int64_t)(L - 1) * LL : i - LL;
+    const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym], e = sl[izp], f = sl[izm];
+    const float hx = a.x + b.x + c.x + d.x + e.x + f.x;
+    const float hy = a.y + b.y + c.y + d.y + e.y + f.y;
+    const float hz = a.z + b.z + c.z + d.z + e.z + f.z;
+    const float4 si = sl[i];
+    const uint4 w = philox(make_uint4((uint32_t)j, sweep, lattice_id_of(g, lat),
+                                      ctr_w(TAG_HEIS, (uint32_t)colour, 0)), rk);
+    const float4 n = unit_vector(w.x, w.y);
+    const float u3 = uniform24(w.z);
+    const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
+    const float beta = __uint_as_float(__ldg(thr + 4 * slot_of(g, lat)));
+    if (dE <= 0.0f || u3 < expf(-beta * dE)) sl[i] = n;
+  }
+}
+
+// s <- s / |s| with IEEE sqrt and division.
+__global__ void heis_renorm_kernel(float4 *__restrict__ s, int64_t total) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    float4 v = s[k];
+    const float r = __fsqrt_rn(v.x * v.x + v.y * v.y + v.z * v.z);
+    v.x = __fdiv_rn(v.x, r);
+    v.y = __fdiv_rn(v.y, r);
+    v.z = __fdiv_rn(v.z, r);
+    s[k] = v;
+  }
+}
+
+unsigned capped_grid(int64_t n) {
+  unsigned g = grid_for(n, 256);
+  return g > (1u << 20) ? (1u << 20) : g;
+}
+
+}  // namespace
+
+cudaError_t launch_init_heis(spin_lattice *h) {
+  const int64_t total = h->n_lat * h->g.N;
+  if (h->d.hot_start)
+    heis_init_kernel<<<capped_grid(total), 256, 0, h->stream>>>((float4 *)h->spins, h->g, h->n_lat,
+                                                                  make_round_keys(h->d.seed));
+  else
+    heis_cold_kernel<<<capped_grid(total), 256, 0, h->stream>>>((float4 *)h->spins, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
+  const RoundKeys rk = make_round_keys(h->d.seed);
+  const int64_t half = h->n_lat * (h->g.N / 2);
+  for (int64_t k = 0; k < n_sweeps; ++k) {
+    const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
+    for (int colour = 0; colour < 2; ++colour)
+      heis_phase_kernel<<<capped_grid(half), 256, 0, h->stream>>>((float4 *)h->spins, h->g,
+                                                                  h->n_lat, h->d_thr, rk, sweep,
+                                                                  colour);
+    if ((sweep + 1u) % 100u == 0u)
+      heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>(
+          (float4 *)h->spins, h->n_lat * h->g.N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace spin

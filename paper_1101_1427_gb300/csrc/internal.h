@@ -1,0 +1,72 @@
+// Host-side handle and the launchers each translation unit provides.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/spin.h"
+#include "common.cuh"
+
+struct spin_lattice {
+  spin_desc d;
+  spin::Geom g;
+  cudaStream_t stream;
+  void *spins;           // caller-owned
+  void *couplings;       // caller-owned (may be NULL)
+  int64_t n_lat;         // n_sets * n_temps * n_real lattices
+  int64_t sweeps_done;
+  int64_t pt_steps_done;
+  int variant;           // 2D int8 sweep: 0 phases, 1 fused
+
+  // handle-owned device workspaces
+  uint32_t *d_thr;       // [n_temps][4] Metropolis thresholds, index dE/4
+  std::vector<double> betas_cached;
+  int thr_valid;
+  uint32_t *d_pt_thr;    // concatenated replica-exchange tables
+  int32_t *d_pt_off;     // [n_temps]: offset of pair t's table
+  int32_t *d_pt_len;     // [n_temps]: its length (entries beyond are 0)
+  double *d_pt_dbeta;    // [n_temps]: beta_{t+1} - beta_t
+  std::vector<double> pt_betas_cached;
+  int64_t *d_energy;     // [n_lat] scratch energies for the exchange step
+  int64_t *d_scratch64;  // small reduction scratch
+  int *d_err;            // device error word
+  void *d_pingpong;      // lattice-sized buffer of the fused 2D sweep (lazy)
+  size_t pingpong_bytes;
+};
+
+namespace spin {
+
+// ising_i8.cu
+cudaError_t launch_init_i8(spin_lattice *h);
+cudaError_t launch_couplings_i8(spin_lattice *h);
+cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps);
+
+// msc.cu
+cudaError_t launch_init_msc(spin_lattice *h);
+cudaError_t launch_couplings_msc(spin_lattice *h);
+cudaError_t launch_sweeps_msc(spin_lattice *h, const uint32_t *J, int64_t n_sweeps);
+cudaError_t launch_unpack_msc(spin_lattice *h, int8_t *out);
+cudaError_t launch_pack_msc(spin_lattice *h, const int8_t *in);
+
+// heis.cu
+cudaError_t launch_init_heis(spin_lattice *h);
+cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps);
+
+// measure.cu
+cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *M, int64_t *Q,
+                           double *Ef, double *Mf);
+cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted);
+
+// rng.cu
+cudaError_t launch_rng_fill(uint64_t seed, uint32_t w, uint32_t lattice_id, uint32_t sweep,
+                            uint64_t count, uint32_t *out, cudaStream_t s);
+cudaError_t launch_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out,
+                             cudaStream_t s);
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace spin

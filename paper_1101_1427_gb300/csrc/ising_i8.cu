@@ -1,0 +1,209 @@
+// Ising ferromagnet and +-J EA glass with one int8 (+-1) per spin:
+// initialisation, couplings and the checkerboard Metropolis sweep
+// (Sec. 3.2, Eq. metropolis, Eq. spinglass_hamiltonian).
+#include "internal.h"
+
+namespace spin {
+namespace {
+
+// ---------------------------------------------------------------- init
+// Hot start: s_i = -1 iff bit `bit` of the INIT word of site i is set, with
+// bit = r & 31 for EA lattices (the group's word is shared by its 32
+// realisations) and 0 otherwise.  One Philox call covers four sites.
+__global__ void init_i8_kernel(int8_t *__restrict__ spins, Geom g, int64_t n_lat, RoundKeys rk) {
+  const int64_t quads = (g.N + 3) / 4;
+  const int64_t total = n_lat * quads;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / quads, q4 = k - lat * quads;
+    const uint32_t bit = g.ea ? (uint32_t)(lat % g.n_real) & 31u : 0u;
+    const uint4 w = philox(make_uint4((uint32_t)q4, 0u, lattice_id_of(g, lat), ctr_w(TAG_INIT, 0, 0)), rk);
+    int8_t *s = spins + lat * g.N;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const int64_t i = 4 * q4 + q;
+      if (i < g.N) s[i] = ((word_of(w, q) >> bit) & 1u) ? (int8_t)-1 : (int8_t)1;
+    }
+  }
+}
+
+// Bimodal couplings (Eq. spinglass_hamiltonian): J[r][d][i] = -1 iff bit
+// r & 31 of the COUPLING word of (group r >> 5, direction d, site i) is set.
+__global__ void couplings_i8_kernel(int8_t *__restrict__ J, Geom g, RoundKeys rk) {
+  const int64_t quads = (g.N + 3) / 4;
+  const int64_t total = (int64_t)g.n_real * g.dim * quads;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rd = k / quads, q4 = k - rd * quads;
+    const int r = (int)(rd / g.dim), d = (int)(rd % g.dim);
+    const uint4 w = philox(make_uint4((uint32_t)q4, 0u, lattice_id(0, (uint32_t)r >> 5, 0),
+                                      ctr_w(TAG_COUPLING, 0, (uint32_t)d)), rk);
+    int8_t *out = J + rd * g.N;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const int64_t i = 4 * q4 + q;
+      if (i < g.N) out[i] = ((word_of(w, q) >> (r & 31)) & 1u) ? (int8_t)-1 : (int8_t)1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- 2D phase, L % 8 == 0
+// One thread owns eight consecutive bytes of a row (x = 8m .. 8m+7): the
+// four sites of the active colour among them draw their uniforms from one
+// Philox call (their colour indices j = yL/2 + 4m + q share j >> 2).  The
+// number of antiparallel neighbours of all eight bytes is formed at once
+// with byte-wise arithmetic on 64-bit words: for +-1 bytes, (a ^ b) & 2 is 2
+// iff a != b, so the sum of four such terms is 2n per byte (n <= 4, no
+// carries between bytes).  dE = 2 s h = 8 - 4n.
+__global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__ spins, int L,
+                                                            const uint32_t *__restrict__ thr,
+                                                            Geom g, RoundKeys rk, uint32_t sweep,
+                                                            int colour) {
+  const int chunks = L >> 3;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int64_t lat = blockIdx.z;
+  if (m >= chunks || y >= L) return;
+  int8_t *base = spins + lat * (int64_t)L * L;
+  const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+  const uint64_t *row = reinterpret_cast<const uint64_t *>(base + (int64_t)y * L);
+  const uint64_t C = row[m];
+  const uint64_t U = reinterpret_cast<const uint64_t *>(base + (int64_t)yu * L)[m];
+  const uint64_t D = reinterpret_cast<const uint64_t *>(base + (int64_t)yd * L)[m];
+  const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
+  const uint64_t lb = (uint8_t)base[(int64_t)y * L + xl];
+  const uint64_t rb = (uint8_t)base[(int64_t)y * L + xr];
+  const uint64_t MASK = 0x0202020202020202ull;
+  const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);
+  const uint64_t A = ((C ^ U) & MASK) + ((C ^ D) & MASK) + ((C ^ Lw) & MASK) + ((C ^ Rw) & MASK);
+  const int t = slot_of(g, lat);
+  const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
+  const uint32_t j4 = (uint32_t)y * (uint32_t)chunks + (uint32_t)m;
+  const uint4 r = philox(make_uint4(j4, sweep, lattice_id_of(g, lat), ctr_w(TAG_UPDATE, colour, 0)), rk);
+  const int p = (colour + y) & 1;
+  uint64_t F = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int b = p + 2 * q;
+    const uint32_t n2 = (uint32_t)(A >> (8 * b)) & 0xffu;
+    const uint32_t rq = word_of(r, q);
+    const bool flip = (n2 >= 4u) | ((n2 == 2u) & (rq < thr4)) | ((n2 == 0u) & (rq < thr8));
+    F |= flip ? (0xFEull << (8 * b)) : 0ull;
+  }
+  reinterpret_cast<uint64_t *>(base + (int64_t)y * L)[m] = C ^ F;
+}
+
+// ---------------------------------------------------------------- generic phase
+// Any even L, dim 2 or 3, ferromagnet (J == nullptr) or EA (J[r][d][i]).
+// One thread takes four consecutive colour indices j = 4 j4 .. 4 j4 + 3 (one
+// Philox call) and locates each site from its own coordinates.
+__global__ void __launch_bounds__(256) phase_generic_kernel(int8_t *__restrict__ spins,
+                                                            const int8_t *__restrict__ J,
+                                                            const uint32_t *__restrict__ thr,
+                                                            Geom g, int64_t n_lat, RoundKeys rk,
+                                                            uint32_t sweep, int colour) {
+  const int L = g.L;
+  const int64_t half = g.N / 2;
+  const int64_t quads = (half + 3) / 4;
+  const int64_t total = n_lat * quads;
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / quads, j4 = k - lat * quads;
+    int8_t *s = spins + lat * g.N;
+    const int8_t *Jr = J ? J + (lat % g.n_real) * (int64_t)g.dim * g.N : nullptr;
+    const int t = slot_of(g, lat);
+    const uint4 r = philox(make_uint4((uint32_t)j4, sweep, lattice_id_of(g, lat),
+                                      ctr_w(TAG_UPDATE, colour, 0)), rk);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t j = 4 * j4 + q;
+      if (j >= half) break;
+      const int64_t i0 = 2 * j;
+      const int x0 = (int)(i0 % L);
+      const int y = (int)((i0 / L) % L);
+      const int z = g.dim == 3 ? (int)(i0 / LL) : 0;
+      const int x = x0 + ((colour + y + z) & 1);
+      const int64_t rowbase = i0 - x0;
+      const int64_t i = rowbase + x;
+      const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+      const int64_t ystride = L;
+      const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * ystride : i + ystride;
+      const int64_t iym = y == 0 ? i + (int64_t)(L - 1) * ystride : i - ystride;
+      int h;
+      const int8_t sxp = s[rowbase + xp], sxm = s[rowbase + xm], syp = s[iyp], sym = s[iym];
+      if (Jr) {
+        h = Jr[i] * sxp + Jr[rowbase + xm] * sxm + Jr[g.N + i] * syp + Jr[g.N + iym] * sym;
+      } else {
+        h = sxp + sxm + syp + sym;
+      }
+      if (g.dim == 3) {
+        const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
+        const int64_t izm = z == 0 ? i + (int64_t)(L - 1) * LL : i - LL;
+        if (Jr)
+          h += Jr[2 * g.N + i] * s[izp] + Jr[2 * g.N + izm] * s[izm];
+        else
+          h += s[izp] + s[izm];
+      }
+      const int si = s[i];
+      const int dE = 2 * si * h;
+      const uint32_t rq = word_of(r, (uint32_t)q);
+      const bool flip = dE <= 0 || rq < __ldg(thr + 4 * t + (dE >> 2));
+      if (flip) s[i] = (int8_t)(-si);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_init_i8(spin_lattice *h) {
+  if (!h->d.hot_start)
+    return cudaMemsetAsync(h->spins, 1, (size_t)(h->n_lat * h->g.N), h->stream);
+  const int64_t total = h->n_lat * ((h->g.N + 3) / 4);
+  init_i8_kernel<<<grid_for(total, 256) > 65536u ? 65536u : grid_for(total, 256), 256, 0,
+                   h->stream>>>((int8_t *)h->spins, h->g, h->n_lat, make_round_keys(h->d.seed));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_couplings_i8(spin_lattice *h) {
+  const int64_t total = (int64_t)h->g.n_real * h->g.dim * ((h->g.N + 3) / 4);
+  unsigned grid = grid_for(total, 256);
+  if (grid > 65536u) grid = 65536u;
+  couplings_i8_kernel<<<grid, 256, 0, h->stream>>>((int8_t *)h->couplings, h->g,
+                                                    make_round_keys(h->d.seed));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused2d_i8(spin_lattice *h, int64_t n_sweeps);  // fused2d.cu
+bool fused2d_supported(int L);                                     // fused2d.cu
+
+cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps) {
+  const Geom &g = h->g;
+  const RoundKeys rk = make_round_keys(h->d.seed);
+  const bool fast2d = g.dim == 2 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
+  if (fast2d && h->variant == 1 && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
+  for (int64_t k = 0; k < n_sweeps; ++k) {
+    const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
+    for (int colour = 0; colour < 2; ++colour) {
+      if (fast2d) {
+        const int chunks = g.L / 8;
+        const int bx = chunks < 128 ? chunks : 128;
+        const int by = 256 / bx;
+        dim3 block(bx, by), grid((chunks + bx - 1) / bx, (g.L + by - 1) / by, (unsigned)h->n_lat);
+        ising2d_phase_kernel<<<grid, block, 0, h->stream>>>((int8_t *)h->spins, g.L, h->d_thr, g,
+                                                             rk, sweep, colour);
+      } else {
+        const int64_t total = h->n_lat * ((g.N / 2 + 3) / 4);
+        unsigned grid = grid_for(total, 256);
+        if (grid > 1u << 20) grid = 1u << 20;
+        phase_generic_kernel<<<grid, 256, 0, h->stream>>>((int8_t *)h->spins, J, h->d_thr, g,
+                                                           h->n_lat, rk, sweep, colour);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace spin

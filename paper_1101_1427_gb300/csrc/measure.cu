@@ -1,0 +1,347 @@
+// Reductions (energy, magnetisation, overlap; Sec. 4 measurements by
+// parallel reduction, double accumulation for continuous spins, Sec. 5)
+// and the replica-exchange step (Eq. parallel_tempering, Sec. 7).
+#include "internal.h"
+
+namespace spin {
+
+cudaError_t launch_measure_msc2d(spin_lattice *h, int64_t *E, int64_t *M);  // msc2d.cu
+
+namespace {
+
+__device__ __forceinline__ void add_ll(long long *p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+
+// ---------------------------------------------------------------- int8 lattices
+// E = -sum_{i,d} J_{i,d} s_i s_{i+d}, M = sum_i s_i; integer sums, so the
+// atomic accumulation order does not matter.
+__global__ void measure_i8_kernel(const int8_t *__restrict__ s, const int8_t *__restrict__ J,
+                                  Geom g, long long *__restrict__ E, long long *__restrict__ M) {
+  const int64_t lat = blockIdx.y;
+  const int8_t *sl = s + lat * g.N;
+  const int8_t *Jr = J ? J + (lat % g.n_real) * (int64_t)g.dim * g.N : nullptr;
+  const int L = g.L;
+  const int64_t LL = (int64_t)L * L;
+  long long e = 0, m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = g.dim == 3 ? (int)(i / LL) : 0;
+    const int si = sl[i];
+    const int64_t ixp = i - x + (x == L - 1 ? 0 : x + 1);
+    const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * L : i + L;
+    int bonds = (Jr ? Jr[i] : 1) * sl[ixp] + (Jr ? Jr[g.N + i] : 1) * sl[iyp];
+    if (g.dim == 3) {
+      const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
+      bonds += (Jr ? Jr[2 * g.N + i] : 1) * sl[izp];
+    }
+    e -= si * bonds;
+    m += si;
+  }
+  e = warp_sum(e);
+  m = warp_sum(m);
+  if ((threadIdx.x & 31) == 0) {
+    if (E) add_ll(&E[lat], e);
+    if (M) add_ll(&M[lat], m);
+  }
+}
+
+// q_{t,r} = sum_i s_i^(0) s_i^(1) between sets 0 and 1.
+__global__ void overlap_i8_kernel(const int8_t *__restrict__ s, Geom g, long long *__restrict__ Q) {
+  const int64_t tr = blockIdx.y;  // t * n_real + r
+  const int64_t set_stride = (int64_t)g.n_temps * g.n_real * g.N;
+  const int8_t *s0 = s + tr * g.N, *s1 = s0 + set_stride;
+  long long q = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    q += s0[i] * s1[i];
+  q = warp_sum(q);
+  if ((threadIdx.x & 31) == 0) add_ll(&Q[tr], q);
+}
+
+// ---------------------------------------------------------------- EA, coded words
+// Per word-lattice (a, g, t): counts per bit of unsatisfied bonds, down
+// spins and (set 0 only) spins differing from set 1.  Lane b of every warp
+// accumulates the count of bit b through 32 ballots per word.
+__device__ __forceinline__ void count_bits(uint32_t v, long long &acc, int lane) {
+#pragma unroll
+  for (int b = 0; b < 32; ++b) {
+    const int c = __popc(__ballot_sync(0xffffffffu, (v >> b) & 1u));
+    if (lane == b) acc += c;
+  }
+}
+
+__global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__restrict__ w,
+                                                          const uint32_t *__restrict__ J, Geom g,
+                                                          long long *__restrict__ E,
+                                                          long long *__restrict__ M,
+                                                          long long *__restrict__ Q) {
+  const int G = g.n_real / 32;
+  const int64_t wl = blockIdx.y;
+  const int t = (int)(wl % g.n_temps);
+  const int grp = (int)((wl / g.n_temps) % G);
+  const int a = (int)(wl / ((int64_t)g.n_temps * G));
+  const uint32_t *s = w + wl * g.N;
+  const uint32_t *Jg = J + (int64_t)grp * 3 * g.N;
+  const bool do_q = Q && a == 0 && g.n_sets >= 2;
+  const uint32_t *s1 = s + (int64_t)G * g.n_temps * g.N;  // set 1, same (g, t)
+  const int L = g.L;
+  const int64_t LL = (int64_t)L * L;
+  const int lane = threadIdx.x & 31;
+  long long unsat = 0, down = 0, diff = 0;
+  // every lane of a warp iterates the same number of times (ballots)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t warp_start = start - lane;
+  for (int64_t base = warp_start; base < g.N; base += stride) {
+    const int64_t i = base + lane;
+    uint32_t U = 0, D = 0, X = 0;
+    uint32_t U2 = 0, U3 = 0;
+    if (i < g.N) {
+      const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / LL);
+      const uint32_t S = s[i];
+      const int64_t ixp = i - x + (x == L - 1 ? 0 : x + 1);
+      const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * L : i + L;
+      const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
+      U = S ^ s[ixp] ^ Jg[i];
+      U2 = S ^ s[iyp] ^ Jg[g.N + i];
+      U3 = S ^ s[izp] ^ Jg[2 * g.N + i];
+      D = S;
+      if (do_q) X = S ^ s1[i];
+    }
+    count_bits(U, unsat, lane);
+    count_bits(U2, unsat, lane);
+    count_bits(U3, unsat, lane);
+    if (M) count_bits(D, down, lane);
+    if (do_q) count_bits(X, diff, lane);
+  }
+  // lane b holds this warp's counts for realisation 32 grp + b
+  const int64_t lat = ((int64_t)a * g.n_temps + t) * g.n_real + 32 * grp + lane;
+  if (E) add_ll(&E[lat], 2 * unsat);
+  if (M) add_ll(&M[lat], -2 * down);
+  if (do_q) add_ll(&Q[(int64_t)t * g.n_real + 32 * grp + lane], -2 * diff);
+}
+
+// constant parts: E = 2 unsat - 3N, M = N - 2 down, Q = N - 2 diff
+__global__ void add_const_kernel(long long *__restrict__ v, int64_t n, long long c) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[k] += c;
+}
+
+// ---------------------------------------------------------------- Heisenberg
+// Per-block partial sums in double, then a fixed-order second pass, so the
+// result does not depend on scheduling.
+constexpr int kHeisBlocks = 64;
+
+__global__ void measure_heis_kernel(const float4 *__restrict__ s, Geom g,
+                                    double *__restrict__ partial) {
+  const int64_t lat = blockIdx.y;
+  const float4 *sl = s + lat * g.N;
+  const int L = g.L;
+  const int64_t LL = (int64_t)L * L;
+  double e = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / LL);
+    const float4 a = sl[i];
+    const float4 bx = sl[i - x + (x == L - 1 ? 0 : x + 1)];
+    const float4 by = sl[y == L - 1 ? i - (int64_t)(L - 1) * L : i + L];
+    const float4 bz = sl[z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL];
+    const double ax = a.x, ay = a.y, az = a.z;
+    e -= ax * ((double)bx.x + (double)by.x + (double)bz.x) +
+         ay * ((double)bx.y + (double)by.y + (double)bz.y) +
+         az * ((double)bx.z + (double)by.z + (double)bz.z);
+    mx += ax;
+    my += ay;
+    mz += az;
+  }
+  __shared__ double red[4][32];
+  e = warp_sum(e);
+  mx = warp_sum(mx);
+  my = warp_sum(my);
+  mz = warp_sum(mz);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][wid] = e;
+    red[1][wid] = mx;
+    red[2][wid] = my;
+    red[3][wid] = mz;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double acc = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) acc += red[threadIdx.x][k];
+    partial[(lat * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = acc;
+  }
+}
+
+__global__ void finish_heis_kernel(const double *__restrict__ partial, int64_t n_lat, int nb,
+                                   double *__restrict__ Ef, double *__restrict__ Mf) {
+  const int64_t lat = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (lat >= n_lat) return;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nb; ++b)
+    for (int c = 0; c < 4; ++c) acc[c] += partial[(lat * nb + b) * 4 + c];
+  if (Ef) Ef[lat] = acc[0];
+  if (Mf) {
+    Mf[3 * lat] = acc[1];
+    Mf[3 * lat + 1] = acc[2];
+    Mf[3 * lat + 2] = acc[3];
+  }
+}
+
+// ---------------------------------------------------------------- replica exchange
+// Thread per (set a, realisation r, pair t) of the step's parity.
+// Delta = dbeta_t (E_{t+1} - E_t); accept iff Delta >= 0 or the PT word of
+// (a, t, step, r) is below the tabulated threshold of exp(Delta).
+__global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
+                                 const double *__restrict__ dbeta,
+                                 const uint32_t *__restrict__ tab, const int32_t *__restrict__ off,
+                                 const int32_t *__restrict__ len, RoundKeys rk, uint32_t step,
+                                 uint8_t *__restrict__ decision, long long *__restrict__ accepted) {
+  const int parity = (int)(step & 1u);
+  const int n_pairs = (g.n_temps - parity) / 2;  // pairs (t, t+1), t = parity + 2k
+  const int64_t total = (int64_t)g.n_sets * n_pairs * g.n_real;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  const int r = (int)(k % g.n_real);
+  const int pk = (int)((k / g.n_real) % n_pairs);
+  const int a = (int)(k / ((int64_t)g.n_real * n_pairs));
+  const int t = parity + 2 * pk;
+  const int64_t lat0 = ((int64_t)a * g.n_temps + t) * g.n_real + r;
+  const int64_t lat1 = lat0 + g.n_real;
+  const long long dE = E[lat1] - E[lat0];
+  const double db = dbeta[t];
+  bool acc;
+  if (db * (double)dE >= 0.0) {
+    acc = true;
+  } else {
+    const long long m = (dE < 0 ? -dE : dE) / 4;
+    const uint32_t thr = m < len[t] ? tab[off[t] + m] : 0u;
+    const uint4 w = philox(make_uint4((uint32_t)r >> 2, step, lattice_id(a, 0, t), ctr_w(TAG_PT, 0, 0)), rk);
+    acc = word_of(w, (uint32_t)r & 3u) < thr;
+  }
+  decision[lat0] = acc ? 1 : 0;
+  if (acc && accepted) add_ll(&accepted[a * g.n_temps + t], 1);
+}
+
+// Exchange of whole lattices (int8, or coded 2D lattices), 16 bytes per thread.
+__global__ void pt_swap_bytes_kernel(uint8_t *__restrict__ s, const uint8_t *__restrict__ decision,
+                                     Geom g, int parity, int64_t lat_bytes) {
+  const int64_t lat0 = blockIdx.y;
+  const int t = slot_of(g, lat0);
+  if (((t - parity) & 1) || t + 1 >= g.n_temps || !decision[lat0]) return;
+  uint4 *p0 = reinterpret_cast<uint4 *>(s + lat0 * lat_bytes);
+  uint4 *p1 = reinterpret_cast<uint4 *>(s + (lat0 + g.n_real) * lat_bytes);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < lat_bytes / 16;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 a = p0[k], b = p1[k];
+    p0[k] = b;
+    p1[k] = a;
+  }
+}
+
+// Bitwise exchange of coded EA words: per (a, g, pair) the accepted
+// realisations form a mask A; x = (w_t ^ w_{t+1}) & A exchanges those bits.
+__global__ void pt_swap_msc_kernel(uint32_t *__restrict__ w, const uint8_t *__restrict__ decision,
+                                   Geom g, int parity) {
+  const int G = g.n_real / 32;
+  const int64_t wl = blockIdx.y;  // (a, grp, t)
+  const int t = (int)(wl % g.n_temps);
+  if (((t - parity) & 1) || t + 1 >= g.n_temps) return;
+  const int grp = (int)((wl / g.n_temps) % G);
+  const int a = (int)(wl / ((int64_t)g.n_temps * G));
+  uint32_t mask = 0;
+  const int64_t lat0 = ((int64_t)a * g.n_temps + t) * g.n_real + 32 * grp;
+  for (int b = 0; b < 32; ++b) mask |= (uint32_t)decision[lat0 + b] << b;
+  if (!mask) return;
+  uint32_t *w0 = w + wl * g.N, *w1 = w0 + g.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a0 = w0[i], a1 = w1[i];
+    const uint32_t x = (a0 ^ a1) & mask;
+    w0[i] = a0 ^ x;
+    w1[i] = a1 ^ x;
+  }
+}
+
+unsigned capped(int64_t n, unsigned cap) {
+  unsigned g = grid_for(n, 256);
+  return g > cap ? cap : g;
+}
+
+}  // namespace
+
+cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *M, int64_t *Q,
+                           double *Ef, double *Mf) {
+  const Geom &g = h->g;
+  cudaStream_t st = h->stream;
+  const int64_t nl = h->n_lat;
+  if (h->d.model == SPIN_HEISENBERG) {
+    if (!Ef && !Mf) return cudaSuccess;
+    double *partial = (double *)h->d_scratch64;
+    measure_heis_kernel<<<dim3(kHeisBlocks, (unsigned)nl), 256, 0, st>>>((const float4 *)h->spins,
+                                                                         g, partial);
+    finish_heis_kernel<<<grid_for(nl, 128), 128, 0, st>>>(partial, nl, kHeisBlocks, Ef, Mf);
+    return cudaGetLastError();
+  }
+  if (h->d.layout == SPIN_MSC1 && h->d.model == SPIN_ISING) {
+    if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
+    return launch_measure_msc2d(h, E, M);
+  }
+  if (E) cudaMemsetAsync(E, 0, sizeof(int64_t) * nl, st);
+  if (M) cudaMemsetAsync(M, 0, sizeof(int64_t) * nl, st);
+  if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
+  if (h->d.layout == SPIN_I8) {
+    if (E || M)
+      measure_i8_kernel<<<dim3(capped(g.N, 1024), (unsigned)nl), 256, 0, st>>>(
+          (const int8_t *)h->spins, (const int8_t *)J, g, (long long *)E, (long long *)M);
+    if (Q && g.n_sets >= 2)
+      overlap_i8_kernel<<<dim3(capped(g.N, 1024), (unsigned)(g.n_temps * g.n_real)), 256, 0, st>>>(
+          (const int8_t *)h->spins, g, (long long *)Q);
+    return cudaGetLastError();
+  }
+  // EA coded words
+  const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
+  unsigned gx = capped(g.N, 64);
+  measure_msc_kernel<<<dim3(gx, (unsigned)n_wl), 256, 0, st>>>(
+      (const uint32_t *)h->spins, (const uint32_t *)J, g, (long long *)E, (long long *)M,
+      (g.n_sets >= 2) ? (long long *)Q : nullptr);
+  if (E) add_const_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)E, nl, -3 * (long long)g.N);
+  if (M) add_const_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)M, nl, (long long)g.N);
+  if (Q && g.n_sets >= 2)
+    add_const_kernel<<<capped((int64_t)g.n_temps * g.n_real, 4096), 256, 0, st>>>(
+        (long long *)Q, (int64_t)g.n_temps * g.n_real, (long long)g.N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted) {
+  const Geom &g = h->g;
+  cudaStream_t st = h->stream;
+  cudaError_t e = launch_measure(h, J, h->d_energy, nullptr, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  const uint32_t step = (uint32_t)h->pt_steps_done;
+  const int parity = (int)(step & 1u);
+  const int n_pairs = (g.n_temps - parity) / 2;
+  uint8_t *decision = (uint8_t *)(h->d_energy + 2 * h->n_lat);
+  if (n_pairs <= 0) return cudaSuccess;
+  const int64_t total = (int64_t)g.n_sets * n_pairs * g.n_real;
+  pt_decide_kernel<<<grid_for(total, 256), 256, 0, st>>>(
+      (const long long *)h->d_energy, g, h->d_pt_dbeta, h->d_pt_thr, h->d_pt_off, h->d_pt_len,
+      make_round_keys(h->d.seed), step, decision, (long long *)accepted);
+  if (h->d.layout == SPIN_MSC1 && h->d.model == SPIN_EA) {
+    const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
+    pt_swap_msc_kernel<<<dim3(capped(g.N, 64), (unsigned)n_wl), 256, 0, st>>>(
+        (uint32_t *)h->spins, decision, g, parity);
+  } else {
+    int64_t lat_bytes = g.N;  // int8
+    if (h->d.layout == SPIN_MSC1) lat_bytes = g.N / 8;
+    if (h->d.layout == SPIN_F32X4) lat_bytes = g.N * 16;
+    pt_swap_bytes_kernel<<<dim3(capped(lat_bytes / 16, 1024), (unsigned)h->n_lat), 256, 0, st>>>(
+        (uint8_t *)h->spins, decision, g, parity, lat_bytes);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace spin

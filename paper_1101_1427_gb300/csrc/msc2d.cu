@@ -1,0 +1,289 @@
+// 2D Ising ferromagnet with synchronous multi-spin coding (Sec. 6: several
+// spins of one lattice per word).  Per lattice the spins are stored as
+// [2 colours][L rows][L/64 words]; in row y the colour-c sites are
+// x = 2k + ((c + y) & 1), k = 0 .. L/2-1, grouped in blocks of 128 k's with
+// k = 128 B + 4 l + q stored in bit l of word 4 B + q (bit set <=> s = -1).
+//
+// Every site keeps its own uniform (sites of one lattice must not share
+// random numbers), drawn exactly as in the int8 layout: for k = 128 B + 4 l + q
+// the colour index is j = y L/2 + k, so lane l of a warp computes the Philox
+// call j >> 2 = y L/8 + 32 B + l and its word q belongs to word 4 B + q,
+// bit l.  The comparisons with the two thresholds become masks through
+// warp ballots; the neighbour count and the flip decision are bit-sliced.
+#include "internal.h"
+
+namespace spin {
+namespace {
+
+struct Msc2d {
+  int L;
+  int wpr;   // words per row and colour = L / 64
+  int bpr;   // blocks per row = L / 256
+  int64_t lat_words;  // 2 * L * wpr
+};
+
+__device__ __forceinline__ int64_t row_word(const Msc2d &m, int64_t lat, int c, int y) {
+  return lat * m.lat_words + ((int64_t)c * m.L + y) * m.wpr;
+}
+
+// One colour phase.  Each warp owns 32 consecutive blocks of the global
+// block list (lattice, row, block); first every lane draws its uniforms for
+// each of those blocks in turn and the ballots of (r < thr4), (r < thr8) are
+// kept by the lane that owns the block; then each lane updates its block.
+__global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__ w, Msc2d m,
+                                                          Geom g, int64_t n_lat,
+                                                          const uint32_t *__restrict__ thr,
+                                                          RoundKeys rk, uint32_t sweep,
+                                                          int colour) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t total_blocks = n_lat * m.L * m.bpr;
+  const int64_t first = warp * 32;
+  if (first >= total_blocks) return;
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  uint32_t m4[4] = {0, 0, 0, 0}, m8[4] = {0, 0, 0, 0};
+  for (int b = 0; b < 32; ++b) {
+    const int64_t gb = first + b;
+    if (gb >= total_blocks) break;  // uniform over the warp
+    const int64_t lat = gb / ((int64_t)m.L * m.bpr);
+    const int64_t rem = gb - lat * ((int64_t)m.L * m.bpr);
+    const int y = (int)(rem / m.bpr), B = (int)(rem % m.bpr);
+    const int t = slot_of(g, lat);
+    const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
+    const uint32_t j4 = (uint32_t)y * (uint32_t)(m.L >> 3) + 32u * (uint32_t)B + (uint32_t)lane;
+    const uint4 r = philox(make_uint4(j4, sweep, lattice_id_of(g, lat), wctr), rk);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t rq = word_of(r, q);
+      const uint32_t b4 = __ballot_sync(0xffffffffu, rq < thr4);
+      const uint32_t b8 = __ballot_sync(0xffffffffu, rq < thr8);
+      if (lane == b) {
+        m4[q] = b4;
+        m8[q] = b8;
+      }
+    }
+  }
+  const int64_t gb = first + lane;
+  if (gb >= total_blocks) return;
+  const int64_t lat = gb / ((int64_t)m.L * m.bpr);
+  const int64_t rem = gb - lat * ((int64_t)m.L * m.bpr);
+  const int y = (int)(rem / m.bpr), B = (int)(rem % m.bpr);
+  const int yu = y == 0 ? m.L - 1 : y - 1, yd = y == m.L - 1 ? 0 : y + 1;
+  const int oc = colour ^ 1;
+  uint32_t *S = w + row_word(m, lat, colour, y) + 4 * B;
+  const uint32_t *O = w + row_word(m, lat, oc, y);
+  const uint32_t *Uu = w + row_word(m, lat, oc, yu) + 4 * B;
+  const uint32_t *Dd = w + row_word(m, lat, oc, yd) + 4 * B;
+  const uint4 s = *reinterpret_cast<const uint4 *>(S);
+  const uint4 o = *reinterpret_cast<const uint4 *>(O + 4 * B);
+  const uint4 u = *reinterpret_cast<const uint4 *>(Uu);
+  const uint4 d = *reinterpret_cast<const uint4 *>(Dd);
+  const int p = (colour + y) & 1;
+  // second horizontal neighbour: k - 1 (p = 0) or k + 1 (p = 1)
+  uint32_t sh[4];
+  if (p == 0) {
+    const int Bp = B == 0 ? m.bpr - 1 : B - 1;
+    const uint32_t prev3 = O[4 * Bp + 3];
+    sh[0] = (o.w << 1) | (prev3 >> 31);
+    sh[1] = o.x;
+    sh[2] = o.y;
+    sh[3] = o.z;
+  } else {
+    const int Bn = B == m.bpr - 1 ? 0 : B + 1;
+    const uint32_t next0 = O[4 * Bn];
+    sh[0] = o.y;
+    sh[1] = o.z;
+    sh[2] = o.w;
+    sh[3] = (o.x >> 1) | (next0 << 31);
+  }
+  const uint32_t sv[4] = {s.x, s.y, s.z, s.w}, ov[4] = {o.x, o.y, o.z, o.w};
+  const uint32_t uv[4] = {u.x, u.y, u.z, u.w}, dv[4] = {d.x, d.y, d.z, d.w};
+  uint32_t nv[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t a0 = sv[q] ^ uv[q], a1 = sv[q] ^ dv[q], a2 = sv[q] ^ ov[q], a3 = sv[q] ^ sh[q];
+    const uint32_t s1 = a0 ^ a1, c1 = a0 & a1, s2 = a2 ^ a3, c2 = a2 & a3;
+    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
+    const uint32_t b1 = c1 ^ c2 ^ c3, b2 = (c1 & c2) | (c3 & (c1 ^ c2));
+    // n antiparallel neighbours, dE = 8 - 4n
+    const uint32_t ge2 = b2 | b1, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
+    nv[q] = sv[q] ^ (ge2 | (eq1 & m4[q]) | (eq0 & m8[q]));
+  }
+  *reinterpret_cast<uint4 *>(S) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
+}
+
+// Hot start: bit 0 of the INIT word of each site, as in the int8 layout.
+__global__ void msc2d_init_kernel(uint32_t *__restrict__ w, Msc2d m, Geom g, int64_t n_lat,
+                                  RoundKeys rk, int hot) {
+  const int64_t total = n_lat * m.lat_words;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (!hot) {
+      w[k] = 0u;
+      continue;
+    }
+    const int64_t lat = k / m.lat_words;
+    const int64_t rem = k - lat * m.lat_words;
+    const int c = (int)(rem / ((int64_t)m.L * m.wpr));
+    const int y = (int)((rem / m.wpr) % m.L);
+    const int wi = (int)(rem % m.wpr);
+    const int B = wi >> 2, q = wi & 3;
+    const int p = (c + y) & 1;
+    const uint32_t lid = lattice_id_of(g, lat);
+    uint32_t v = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int k2 = 128 * B + 4 * l + q;
+      const int64_t i = (int64_t)y * m.L + 2 * k2 + p;
+      const uint4 r = philox(make_uint4((uint32_t)(i >> 2), 0u, lid, ctr_w(TAG_INIT, 0, 0)), rk);
+      v |= (word_of(r, (uint32_t)(i & 3)) & 1u) << l;
+    }
+    w[k] = v;
+  }
+}
+
+__global__ void msc2d_unpack_kernel(const uint32_t *__restrict__ w, int8_t *__restrict__ out,
+                                    Msc2d m, int64_t n_lat) {
+  const int64_t N = (int64_t)m.L * m.L;
+  const int64_t total = n_lat * N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / N, i = k - lat * N;
+    const int y = (int)(i / m.L), x = (int)(i % m.L);
+    const int c = (x + y) & 1, kk = x >> 1;
+    const int B = kk >> 7, l = (kk >> 2) & 31, q = kk & 3;
+    const uint32_t v = w[row_word(m, lat, c, y) + 4 * B + q];
+    out[k] = ((v >> l) & 1u) ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+__global__ void msc2d_pack_kernel(const int8_t *__restrict__ in, uint32_t *__restrict__ w,
+                                  Msc2d m, int64_t n_lat) {
+  const int64_t total = n_lat * m.lat_words;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / m.lat_words;
+    const int64_t rem = k - lat * m.lat_words;
+    const int c = (int)(rem / ((int64_t)m.L * m.wpr));
+    const int y = (int)((rem / m.wpr) % m.L);
+    const int wi = (int)(rem % m.wpr);
+    const int B = wi >> 2, q = wi & 3;
+    const int p = (c + y) & 1;
+    uint32_t v = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int x = 2 * (128 * B + 4 * l + q) + p;
+      v |= (in[lat * (int64_t)m.L * m.L + (int64_t)y * m.L + x] < 0 ? 1u : 0u) << l;
+    }
+    w[k] = v;
+  }
+}
+
+Msc2d geom2d(const spin_lattice *h) {
+  Msc2d m;
+  m.L = h->g.L;
+  m.wpr = m.L / 64;
+  m.bpr = m.L / 256;
+  m.lat_words = 2 * (int64_t)m.L * m.wpr;
+  return m;
+}
+
+unsigned capped2(int64_t n) {
+  unsigned g = grid_for(n, 256);
+  return g > (1u << 20) ? (1u << 20) : g;
+}
+
+}  // namespace
+
+cudaError_t launch_init_msc2d(spin_lattice *h) {
+  const Msc2d m = geom2d(h);
+  msc2d_init_kernel<<<capped2(h->n_lat * m.lat_words), 256, 0, h->stream>>>(
+      (uint32_t *)h->spins, m, h->g, h->n_lat, make_round_keys(h->d.seed), h->d.hot_start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweeps_msc2d(spin_lattice *h, int64_t n_sweeps) {
+  const Msc2d m = geom2d(h);
+  const RoundKeys rk = make_round_keys(h->d.seed);
+  const int64_t blocks = h->n_lat * m.L * m.bpr;
+  const int64_t threads = ((blocks + 31) / 32) * 32;
+  for (int64_t k = 0; k < n_sweeps; ++k) {
+    const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
+    for (int colour = 0; colour < 2; ++colour)
+      msc2d_phase_kernel<<<grid_for(threads, 256), 256, 0, h->stream>>>(
+          (uint32_t *)h->spins, m, h->g, h->n_lat, h->d_thr, rk, sweep, colour);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_unpack_msc2d(spin_lattice *h, int8_t *out) {
+  const Msc2d m = geom2d(h);
+  msc2d_unpack_kernel<<<capped2(h->n_lat * h->g.N), 256, 0, h->stream>>>(
+      (const uint32_t *)h->spins, out, m, h->n_lat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_msc2d(spin_lattice *h, const int8_t *in) {
+  const Msc2d m = geom2d(h);
+  msc2d_pack_kernel<<<capped2(h->n_lat * m.lat_words), 256, 0, h->stream>>>(
+      in, (uint32_t *)h->spins, m, h->n_lat);
+  return cudaGetLastError();
+}
+
+// Energy and magnetisation of the 2D coded lattices: every bond joins a
+// colour-0 and a colour-1 site, so counting the antiparallel neighbours of
+// the colour-0 words counts each bond once; E = 2 n_anti - 2N, M = N - 2 n_down.
+__global__ void msc2d_measure_kernel(const uint32_t *__restrict__ w, Msc2d m, int64_t n_lat,
+                                     long long *__restrict__ E, long long *__restrict__ M) {
+  const int64_t lat = blockIdx.y;
+  const int64_t words = (int64_t)m.L * m.wpr;  // colour-0 words of one lattice
+  long long anti = 0, down = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < words;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(k / m.wpr), wi = (int)(k % m.wpr);
+    const int B = wi >> 2, q = wi & 3;
+    const int yu = y == 0 ? m.L - 1 : y - 1, yd = y == m.L - 1 ? 0 : y + 1;
+    const uint32_t S = w[row_word(m, lat, 0, y) + wi];
+    const uint32_t *O = w + row_word(m, lat, 1, y);
+    const uint32_t up = w[row_word(m, lat, 1, yu) + wi], dn = w[row_word(m, lat, 1, yd) + wi];
+    uint32_t sh;
+    if (((0 + y) & 1) == 0) {
+      const int Bp = B == 0 ? m.bpr - 1 : B - 1;
+      sh = q == 0 ? (O[4 * B + 3] << 1) | (O[4 * Bp + 3] >> 31) : O[4 * B + q - 1];
+    } else {
+      const int Bn = B == m.bpr - 1 ? 0 : B + 1;
+      sh = q == 3 ? (O[4 * B] >> 1) | (O[4 * Bn] << 31) : O[4 * B + q + 1];
+    }
+    anti += __popc(S ^ up) + __popc(S ^ dn) + __popc(S ^ O[wi]) + __popc(S ^ sh);
+    down += __popc(S) + __popc(w[row_word(m, lat, 1, y) + wi]);
+  }
+  anti = warp_sum(anti);
+  down = warp_sum(down);
+  if ((threadIdx.x & 31) == 0) {
+    const long long N = (long long)m.L * m.L;
+    atomicAdd((unsigned long long *)&E[lat], (unsigned long long)(2 * anti));
+    atomicAdd((unsigned long long *)&M[lat], (unsigned long long)(-2 * down));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicAdd((unsigned long long *)&E[lat], (unsigned long long)(-2 * N));
+      atomicAdd((unsigned long long *)&M[lat], (unsigned long long)N);
+    }
+  }
+}
+
+cudaError_t launch_measure_msc2d(spin_lattice *h, int64_t *E, int64_t *M) {
+  const Msc2d m = geom2d(h);
+  long long *e = (long long *)E, *mm = (long long *)M;
+  // both outputs are required by the kernel; route a missing one to scratch
+  if (!e) e = (long long *)h->d_energy;
+  if (!mm) mm = (long long *)h->d_energy + h->n_lat;
+  cudaMemsetAsync(e, 0, sizeof(long long) * h->n_lat, h->stream);
+  cudaMemsetAsync(mm, 0, sizeof(long long) * h->n_lat, h->stream);
+  const int64_t words = (int64_t)m.L * m.wpr;
+  unsigned gx = grid_for(words, 256);
+  if (gx > 4096u) gx = 4096u;
+  msc2d_measure_kernel<<<dim3(gx, (unsigned)h->n_lat), 256, 0, h->stream>>>(
+      (const uint32_t *)h->spins, m, h->n_lat, e, mm);
+  return cudaGetLastError();
+}
+
+}  // namespace spin

@@ -1,0 +1,130 @@
+"""A library handle together with the device tensors it borrows.
+
+PyTorch provides the device memory and the stream; the spins, couplings and
+measurement buffers are plain CUDA tensors whose pointers are passed through
+the C ABI.  No arithmetic of the method happens here.
+"""
+import torch
+
+from . import _binding as B
+
+
+def _words(model, layout, dim, L, n_real, n_temps, n_sets):
+    N = L ** dim
+    n_lat = n_sets * n_temps * n_real
+    if layout == B.SPIN_I8:
+        return torch.int8, n_lat * N
+    if layout == B.SPIN_F32X4:
+        return torch.float32, 4 * n_lat * N
+    if model == B.SPIN_EA:
+        return torch.int32, n_sets * (n_real // 32) * n_temps * N
+    return torch.int32, n_lat * 2 * L * (L // 64)
+
+
+class Lattice:
+    """Spins (and couplings) on the current CUDA device plus a handle.
+
+    model: SPIN_ISING / SPIN_EA / SPIN_HEISENBERG; layout: SPIN_I8 /
+    SPIN_MSC1 / SPIN_F32X4.  Lattice index lat = (a * n_temps + t) * n_real + r.
+    """
+
+    def __init__(self, model, dim, L, layout, n_real=1, n_temps=1, n_sets=1, seed=1,
+                 hot_start=True, stream=None, device=None):
+        self.model, self.dim, self.L, self.layout = model, dim, L, layout
+        self.n_real, self.n_temps, self.n_sets = n_real, n_temps, n_sets
+        self.seed = seed
+        self.N = L ** dim
+        self.n_lat = n_sets * n_temps * n_real
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        dtype, count = _words(model, layout, dim, L, n_real, n_temps, n_sets)
+        self.spins = torch.empty(count, dtype=dtype, device=self.device)
+        self.couplings = None
+        if model == B.SPIN_EA:
+            if layout == B.SPIN_I8:
+                self.couplings = torch.empty(n_real * dim * self.N, dtype=torch.int8,
+                                             device=self.device)
+            else:
+                self.couplings = torch.empty((n_real // 32) * dim * self.N, dtype=torch.int32,
+                                             device=self.device)
+        self.desc = B.spin_desc(model, dim, L, layout, n_real, n_temps, n_sets, int(hot_start),
+                                seed, self.stream.cuda_stream)
+        self.h = B.spin_init(self.desc, self.spins, self.couplings)
+
+    # -------------------------------------------------------------- the ABI calls
+    def sweep(self, betas, n_sweeps=1):
+        B.spin_sweep(self.h, self.couplings, list(betas), n_sweeps, self.seed)
+
+    def measure(self):
+        """Returns device tensors (E, M, Q) or (Ef, Mf) for Heisenberg."""
+        if self.model == B.SPIN_HEISENBERG:
+            Ef = torch.empty(self.n_lat, dtype=torch.float64, device=self.device)
+            Mf = torch.empty(self.n_lat * 3, dtype=torch.float64, device=self.device)
+            B.spin_measure(self.h, None, Ef=Ef, Mf=Mf)
+            return Ef, Mf.view(self.n_lat, 3)
+        E = torch.empty(self.n_lat, dtype=torch.int64, device=self.device)
+        M = torch.empty(self.n_lat, dtype=torch.int64, device=self.device)
+        Q = None
+        if self.n_sets >= 2:
+            Q = torch.empty(self.n_temps * self.n_real, dtype=torch.int64, device=self.device)
+        B.spin_measure(self.h, self.couplings, E=E, M=M, Q=Q)
+        return E, M, Q
+
+    def pt_swap(self, betas, accepted=None):
+        B.spin_pt_swap(self.h, self.couplings, list(betas), self.seed, accepted)
+
+    def run(self, betas, n_sweeps, measure_every=0, pt_every=0, series=True, accepted=None):
+        n_meas = n_sweeps // measure_every if measure_every > 0 else 0
+        out = {}
+        if series and n_meas:
+            if self.model == B.SPIN_HEISENBERG:
+                out["Ef"] = torch.empty(n_meas * self.n_lat, dtype=torch.float64, device=self.device)
+                out["Mf"] = torch.empty(n_meas * self.n_lat * 3, dtype=torch.float64,
+                                        device=self.device)
+            else:
+                out["E"] = torch.empty(n_meas * self.n_lat, dtype=torch.int64, device=self.device)
+                out["M"] = torch.empty(n_meas * self.n_lat, dtype=torch.int64, device=self.device)
+                if self.n_sets >= 2:
+                    out["Q"] = torch.empty(n_meas * self.n_temps * self.n_real, dtype=torch.int64,
+                                           device=self.device)
+        B.spin_run(self.h, self.couplings, list(betas), n_sweeps, measure_every, pt_every,
+                   out.get("E"), out.get("M"), out.get("Q"), out.get("Ef"), out.get("Mf"),
+                   accepted)
+        return out
+
+    def unpack(self):
+        """Spins as int8 +-1, shape [n_sets, n_temps, n_real, N] (I8 / MSC1)."""
+        out = torch.empty(self.n_lat * self.N, dtype=torch.int8, device=self.device)
+        B.spin_unpack_i8(self.h, out)
+        return out.view(self.n_sets, self.n_temps, self.n_real, self.N)
+
+    def pack(self, spins_i8):
+        B.spin_pack_i8(self.h, spins_i8.contiguous().view(-1))
+
+    def sync(self):
+        B.spin_sync(self.h)
+
+    @property
+    def sweeps_done(self):
+        return B.spin_sweeps_done(self.h)
+
+    @property
+    def pt_steps_done(self):
+        return B.spin_pt_steps_done(self.h)
+
+    def set_counters(self, sweeps_done, pt_steps_done=0):
+        B.spin_set_counters(self.h, sweeps_done, pt_steps_done)
+
+    def set_variant(self, variant):
+        B.spin_set_variant(self.h, variant)
+
+    def close(self):
+        if self.h is not None:
+            B.spin_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, on the
+same seeded inputs.  Ising / EA lattices, energies, magnetisations, overlaps
+and exchange decisions are compared bit for bit; Heisenberg spins within the
+stated FP32 tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1101_1427_gb300 as sp  # noqa: E402
+from paper_1101_1427_gb300 import _binding as B  # noqa: E402
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------------ Philox
+@pytest.mark.parametrize("tag,colour,extra,lid,sweep", [
+    (0, 0, 0, 0, 0), (0, 1, 0, 0x01002003, 7), (1, 0, 5, 12, 0), (3, 0, 0, 0xFFFFFF, 2 ** 31 + 5),
+    (4, 1, (1 << 27) - 1, 99, 123456)])
+def test_rng_matches_oracle(tag, colour, extra, lid, sweep):
+    seed = 0x9E3779B97F4A7C15
+    count = 4099  # ragged tail
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    B.spin_rng_fill(seed, tag, colour, extra, lid, sweep, count, out)
+    got = host(out).view(np.uint32)
+    for idx in list(range(16)) + [1000, 1001, 4095, 4096, 4097, 4098]:
+        assert got[idx] == oracle.draw(seed, tag, colour, extra, lid, sweep, idx), idx
+
+
+# ------------------------------------------------------------------ Ising, int8
+def oracle_lattices_ising(dim, L, seed, n_real, n_temps, n_sets, ea=False):
+    out = np.zeros((n_sets, n_temps, n_real, L ** dim), np.int8)
+    for a in range(n_sets):
+        for t in range(n_temps):
+            for r in range(n_real):
+                lid = oracle.lattice_id(a, (r >> 5) if ea else r, t)
+                out[a, t, r] = oracle.ising_init(dim, L, seed, lid, bit=(r & 31) if ea else 0)
+    return out
+
+
+@pytest.mark.parametrize("dim,L,n_real,n_temps", [(2, 64, 1, 1), (2, 6, 2, 3), (3, 8, 1, 2), (3, 10, 3, 1)])
+def test_ising_init_matches_oracle(dim, L, n_real, n_temps):
+    lat = sp.Lattice(B.SPIN_ISING, dim, L, B.SPIN_I8, n_real=n_real, n_temps=n_temps, seed=77)
+    got = host(lat.spins).reshape(1, n_temps, n_real, -1)
+    assert np.array_equal(got, oracle_lattices_ising(dim, L, 77, n_real, n_temps, 1))
+
+
+def _ising_run_oracle(dim, L, seed, betas, n_real, n_sweeps, first=0):
+    n_temps = len(betas)
+    s = oracle_lattices_ising(dim, L, seed, n_real, n_temps, 1)
+    E = np.zeros((n_sweeps, n_temps, n_real), np.int64)
+    M = np.zeros((n_sweeps, n_temps, n_real), np.int64)
+    for t in range(n_temps):
+        for r in range(n_real):
+            e, m, _ = oracle.ising_run(dim, L, s[0, t, r], betas[t], seed,
+                                       oracle.lattice_id(0, r, t), first, n_sweeps)
+            E[:, t, r], M[:, t, r] = e, m
+    return s, E, M
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ising2d_L64_1000_sweeps_bit_exact(variant):
+    """2D Ising L=64, beta = 0.4407, 1000 sweeps, E and M after every sweep."""
+    L, seed, beta, n = 64, 1, 0.4407, 1000
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=seed)
+    lat.set_variant(variant)
+    out = lat.run([beta], n, measure_every=1)
+    s, E, M = _ising_run_oracle(2, L, seed, [beta], 1, n)
+    assert np.array_equal(host(out["E"]), E.ravel())
+    assert np.array_equal(host(out["M"]), M.ravel())
+    assert np.array_equal(host(lat.spins), s.ravel())
+    assert lat.sweeps_done == n
+
+
+@pytest.mark.parametrize("dim,L,betas,n_real,variant", [
+    (2, 6, [0.3, 0.44], 2, 0),        # generic kernel, L % 8 != 0
+    (2, 24, [0.5], 1, 0),             # 2D kernel, L % 16 != 0
+    (2, 48, [0.4, 0.45, 0.9], 2, 1),  # fused kernel, several lattices, ragged strips
+    (2, 32, [0.0, 5.0], 1, 1),        # infinite and (near) zero temperature
+    (3, 8, [0.22, 0.3], 1, 0),
+    (3, 12, [0.25], 2, 0)])
+def test_ising_sweeps_bit_exact(dim, L, betas, n_real, variant):
+    seed, n = 5, 13
+    lat = sp.Lattice(B.SPIN_ISING, dim, L, B.SPIN_I8, n_real=n_real, n_temps=len(betas), seed=seed)
+    if variant:
+        lat.set_variant(1)
+    lat.sweep(betas, 5)
+    lat.sweep(betas, 8)  # continues the chain
+    s, E, M = _ising_run_oracle(dim, L, seed, betas, n_real, n)
+    assert np.array_equal(host(lat.spins), s.ravel())
+    Eg, Mg, _ = lat.measure()
+    assert np.array_equal(host(Eg), E[-1].ravel()) and np.array_equal(host(Mg), M[-1].ravel())
+
+
+def test_fused_equals_phases_on_large_lattice():
+    L, seed = 4096, 3
+    a = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=seed)
+    b = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=seed)
+    a.set_variant(0)
+    b.set_variant(1)
+    a.sweep([0.4407], 3)
+    b.sweep([0.4407], 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a.spins, b.spins)
+
+
+# ------------------------------------------------------------------ EA
+def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None):
+    n_temps = len(betas)
+    reals = range(n_real) if reals is None else reals
+    res = {}
+    for r in reals:
+        J = oracle.ea_couplings(3, L, r, seed)
+        sp_ = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t),
+                                                    bit=r & 31) for t in range(n_temps)])
+                        for a in range(n_sets)]).copy()
+        E, Q, acc, _ = oracle.pt_run(3, L, sp_, betas, seed, r, r >> 5, 0, n_sweeps, pt_every, J=J)
+        res[r] = (J, sp_, E, Q, acc)
+    return res
+
+
+@pytest.mark.parametrize("layout", [B.SPIN_I8, B.SPIN_MSC1])
+def test_ea_couplings_and_init_match_oracle(layout):
+    L, seed, n_real = 6, 11, 64
+    lat = sp.Lattice(B.SPIN_EA, 3, L, layout, n_real=n_real, n_temps=2, n_sets=2, seed=seed)
+    got = host(lat.unpack())
+    exp = oracle_lattices_ising(3, L, seed, n_real, 2, 2, ea=True)
+    assert np.array_equal(got, exp)
+    if layout == B.SPIN_I8:
+        Jg = host(lat.couplings).reshape(n_real, -1)
+        for r in (0, 1, 31, 32, 63):
+            assert np.array_equal(Jg[r], oracle.ea_couplings(3, L, r, seed))
+    else:
+        Jw = host(lat.couplings).view(np.uint32).reshape(n_real // 32, 3 * L ** 3)
+        for r in (0, 5, 31, 32, 63):
+            bits = ((Jw[r >> 5] >> np.uint32(r & 31)) & 1).astype(np.int8)
+            assert np.array_equal(1 - 2 * bits, oracle.ea_couplings(3, L, r, seed))
+
+
+@pytest.mark.parametrize("layout,L", [(B.SPIN_I8, 6), (B.SPIN_MSC1, 6), (B.SPIN_MSC1, 8)])
+def test_ea_sweeps_measure_bit_exact(layout, L):
+    seed, n_real, betas, n = 13, 64, [0.9, 1.3, 2.0], 6
+    lat = sp.Lattice(B.SPIN_EA, 3, L, layout, n_real=n_real, n_temps=3, n_sets=2, seed=seed)
+    lat.sweep(betas, n)
+    E, M, Q = lat.measure()
+    got = host(lat.unpack())
+    E, M, Q = host(E).reshape(2, 3, n_real), host(M).reshape(2, 3, n_real), host(Q).reshape(3, n_real)
+    ref = _ea_oracle(L, seed, betas, n_real, 2, n, reals=[0, 1, 30, 31, 32, 47, 63])
+    for r, (J, s, Es, Qs, _) in ref.items():
+        assert np.array_equal(got[:, :, r], s), r
+        assert np.array_equal(E[:, :, r], Es[-1]), r
+        assert np.array_equal(Q[:, r], Qs[-1]), r
+        for a in range(2):
+            for t in range(3):
+                assert M[a, t, r] == s[a, t].sum()
+
+
+@pytest.mark.parametrize("layout", [B.SPIN_I8, B.SPIN_MSC1])
+def test_ea_parallel_tempering_bit_exact(layout):
+    L, seed, n_real, n = 4, 21, 32, 40
+    betas = list(1.0 / np.geomspace(0.9, 2.0, 5))
+    lat = sp.Lattice(B.SPIN_EA, 3, L, layout, n_real=n_real, n_temps=5, n_sets=2, seed=seed)
+    acc = torch.zeros(2 * 5, dtype=torch.int64, device="cuda")
+    out = lat.run(betas, n, measure_every=1, pt_every=1, accepted=acc)
+    got = host(lat.unpack())
+    Eser = host(out["E"]).reshape(n, 2, 5, n_real)
+    Qser = host(out["Q"]).reshape(n, 5, n_real)
+    ref = _ea_oracle(L, seed, betas, n_real, 2, n, pt_every=1)
+    acc_ref = np.zeros((2, 5), np.int64)
+    for r, (J, s, Es, Qs, ac) in ref.items():
+        assert np.array_equal(got[:, :, r], s), r
+        assert np.array_equal(Eser[:, :, :, r], Es), r
+        assert np.array_equal(Qser[:, :, r], Qs), r
+        acc_ref += ac
+    assert np.array_equal(host(acc).reshape(2, 5), acc_ref)
+    assert acc_ref.sum() > 0
+    assert lat.pt_steps_done == n
+
+
+def test_msc_equals_int8_ea():
+    L, seed, n_real, betas = 8, 4, 64, [1.0, 1.5]
+    a = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_I8, n_real=n_real, n_temps=2, n_sets=2, seed=seed)
+    b = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=2, n_sets=2, seed=seed)
+    for lat in (a, b):
+        lat.run(betas, 25, pt_every=1)
+    assert torch.equal(a.unpack(), b.unpack())
+
+
+# ------------------------------------------------------------------ 2D coded ferromagnet
+@pytest.mark.parametrize("L,betas", [(256, [0.4407]), (512, [0.4, 0.5])])
+def test_msc2d_bit_exact(L, betas):
+    seed, n = 9, 7
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, n_temps=len(betas), seed=seed)
+    assert np.array_equal(host(lat.unpack()).reshape(len(betas), -1),
+                          oracle_lattices_ising(2, L, seed, 1, len(betas), 1).reshape(len(betas), -1))
+    lat.sweep(betas, n)
+    s, E, M = _ising_run_oracle(2, L, seed, betas, 1, n)
+    assert np.array_equal(host(lat.unpack()).ravel(), s.ravel())
+    Eg, Mg, _ = lat.measure()
+    assert np.array_equal(host(Eg), E[-1].ravel()) and np.array_equal(host(Mg), M[-1].ravel())
+
+
+def test_msc2d_pack_roundtrip():
+    L = 256
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, seed=2)
+    x = torch.where(torch.rand(L * L, device="cuda") < 0.5, -1, 1).to(torch.int8)
+    lat.pack(x)
+    assert torch.equal(lat.unpack().view(-1), x)
+
+
+# ------------------------------------------------------------------ Heisenberg
+def test_heis_init_close_to_oracle():
+    L = 8
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=3)
+    got = host(lat.spins).reshape(-1, 4)
+    ref = oracle.heis_init(3, L, 3, oracle.lattice_id(0, 0, 0))
+    assert np.max(np.abs(got[:, :3] - ref)) < 1e-6 and np.all(got[:, 3] == 0)
+
+
+def test_heis_one_sweep_within_tolerance():
+    """Same FP32 start for both; after one sweep every site agrees to 1e-5,
+    except sites whose accept/reject margin |u3 - exp(-beta dE)| is below 1e-5
+    in the FP64 oracle and the later-updated neighbours of such sites."""
+    L, seed, beta = 16, 8, 0.693
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=seed)
+    s0 = oracle.heis_init(3, L, seed, 0).astype(np.float32)
+    dev = np.zeros((L ** 3, 4), np.float32)
+    dev[:, :3] = s0
+    lat.spins.copy_(torch.from_numpy(dev.ravel()))
+    lat.sweep([beta], 1)
+    got = host(lat.spins).reshape(-1, 4)[:, :3]
+    ref = s0.astype(np.float64)
+    margin = oracle.heis_sweep(3, L, ref, beta, seed, 0, 0, want_margin=True)
+    err = np.max(np.abs(got - ref), axis=1)
+    flagged = margin < 1e-5
+    idx = np.arange(L ** 3)
+    x, y, z = idx % L, (idx // L) % L, idx // (L * L)
+    near = flagged.copy()
+    for d in (1, -1):
+        for sh in ((x + d) % L + L * y + L * L * z, x + L * ((y + d) % L) + L * L * z,
+                   x + L * y + L * L * ((z + d) % L)):
+            near |= flagged[sh]
+    bad = (err > 1e-5) & ~near
+    assert not bad.any(), (np.nonzero(bad)[0][:10], err[bad][:10])
+    assert (err > 1e-5).sum() <= 20
+
+
+def test_heis_renormalisation_bound():
+    L = 16
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=4)
+    lat.sweep([0.693], 100)
+    v = host(lat.spins).reshape(-1, 4)[:, :3].astype(np.float64)
+    assert np.max(np.abs(np.linalg.norm(v, axis=1) - 1)) <= 1e-6
+
+
+def test_heis_measure_matches_oracle_on_oracle_state():
+    L = 12
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, n_temps=2, seed=5)
+    states = [oracle.heis_init(3, L, 5 + k, 0).astype(np.float32).astype(np.float64) for k in range(2)]
+    dev = np.zeros((2, L ** 3, 4), np.float32)
+    for k in range(2):
+        dev[k, :, :3] = states[k]
+    lat.spins.copy_(torch.from_numpy(dev.ravel()))
+    Ef, Mf = lat.measure()
+    Ef, Mf = host(Ef), host(Mf)
+    for k in range(2):
+        assert abs(Ef[k] - oracle.heis_energy(3, L, states[k])) < 1e-9 * L ** 3
+        assert np.allclose(Mf[k], oracle.heis_magnetisation(3, L, states[k]), atol=1e-9 * L ** 3)
+
+
+def test_ising_measure_on_oracle_state():
+    L = 20
+    lat = sp.Lattice(B.SPIN_ISING, 3, L, B.SPIN_I8, seed=5)
+    s = oracle.ising_init(3, L, 99, 0)
+    lat.spins.copy_(torch.from_numpy(s))
+    E, M, _ = lat.measure()
+    assert host(E)[0] == oracle.ising_energy(3, L, s) and host(M)[0] == s.sum()
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(B.SpinError):
+        sp.Lattice(B.SPIN_ISING, 2, 63, B.SPIN_I8)
+    with pytest.raises(B.SpinError):
+        sp.Lattice(B.SPIN_EA, 3, 8, B.SPIN_MSC1, n_real=20)
+    lat = sp.Lattice(B.SPIN_ISING, 2, 16, B.SPIN_I8, seed=1)
+    with pytest.raises(B.SpinError):
+        lat.sweep([float("nan")])
+    with pytest.raises(B.SpinError):
+        B.spin_sweep(lat.h, None, [0.4], 1, 2)  # wrong seed
+    with pytest.raises(B.SpinError):
+        lat.sweep([-0.1])
+    lat.sync()

@@ -99,7 +99,13 @@ int validate_desc(const spin_desc *d) {
   // per-lattice launches put the lattice index in grid.y (at most 65535)
   const int64_t n_lat = (int64_t)d->n_sets * d->n_temps * d->n_real;
   if (d->layout != SPIN_MSC1 && n_lat > 65535) return SPIN_EINVAL;
-  if (d->layout == SPIN_MSC1 && d->model == SPIN_ISING && n_lat > 65535) return SPIN_EINVAL;
+  // per-site kernels index sites (and 16-byte float4 words) with 32-bit integers
+  int64_t N = 1;
+  for (int k = 0; k < d->dim; ++k) N *= d->L;
+  if (n_lat * N * (d->layout == SPIN_F32X4 ? 4 : 1) >= ((int64_t)1 << 32)) return SPIN_EINVAL;
+  if (d->layout == SPIN_MSC1 && d->model == SPIN_ISING &&
+      (n_lat > 65535 || n_lat * d->L * (d->L / 256) >= ((int64_t)1 << 31)))
+    return SPIN_EINVAL;
   if (d->layout == SPIN_MSC1 && d->model == SPIN_EA &&
       (int64_t)d->n_sets * (d->n_real / 32) * d->n_temps > 65535)
     return SPIN_EINVAL;
@@ -174,6 +180,11 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   h->g.n_temps = desc->n_temps;
   h->g.n_sets = desc->n_sets;
   h->g.ea = desc->model == SPIN_EA;
+  h->g.fL = make_fastdiv((uint32_t)desc->L);
+  h->g.fhalf = make_fastdiv((uint32_t)(h->g.N / 2));
+  h->g.fquads = make_fastdiv((uint32_t)((h->g.N / 2 + 3) / 4));
+  h->g.freal = make_fastdiv((uint32_t)desc->n_real);
+  h->g.ftemps = make_fastdiv((uint32_t)desc->n_temps);
   h->n_lat = (int64_t)desc->n_sets * desc->n_temps * desc->n_real;
   h->variant = (desc->model == SPIN_ISING && desc->dim == 2 && desc->layout == SPIN_I8 &&
                 fused2d_supported(desc->L))

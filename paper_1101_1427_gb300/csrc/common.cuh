@@ -38,11 +38,19 @@ inline RoundKeys make_round_keys(uint64_t seed) {
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplications whose halves are mixed with the other two counter words
 // and the round key.
+__device__ __forceinline__ uint64_t mul_wide(uint32_t a, uint32_t b) {
+  uint64_t p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  return p;
+}
+
 __device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys &rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint64_t p0 = mul_wide(0xD2511F53u, c.x);
+    const uint64_t p1 = mul_wide(0xCD9E8D57u, c.z);
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
   }
   return c;
@@ -65,6 +73,30 @@ __device__ __forceinline__ float uniform24(uint32_t x) {
   return __uint2float_rn(x >> 8) * 5.9604644775390625e-8f;
 }
 
+// Unsigned 32-bit division by a run-time invariant divisor with one
+// multiply-high (Granlund & Montgomery, PLDI 1994, round-up method):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, n).
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // Geometry of one lattice of a handle.
 struct Geom {
   int dim;
@@ -74,7 +106,49 @@ struct Geom {
   int n_temps;
   int n_sets;
   int ea;          // realisation key is r >> 5
+  FastDiv fL;      // division by L
+  FastDiv fhalf;   // division by N / 2
+  FastDiv fquads;  // division by (N / 2 + 3) / 4
+  FastDiv freal;   // division by n_real
+  FastDiv ftemps;  // division by n_temps
 };
+
+// Site of colour index j (colour c): i = 2j + parity, with its coordinates.
+struct Site {
+  uint32_t i, x, y, z, rowbase;
+};
+
+__device__ __forceinline__ Site site_of(const Geom &g, uint32_t j, int colour) {
+  Site s;
+  const uint32_t i0 = 2u * j;
+  const uint32_t row = fdiv(i0, g.fL);  // y + L z
+  const uint32_t x0 = i0 - row * (uint32_t)g.L;
+  if (g.dim == 3) {
+    s.z = fdiv(row, g.fL);
+    s.y = row - s.z * (uint32_t)g.L;
+  } else {
+    s.z = 0;
+    s.y = row;
+  }
+  s.x = x0 + ((colour + s.y + s.z) & 1u);
+  s.rowbase = i0 - x0;
+  s.i = s.rowbase + s.x;
+  return s;
+}
+
+// 32-bit versions for per-site kernels (lattice index < 2^32)
+__device__ __forceinline__ uint32_t slot_of32(const Geom &g, uint32_t lat) {
+  const uint32_t q = fdiv(lat, g.freal);
+  return q - fdiv(q, g.ftemps) * (uint32_t)g.n_temps;
+}
+
+__device__ __forceinline__ uint32_t lattice_id32(const Geom &g, uint32_t lat) {
+  const uint32_t q = fdiv(lat, g.freal);
+  const uint32_t r = lat - q * (uint32_t)g.n_real;
+  const uint32_t a = fdiv(q, g.ftemps);
+  const uint32_t t = q - a * (uint32_t)g.n_temps;
+  return lattice_id(a, g.ea ? (r >> 5) : r, t);
+}
 
 __host__ __device__ __forceinline__ uint32_t lattice_id_of(const Geom &g, int64_t lat) {
   const uint32_t r = (uint32_t)(lat % g.n_real);

@@ -38,42 +38,32 @@ __global__ void heis_cold_kernel(float4 *__restrict__ s, int64_t total) {
 // accept iff dE <= 0 or u3 < exp(-beta dE).  beta (float) is read from
 // word 0 of the slot's row of the threshold table.
 __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s, Geom g,
-                                                         int64_t n_lat,
+                                                         uint32_t total,
                                                          const uint32_t *__restrict__ thr,
                                                          RoundKeys rk, uint32_t sweep,
                                                          int colour) {
-  const int L = g.L;
-  const int64_t half = g.N / 2;
-  const int64_t total = n_lat * half;
-  const int64_t LL = (int64_t)L * L;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lat = k / half, j = k - lat * half;
-    float4 *sl = s + lat * g.N;
-    const int64_t i0 = 2 * j;
-    const int x0 = (int)(i0 % L);
-    const int y = (int)((i0 / L) % L);
-    const int z = (int)(i0 / LL);
-    const int x = x0 + ((colour + y + z) & 1);
-    const int64_t rowbase = i0 - x0;
-    const int64_t i = rowbase + x;
-    const int64_t ixp = rowbase + (x == L - 1 ? 0 : x + 1);
-    const int64_t ixm = rowbase + (x == 0 ? L - 1 : x - 1);
-    const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * L : i + L;
-    const int64_t iym = y == 0 ? i + (int64_t)(L - 1) * L : i - L;
-    const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
-    const int64_t izm = z == 0 ? i + (int64_t)(L - 1) * LL : i - LL;
+  const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N, half = N / 2;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const uint32_t lat = fdiv(k, g.fhalf), j = k - lat * half;
+    float4 *sl = s + (size_t)lat * N;
+    const Site st = site_of(g, j, colour);
+    const uint32_t i = st.i;
+    const uint32_t ixp = st.rowbase + (st.x == L - 1 ? 0 : st.x + 1);
+    const uint32_t ixm = st.rowbase + (st.x == 0 ? L - 1 : st.x - 1);
+    const uint32_t iyp = st.y == L - 1 ? i - (L - 1) * L : i + L;
+    const uint32_t iym = st.y == 0 ? i + (L - 1) * L : i - L;
+    const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
+    const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
     const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym], e = sl[izp], f = sl[izm];
     const float hx = a.x + b.x + c.x + d.x + e.x + f.x;
     const float hy = a.y + b.y + c.y + d.y + e.y + f.y;
     const float hz = a.z + b.z + c.z + d.z + e.z + f.z;
     const float4 si = sl[i];
-    const uint4 w = philox(make_uint4((uint32_t)j, sweep, lattice_id_of(g, lat),
-                                      ctr_w(TAG_HEIS, (uint32_t)colour, 0)), rk);
+    const uint4 w = philox(make_uint4(j, sweep, lattice_id32(g, lat), ctr_w(TAG_HEIS, (uint32_t)colour, 0)), rk);
     const float4 n = unit_vector(w.x, w.y);
     const float u3 = uniform24(w.z);
     const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
-    const float beta = __uint_as_float(__ldg(thr + 4 * slot_of(g, lat)));
+    const float beta = __uint_as_float(__ldg(thr + 4 * slot_of32(g, lat)));
     if (dE <= 0.0f || u3 < expf(-beta * dE)) sl[i] = n;
   }
 }
@@ -110,13 +100,12 @@ cudaError_t launch_init_heis(spin_lattice *h) {
 
 cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
   const RoundKeys rk = make_round_keys(h->d.seed);
-  const int64_t half = h->n_lat * (h->g.N / 2);
+  const uint32_t half = (uint32_t)(h->n_lat * (h->g.N / 2));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour)
-      heis_phase_kernel<<<capped_grid(half), 256, 0, h->stream>>>((float4 *)h->spins, h->g,
-                                                                  h->n_lat, h->d_thr, rk, sweep,
-                                                                  colour);
+      heis_phase_kernel<<<capped_grid(half), 256, 0, h->stream>>>((float4 *)h->spins, h->g, half,
+                                                                  h->d_thr, rk, sweep, colour);
     if ((sweep + 1u) % 100u == 0u)
       heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>(
           (float4 *)h->spins, h->n_lat * h->g.N);

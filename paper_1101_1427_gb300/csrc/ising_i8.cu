@@ -81,15 +81,16 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
   const uint32_t j4 = (uint32_t)y * (uint32_t)chunks + (uint32_t)m;
   const uint4 r = philox(make_uint4(j4, sweep, lattice_id_of(g, lat), ctr_w(TAG_UPDATE, colour, 0)), rk);
   const int p = (colour + y) & 1;
-  uint64_t F = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int b = p + 2 * q;
-    const uint32_t n2 = (uint32_t)(A >> (8 * b)) & 0xffu;
-    const uint32_t rq = word_of(r, q);
-    const bool flip = (n2 >= 4u) | ((n2 == 2u) & (rq < thr4)) | ((n2 == 0u) & (rq < thr8));
-    F |= flip ? (0xFEull << (8 * b)) : 0ull;
-  }
+  // active bytes to the even positions; n >= 2 flips outright, else r < thr(dE)
+  const uint64_t An = A >> (8 * p);
+  const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
+  const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
+  const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
+  const uint32_t t0 = (lo & 0x2u) ? thr4 : thr8, t1 = (lo & 0x20000u) ? thr4 : thr8;
+  const uint32_t t2 = (hi & 0x2u) ? thr4 : thr8, t3 = (hi & 0x20000u) ? thr4 : thr8;
+  const uint32_t f_lo = g_lo | (uint32_t)(r.x < t0) | ((uint32_t)(r.y < t1) << 16);
+  const uint32_t f_hi = g_hi | (uint32_t)(r.z < t2) | ((uint32_t)(r.w < t3) << 16);
+  const uint64_t F = (((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu)) << (8 * p);
   reinterpret_cast<uint64_t *>(base + (int64_t)y * L)[m] = C ^ F;
 }
 
@@ -100,54 +101,44 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
 __global__ void __launch_bounds__(256) phase_generic_kernel(int8_t *__restrict__ spins,
                                                             const int8_t *__restrict__ J,
                                                             const uint32_t *__restrict__ thr,
-                                                            Geom g, int64_t n_lat, RoundKeys rk,
+                                                            Geom g, uint32_t total, RoundKeys rk,
                                                             uint32_t sweep, int colour) {
-  const int L = g.L;
-  const int64_t half = g.N / 2;
-  const int64_t quads = (half + 3) / 4;
-  const int64_t total = n_lat * quads;
-  const int64_t LL = (int64_t)L * L;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lat = k / quads, j4 = k - lat * quads;
-    int8_t *s = spins + lat * g.N;
-    const int8_t *Jr = J ? J + (lat % g.n_real) * (int64_t)g.dim * g.N : nullptr;
-    const int t = slot_of(g, lat);
-    const uint4 r = philox(make_uint4((uint32_t)j4, sweep, lattice_id_of(g, lat),
-                                      ctr_w(TAG_UPDATE, colour, 0)), rk);
+  const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N, half = N / 2;
+  const uint32_t quads = (half + 3) / 4;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const uint32_t lat = fdiv(k, g.fquads), j4 = k - lat * quads;
+    int8_t *s = spins + (size_t)lat * N;
+    const int8_t *Jr = J ? J + (size_t)(lat - fdiv(lat, g.freal) * (uint32_t)g.n_real) * g.dim * N : nullptr;
+    const uint32_t t = slot_of32(g, lat);
+    const uint4 r = philox(make_uint4(j4, sweep, lattice_id32(g, lat), ctr_w(TAG_UPDATE, colour, 0)), rk);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t j = 4 * j4 + q;
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t j = 4 * j4 + q;
       if (j >= half) break;
-      const int64_t i0 = 2 * j;
-      const int x0 = (int)(i0 % L);
-      const int y = (int)((i0 / L) % L);
-      const int z = g.dim == 3 ? (int)(i0 / LL) : 0;
-      const int x = x0 + ((colour + y + z) & 1);
-      const int64_t rowbase = i0 - x0;
-      const int64_t i = rowbase + x;
-      const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
-      const int64_t ystride = L;
-      const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * ystride : i + ystride;
-      const int64_t iym = y == 0 ? i + (int64_t)(L - 1) * ystride : i - ystride;
+      const Site st = site_of(g, j, colour);
+      const uint32_t i = st.i;
+      const uint32_t ixp = st.rowbase + (st.x == L - 1 ? 0 : st.x + 1);
+      const uint32_t ixm = st.rowbase + (st.x == 0 ? L - 1 : st.x - 1);
+      const uint32_t iyp = st.y == L - 1 ? i - (L - 1) * L : i + L;
+      const uint32_t iym = st.y == 0 ? i + (L - 1) * L : i - L;
       int h;
-      const int8_t sxp = s[rowbase + xp], sxm = s[rowbase + xm], syp = s[iyp], sym = s[iym];
+      const int8_t sxp = s[ixp], sxm = s[ixm], syp = s[iyp], sym = s[iym];
       if (Jr) {
-        h = Jr[i] * sxp + Jr[rowbase + xm] * sxm + Jr[g.N + i] * syp + Jr[g.N + iym] * sym;
+        h = Jr[i] * sxp + Jr[ixm] * sxm + Jr[N + i] * syp + Jr[N + iym] * sym;
       } else {
         h = sxp + sxm + syp + sym;
       }
       if (g.dim == 3) {
-        const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
-        const int64_t izm = z == 0 ? i + (int64_t)(L - 1) * LL : i - LL;
+        const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
+        const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
         if (Jr)
-          h += Jr[2 * g.N + i] * s[izp] + Jr[2 * g.N + izm] * s[izm];
+          h += Jr[2 * N + i] * s[izp] + Jr[2 * N + izm] * s[izm];
         else
           h += s[izp] + s[izm];
       }
       const int si = s[i];
       const int dE = 2 * si * h;
-      const uint32_t rq = word_of(r, (uint32_t)q);
+      const uint32_t rq = word_of(r, q);
       const bool flip = dE <= 0 || rq < __ldg(thr + 4 * t + (dE >> 2));
       if (flip) s[i] = (int8_t)(-si);
     }
@@ -193,11 +184,11 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
         ising2d_phase_kernel<<<grid, block, 0, h->stream>>>((int8_t *)h->spins, g.L, h->d_thr, g,
                                                              rk, sweep, colour);
       } else {
-        const int64_t total = h->n_lat * ((g.N / 2 + 3) / 4);
+        const uint32_t total = (uint32_t)(h->n_lat * ((g.N / 2 + 3) / 4));
         unsigned grid = grid_for(total, 256);
         if (grid > 1u << 20) grid = 1u << 20;
         phase_generic_kernel<<<grid, 256, 0, h->stream>>>((int8_t *)h->spins, J, h->d_thr, g,
-                                                           h->n_lat, rk, sweep, colour);
+                                                           total, rk, sweep, colour);
       }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;

@@ -46,6 +46,46 @@ __global__ void measure_i8_kernel(const int8_t *__restrict__ s, const int8_t *__
   }
 }
 
+// 2D ferromagnet, L % 16 == 0: one thread per 16-byte row segment.  For +-1
+// bytes bit 1 is set iff s = -1, so antiparallel bonds to the right and
+// downward neighbours are popcounts of (a ^ b) & 0x02..; E = 2 n_anti - 2N,
+// M = N - 2 n_down.
+__global__ void measure2d_i8_kernel(const int8_t *__restrict__ s, int L, long long *__restrict__ E,
+                                    long long *__restrict__ M) {
+  const int64_t lat = blockIdx.y;
+  const int8_t *sl = s + lat * (int64_t)L * L;
+  const uint32_t segs = (uint32_t)(L >> 4);
+  const uint32_t total = segs * (uint32_t)L;
+  const uint64_t B1 = 0x0202020202020202ull;
+  long long anti = 0, down = 0;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const uint32_t y = k / segs, sg = k - y * segs;
+    const int8_t *row = sl + (int64_t)y * L;
+    const int8_t *nrow = sl + (int64_t)(y == (uint32_t)L - 1 ? 0 : y + 1) * L;
+    const uint4 c = *reinterpret_cast<const uint4 *>(row + 16 * sg);
+    const uint4 d = *reinterpret_cast<const uint4 *>(nrow + 16 * sg);
+    const uint64_t c0 = (uint64_t)c.x | ((uint64_t)c.y << 32), c1 = (uint64_t)c.z | ((uint64_t)c.w << 32);
+    const uint64_t d0 = (uint64_t)d.x | ((uint64_t)d.y << 32), d1 = (uint64_t)d.z | ((uint64_t)d.w << 32);
+    const uint64_t nb = (uint8_t)row[sg == segs - 1 ? 0 : 16 * sg + 16];
+    const uint64_t r0 = (c0 >> 8) | (c1 << 56), r1 = (c1 >> 8) | (nb << 56);
+    anti += __popcll((c0 ^ r0) & B1) + __popcll((c1 ^ r1) & B1) + __popcll((c0 ^ d0) & B1) +
+            __popcll((c1 ^ d1) & B1);
+    down += __popcll(c0 & B1) + __popcll(c1 & B1);
+  }
+  anti = warp_sum(anti);
+  down = warp_sum(down);
+  if ((threadIdx.x & 31) == 0) {
+    if (E) add_ll(&E[lat], 2 * anti);
+    if (M) add_ll(&M[lat], -2 * down);
+  }
+}
+
+__global__ void add_per_lattice_kernel(long long *__restrict__ v, int64_t n, long long c) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[k] += c;
+}
+
 // q_{t,r} = sum_i s_i^(0) s_i^(1) between sets 0 and 1.
 __global__ void overlap_i8_kernel(const int8_t *__restrict__ s, Geom g, long long *__restrict__ Q) {
   const int64_t tr = blockIdx.y;  // t * n_real + r
@@ -60,15 +100,55 @@ __global__ void overlap_i8_kernel(const int8_t *__restrict__ s, Geom g, long lon
 }
 
 // ---------------------------------------------------------------- EA, coded words
-// Per word-lattice (a, g, t): counts per bit of unsatisfied bonds, down
-// spins and (set 0 only) spins differing from set 1.  Lane b of every warp
-// accumulates the count of bit b through 32 ballots per word.
-__device__ __forceinline__ void count_bits(uint32_t v, long long &acc, int lane) {
+// Per word-lattice (a, g, t) and realisation bit b: the number of
+// unsatisfied bonds, of down spins and (set 0 only) of spins that differ
+// from set 1.  Each thread adds its words into bit-sliced vertical counters
+// (plane k holds bit k of 32 per-realisation counts); the counters of a warp
+// are added with shuffles, those of the warps through shared memory, and
+// lane b of warp 0 finally reads count b out of the planes.
+constexpr int kThr = 6;   // per-thread planes: at most 16 sites x 3 bonds = 48 < 64
+constexpr int kWarp = 11; // per-warp planes: at most 32 x 48 = 1536 < 2048
+
+// counter += one bit-plane of weight 2^w
+template <int K>
+__device__ __forceinline__ void vc_add(uint32_t (&C)[K], uint32_t v, int w) {
 #pragma unroll
-  for (int b = 0; b < 32; ++b) {
-    const int c = __popc(__ballot_sync(0xffffffffu, (v >> b) & 1u));
-    if (lane == b) acc += c;
+  for (int k = 0; k < K; ++k) {
+    if (k < w) continue;
+    const uint32_t c = C[k] & v;
+    C[k] ^= v;
+    v = c;
   }
+}
+
+// Sums the per-thread counters of the block; lane b of warp 0 gets count b.
+__device__ long long vc_block_total(const uint32_t (&c)[kThr], uint32_t (*sm)[kWarp]) {
+  uint32_t C[kWarp];
+#pragma unroll
+  for (int k = 0; k < kWarp; ++k) C[k] = k < kThr ? c[k] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {  // bit-sliced ripple-carry adds across the warp
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < kWarp; ++k) {
+      const uint32_t a = C[k], b = __shfl_xor_sync(0xffffffffu, C[k], o);
+      C[k] = a ^ b ^ carry;
+      carry = (a & b) | (carry & (a ^ b));
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < kWarp; ++k) sm[wid][k] = C[k];
+  __syncthreads();
+  long long tot = 0;
+  if (wid == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int k = 0; k < kWarp; ++k) tot += (long long)((sm[w][k] >> lane) & 1u) << k;
+  }
+  __syncthreads();
+  return tot;
 }
 
 __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__restrict__ w,
@@ -76,50 +156,43 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
                                                           long long *__restrict__ E,
                                                           long long *__restrict__ M,
                                                           long long *__restrict__ Q) {
-  const int G = g.n_real / 32;
-  const int64_t wl = blockIdx.y;
-  const int t = (int)(wl % g.n_temps);
-  const int grp = (int)((wl / g.n_temps) % G);
-  const int a = (int)(wl / ((int64_t)g.n_temps * G));
-  const uint32_t *s = w + wl * g.N;
-  const uint32_t *Jg = J + (int64_t)grp * 3 * g.N;
+  __shared__ uint32_t sm[8][kWarp];
+  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
+  const uint32_t wl = blockIdx.y;
+  const uint32_t t = wl % T, grp = (wl / T) % G, a = wl / (T * G);
+  const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N;
+  const uint32_t *s = w + (size_t)wl * N;
+  const uint32_t *Jg = J + (size_t)grp * 3 * N;
   const bool do_q = Q && a == 0 && g.n_sets >= 2;
-  const uint32_t *s1 = s + (int64_t)G * g.n_temps * g.N;  // set 1, same (g, t)
-  const int L = g.L;
-  const int64_t LL = (int64_t)L * L;
-  const int lane = threadIdx.x & 31;
-  long long unsat = 0, down = 0, diff = 0;
-  // every lane of a warp iterates the same number of times (ballots)
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t warp_start = start - lane;
-  for (int64_t base = warp_start; base < g.N; base += stride) {
-    const int64_t i = base + lane;
-    uint32_t U = 0, D = 0, X = 0;
-    uint32_t U2 = 0, U3 = 0;
-    if (i < g.N) {
-      const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / LL);
-      const uint32_t S = s[i];
-      const int64_t ixp = i - x + (x == L - 1 ? 0 : x + 1);
-      const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * L : i + L;
-      const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
-      U = S ^ s[ixp] ^ Jg[i];
-      U2 = S ^ s[iyp] ^ Jg[g.N + i];
-      U3 = S ^ s[izp] ^ Jg[2 * g.N + i];
-      D = S;
-      if (do_q) X = S ^ s1[i];
-    }
-    count_bits(U, unsat, lane);
-    count_bits(U2, unsat, lane);
-    count_bits(U3, unsat, lane);
-    if (M) count_bits(D, down, lane);
-    if (do_q) count_bits(X, diff, lane);
+  const uint32_t *s1 = s + (size_t)G * T * N;  // set 1, same (g, t)
+  uint32_t CE[kThr] = {}, CM[kThr] = {}, CQ[kThr] = {};
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const uint32_t row = fdiv(i, g.fL), x = i - row * L;
+    const uint32_t z = fdiv(row, g.fL), y = row - z * L;
+    const uint32_t S = s[i];
+    const uint32_t ixp = i - x + (x == L - 1 ? 0 : x + 1);
+    const uint32_t iyp = y == L - 1 ? i - (L - 1) * L : i + L;
+    const uint32_t izp = z == L - 1 ? i - (L - 1) * LL : i + LL;
+    const uint32_t u0 = S ^ s[ixp] ^ Jg[i];
+    const uint32_t u1 = S ^ s[iyp] ^ Jg[N + i];
+    const uint32_t u2 = S ^ s[izp] ^ Jg[2 * N + i];
+    vc_add(CE, u0 ^ u1 ^ u2, 0);
+    vc_add(CE, (u0 & u1) | (u2 & (u0 ^ u1)), 1);
+    if (M) vc_add(CM, S, 0);
+    if (do_q) vc_add(CQ, S ^ s1[i], 0);
   }
-  // lane b holds this warp's counts for realisation 32 grp + b
-  const int64_t lat = ((int64_t)a * g.n_temps + t) * g.n_real + 32 * grp + lane;
-  if (E) add_ll(&E[lat], 2 * unsat);
-  if (M) add_ll(&M[lat], -2 * down);
-  if (do_q) add_ll(&Q[(int64_t)t * g.n_real + 32 * grp + lane], -2 * diff);
+  const uint32_t lane = threadIdx.x & 31;
+  const int64_t lat = ((int64_t)a * T + t) * g.n_real + 32 * grp + lane;
+  const long long unsat = vc_block_total(CE, sm);
+  if (threadIdx.x < 32 && E) add_ll(&E[lat], 2 * unsat);
+  if (M) {
+    const long long down = vc_block_total(CM, sm);
+    if (threadIdx.x < 32) add_ll(&M[lat], -2 * down);
+  }
+  if (do_q) {
+    const long long diff = vc_block_total(CQ, sm);
+    if (threadIdx.x < 32) add_ll(&Q[(int64_t)t * g.n_real + 32 * grp + lane], -2 * diff);
+  }
 }
 
 // constant parts: E = 2 unsat - 3N, M = N - 2 down, Q = N - 2 diff
@@ -294,7 +367,13 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
   if (M) cudaMemsetAsync(M, 0, sizeof(int64_t) * nl, st);
   if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
   if (h->d.layout == SPIN_I8) {
-    if (E || M)
+    if ((E || M) && !J && g.dim == 2 && g.L % 16 == 0) {
+      const int64_t segs = (int64_t)g.L * (g.L / 16);
+      measure2d_i8_kernel<<<dim3(capped(segs, 2048), (unsigned)nl), 256, 0, st>>>(
+          (const int8_t *)h->spins, g.L, (long long *)E, (long long *)M);
+      if (E) add_per_lattice_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)E, nl, -2 * (long long)g.N);
+      if (M) add_per_lattice_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)M, nl, (long long)g.N);
+    } else if (E || M)
       measure_i8_kernel<<<dim3(capped(g.N, 1024), (unsigned)nl), 256, 0, st>>>(
           (const int8_t *)h->spins, (const int8_t *)J, g, (long long *)E, (long long *)M);
     if (Q && g.n_sets >= 2)
@@ -304,7 +383,8 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
   }
   // EA coded words
   const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-  unsigned gx = capped(g.N, 64);
+  // at most 16 sites per thread: 3 * 16 * 256 * 2^k stays inside the 16 planes
+  unsigned gx = (unsigned)((g.N + 256 * 16 - 1) / (256 * 16));
   measure_msc_kernel<<<dim3(gx, (unsigned)n_wl), 256, 0, st>>>(
       (const uint32_t *)h->spins, (const uint32_t *)J, g, (long long *)E, (long long *)M,
       (g.n_sets >= 2) ? (long long *)Q : nullptr);

@@ -55,56 +55,48 @@ __global__ void couplings_msc_kernel(uint32_t *__restrict__ J, Geom g, RoundKeys
 // with R_dE all ones iff the shared uniform r < thr(dE).
 __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w,
                                                         const uint32_t *__restrict__ J, Geom g,
+                                                        uint32_t total,
                                                         const uint32_t *__restrict__ thr,
                                                         RoundKeys rk, uint32_t sweep,
                                                         int colour) {
-  const int L = g.L;
-  const int G = g.n_real / 32;
-  const int64_t half = g.N / 2;
-  const int64_t quads = (half + 3) / 4;
-  const int64_t n_wl = (int64_t)g.n_sets * G * g.n_temps;
-  const int64_t LL = (int64_t)L * L;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_wl * quads;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t wl = k / quads, j4 = k - wl * quads;
-    const int t = (int)(wl % g.n_temps);
-    const int grp = (int)((wl / g.n_temps) % G);
-    const int a = (int)(wl / ((int64_t)g.n_temps * G));
-    uint32_t *s = w + wl * g.N;
-    const uint32_t *Jg = J + (int64_t)grp * 3 * g.N;
-    const uint4 r = philox(make_uint4((uint32_t)j4, sweep, lattice_id(a, grp, t),
+  const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N, half = N / 2;
+  const uint32_t quads = (half + 3) / 4;
+  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const uint32_t wl = fdiv(k, g.fquads), j4 = k - wl * quads;
+    const uint32_t t = wl % T;
+    const uint32_t grp = (wl / T) % G;
+    const uint32_t a = wl / (T * G);
+    uint32_t *s = w + (size_t)wl * N;
+    const uint32_t *Jg = J + (size_t)grp * 3 * N;
+    const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, grp, t),
                                       ctr_w(TAG_UPDATE, (uint32_t)colour, 0)), rk);
     const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t j = 4 * j4 + q;
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t j = 4 * j4 + q;
       if (j >= half) break;
-      const int64_t i0 = 2 * j;
-      const int x0 = (int)(i0 % L);
-      const int y = (int)((i0 / L) % L);
-      const int z = (int)(i0 / LL);
-      const int x = x0 + ((colour + y + z) & 1);
-      const int64_t rowbase = i0 - x0;
-      const int64_t i = rowbase + x;
-      const int64_t ixp = rowbase + (x == L - 1 ? 0 : x + 1);
-      const int64_t ixm = rowbase + (x == 0 ? L - 1 : x - 1);
-      const int64_t iyp = y == L - 1 ? i - (int64_t)(L - 1) * L : i + L;
-      const int64_t iym = y == 0 ? i + (int64_t)(L - 1) * L : i - L;
-      const int64_t izp = z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL;
-      const int64_t izm = z == 0 ? i + (int64_t)(L - 1) * LL : i - LL;
+      const Site st = site_of(g, j, colour);
+      const uint32_t i = st.i;
+      const uint32_t ixp = st.rowbase + (st.x == L - 1 ? 0 : st.x + 1);
+      const uint32_t ixm = st.rowbase + (st.x == 0 ? L - 1 : st.x - 1);
+      const uint32_t iyp = st.y == L - 1 ? i - (L - 1) * L : i + L;
+      const uint32_t iym = st.y == 0 ? i + (L - 1) * L : i - L;
+      const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
+      const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
       const uint32_t S = s[i];
       const uint32_t u0 = S ^ s[ixp] ^ Jg[i];
       const uint32_t u1 = S ^ s[ixm] ^ Jg[ixm];
-      const uint32_t u2 = S ^ s[iyp] ^ Jg[g.N + i];
-      const uint32_t u3 = S ^ s[iym] ^ Jg[g.N + iym];
-      const uint32_t u4 = S ^ s[izp] ^ Jg[2 * g.N + i];
-      const uint32_t u5 = S ^ s[izm] ^ Jg[2 * g.N + izm];
+      const uint32_t u2 = S ^ s[iyp] ^ Jg[N + i];
+      const uint32_t u3 = S ^ s[iym] ^ Jg[N + iym];
+      const uint32_t u4 = S ^ s[izp] ^ Jg[2 * N + i];
+      const uint32_t u5 = S ^ s[izm] ^ Jg[2 * N + izm];
       // bit-sliced count of the six unsatisfied-bond indicators
       const uint32_t s1 = u0 ^ u1 ^ u2, c1 = (u0 & u1) | (u2 & (u0 ^ u1));
       const uint32_t s2 = u3 ^ u4 ^ u5, c2 = (u3 & u4) | (u5 & (u3 ^ u4));
       const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
       const uint32_t b1 = c1 ^ c2 ^ c3, b2 = (c1 & c2) | (c3 & (c1 ^ c2));
-      const uint32_t rq = word_of(r, (uint32_t)q);
+      const uint32_t rq = word_of(r, q);
       const uint32_t R4 = rq < t4 ? ~0u : 0u, R8 = rq < t8 ? ~0u : 0u, R12 = rq < t12 ? ~0u : 0u;
       const uint32_t ge3 = b2 | (b1 & b0);
       const uint32_t eq2 = ~b2 & b1 & ~b0, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
@@ -177,12 +169,12 @@ cudaError_t launch_sweeps_msc_ea(spin_lattice *h, const uint32_t *J, int64_t n_s
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
   const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-  const int64_t work = n_wl * ((g.N / 2 + 3) / 4);
+  const uint32_t work = (uint32_t)(n_wl * ((g.N / 2 + 3) / 4));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour)
-      msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, h->d_thr,
-                                                            rk, sweep, colour);
+      msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
+                                                            h->d_thr, rk, sweep, colour);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -27,77 +27,83 @@ __device__ __forceinline__ int64_t row_word(const Msc2d &m, int64_t lat, int c, 
 }
 
 // One colour phase.  Each warp owns 32 consecutive blocks of the global
-// block list (lattice, row, block); first every lane draws its uniforms for
-// each of those blocks in turn and the ballots of (r < thr4), (r < thr8) are
-// kept by the lane that owns the block; then each lane updates its block.
+// block list (lattice, row, block).  Stage 1: for each of those blocks in
+// turn, lane l draws the Philox call of sites k = 128 B + 4 l + q (q = 0..3)
+// and the warp ballots (r < thr4) and (r < thr8): bit l of the ballot for q
+// is exactly bit l of word 4 B + q, so the two ballots are the acceptance
+// masks of the block's four words; lane 0 parks them in shared memory.
+// Stage 2: lane b updates block b with bit-sliced logic.
+constexpr int kWarps = 8;
+
 __global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__ w, Msc2d m,
-                                                          Geom g, int64_t n_lat,
+                                                          Geom g, uint32_t total_blocks,
                                                           const uint32_t *__restrict__ thr,
                                                           RoundKeys rk, uint32_t sweep,
                                                           int colour) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t total_blocks = n_lat * m.L * m.bpr;
-  const int64_t first = warp * 32;
+  __shared__ uint4 masks[kWarps][32][2];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t first = (blockIdx.x * kWarps + wib) * 32u;
   if (first >= total_blocks) return;
+  // L^2/256 blocks per lattice is a multiple of 32, so all 32 blocks of a
+  // warp lie in one lattice, and the Philox counter of lane l in block b is
+  // 32 b + l (rows are consecutive in the colour index)
+  const uint32_t per_lat = (uint32_t)m.L * (uint32_t)m.bpr;
+  const uint32_t lat = first / per_lat;
+  const uint32_t lid = lattice_id_of(g, lat);
+  const int t = slot_of(g, lat);
+  const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
-  uint32_t m4[4] = {0, 0, 0, 0}, m8[4] = {0, 0, 0, 0};
-  for (int b = 0; b < 32; ++b) {
-    const int64_t gb = first + b;
-    if (gb >= total_blocks) break;  // uniform over the warp
-    const int64_t lat = gb / ((int64_t)m.L * m.bpr);
-    const int64_t rem = gb - lat * ((int64_t)m.L * m.bpr);
-    const int y = (int)(rem / m.bpr), B = (int)(rem % m.bpr);
-    const int t = slot_of(g, lat);
-    const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
-    const uint32_t j4 = (uint32_t)y * (uint32_t)(m.L >> 3) + 32u * (uint32_t)B + (uint32_t)lane;
-    const uint4 r = philox(make_uint4(j4, sweep, lattice_id_of(g, lat), wctr), rk);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t rq = word_of(r, q);
-      const uint32_t b4 = __ballot_sync(0xffffffffu, rq < thr4);
-      const uint32_t b8 = __ballot_sync(0xffffffffu, rq < thr8);
-      if (lane == b) {
-        m4[q] = b4;
-        m8[q] = b8;
-      }
+  uint32_t j4 = 32u * (first - lat * per_lat) + (uint32_t)lane;
+  uint4 *mk = &masks[wib][0][0];
+#pragma unroll 2
+  for (uint32_t b = 0; b < 32u; ++b, j4 += 32u) {
+    const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
+    const uint32_t a0 = __ballot_sync(0xffffffffu, r.x < thr4);
+    const uint32_t a1 = __ballot_sync(0xffffffffu, r.y < thr4);
+    const uint32_t a2 = __ballot_sync(0xffffffffu, r.z < thr4);
+    const uint32_t a3 = __ballot_sync(0xffffffffu, r.w < thr4);
+    const uint32_t e0 = __ballot_sync(0xffffffffu, r.x < thr8);
+    const uint32_t e1 = __ballot_sync(0xffffffffu, r.y < thr8);
+    const uint32_t e2 = __ballot_sync(0xffffffffu, r.z < thr8);
+    const uint32_t e3 = __ballot_sync(0xffffffffu, r.w < thr8);
+    if (lane == 0) {
+      mk[2 * b] = make_uint4(a0, a1, a2, a3);
+      mk[2 * b + 1] = make_uint4(e0, e1, e2, e3);
     }
   }
-  const int64_t gb = first + lane;
-  if (gb >= total_blocks) return;
-  const int64_t lat = gb / ((int64_t)m.L * m.bpr);
-  const int64_t rem = gb - lat * ((int64_t)m.L * m.bpr);
-  const int y = (int)(rem / m.bpr), B = (int)(rem % m.bpr);
-  const int yu = y == 0 ? m.L - 1 : y - 1, yd = y == m.L - 1 ? 0 : y + 1;
+  __syncwarp();
+  const uint32_t gb = first + (uint32_t)lane;
+  const uint32_t rem = gb - lat * per_lat;
+  const uint32_t y = rem / (uint32_t)m.bpr;
+  const uint32_t B = rem - y * (uint32_t)m.bpr;
+  const int yu = y == 0 ? m.L - 1 : (int)y - 1, yd = (int)y == m.L - 1 ? 0 : (int)y + 1;
   const int oc = colour ^ 1;
-  uint32_t *S = w + row_word(m, lat, colour, y) + 4 * B;
-  const uint32_t *O = w + row_word(m, lat, oc, y);
-  const uint32_t *Uu = w + row_word(m, lat, oc, yu) + 4 * B;
-  const uint32_t *Dd = w + row_word(m, lat, oc, yd) + 4 * B;
+  uint32_t *S = w + row_word(m, lat, colour, (int)y) + 4 * B;
+  const uint32_t *O = w + row_word(m, lat, oc, (int)y);
   const uint4 s = *reinterpret_cast<const uint4 *>(S);
   const uint4 o = *reinterpret_cast<const uint4 *>(O + 4 * B);
-  const uint4 u = *reinterpret_cast<const uint4 *>(Uu);
-  const uint4 d = *reinterpret_cast<const uint4 *>(Dd);
-  const int p = (colour + y) & 1;
+  const uint4 u = *reinterpret_cast<const uint4 *>(w + row_word(m, lat, oc, yu) + 4 * B);
+  const uint4 d = *reinterpret_cast<const uint4 *>(w + row_word(m, lat, oc, yd) + 4 * B);
+  const uint4 m4 = mk[2 * lane], m8 = mk[2 * lane + 1];
+  const int p = (colour + (int)y) & 1;
   // second horizontal neighbour: k - 1 (p = 0) or k + 1 (p = 1)
   uint32_t sh[4];
   if (p == 0) {
-    const int Bp = B == 0 ? m.bpr - 1 : B - 1;
-    const uint32_t prev3 = O[4 * Bp + 3];
-    sh[0] = (o.w << 1) | (prev3 >> 31);
+    const uint32_t Bp = B == 0 ? (uint32_t)m.bpr - 1 : B - 1;
+    sh[0] = (o.w << 1) | (O[4 * Bp + 3] >> 31);
     sh[1] = o.x;
     sh[2] = o.y;
     sh[3] = o.z;
   } else {
-    const int Bn = B == m.bpr - 1 ? 0 : B + 1;
-    const uint32_t next0 = O[4 * Bn];
+    const uint32_t Bn = B == (uint32_t)m.bpr - 1 ? 0 : B + 1;
     sh[0] = o.y;
     sh[1] = o.z;
     sh[2] = o.w;
-    sh[3] = (o.x >> 1) | (next0 << 31);
+    sh[3] = (o.x >> 1) | (O[4 * Bn] << 31);
   }
   const uint32_t sv[4] = {s.x, s.y, s.z, s.w}, ov[4] = {o.x, o.y, o.z, o.w};
   const uint32_t uv[4] = {u.x, u.y, u.z, u.w}, dv[4] = {d.x, d.y, d.z, d.w};
+  const uint32_t m4v[4] = {m4.x, m4.y, m4.z, m4.w}, m8v[4] = {m8.x, m8.y, m8.z, m8.w};
   uint32_t nv[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__
     const uint32_t b1 = c1 ^ c2 ^ c3, b2 = (c1 & c2) | (c3 & (c1 ^ c2));
     // n antiparallel neighbours, dE = 8 - 4n
     const uint32_t ge2 = b2 | b1, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
-    nv[q] = sv[q] ^ (ge2 | (eq1 & m4[q]) | (eq0 & m8[q]));
+    nv[q] = sv[q] ^ (ge2 | (eq1 & m4v[q]) | (eq0 & m8v[q]));
   }
   *reinterpret_cast<uint4 *>(S) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
 }
@@ -203,13 +209,13 @@ cudaError_t launch_init_msc2d(spin_lattice *h) {
 cudaError_t launch_sweeps_msc2d(spin_lattice *h, int64_t n_sweeps) {
   const Msc2d m = geom2d(h);
   const RoundKeys rk = make_round_keys(h->d.seed);
-  const int64_t blocks = h->n_lat * m.L * m.bpr;
-  const int64_t threads = ((blocks + 31) / 32) * 32;
+  const int64_t blocks = h->n_lat * m.L * m.bpr;  // < 2^31, checked by spin_init
+  const unsigned grid = (unsigned)((blocks + 32 * kWarps - 1) / (32 * kWarps));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour)
-      msc2d_phase_kernel<<<grid_for(threads, 256), 256, 0, h->stream>>>(
-          (uint32_t *)h->spins, m, h->g, h->n_lat, h->d_thr, rk, sweep, colour);
+      msc2d_phase_kernel<<<grid, 32 * kWarps, 0, h->stream>>>(
+          (uint32_t *)h->spins, m, h->g, (uint32_t)blocks, h->d_thr, rk, sweep, colour);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -1,19 +1,20 @@
 #!/usr/bin/env python
 """Throughput of the checkerboard Metropolis sweep on GB300, in spin flips/ns.
 
-Workload: 2D Ising ferromagnet, L = 16384 (2^28 spins per lattice), int8
-spins, one lattice at each beta in {0.40, 0.4407, 0.50}, hot start, Philox
-uniforms drawn in-kernel.  One step = SWEEPS_PER_STEP checkerboard sweeps of
-all three lattices followed by the energy / magnetisation reduction.  The
-1-bit coded layout of the same workload is timed too and reported beside
-the main number.  A spin flip is one attempted Metropolis update.
+Workload: 2D Ising ferromagnet, L = 16384 (2^28 spins per lattice), one
+lattice at each beta in {0.40, 0.4407, 0.50}, hot start, one Philox uniform
+per attempted flip drawn in-kernel.  One step = SWEEPS_PER_STEP checkerboard
+sweeps of all three lattices followed by the energy / magnetisation
+reduction.  The headline uses the 1-bit multi-spin-coded layout; the int8
+layout of the same workload is timed too and reported beside it.  A spin
+flip is one attempted Metropolis update.
 
 Arms:
   (default)          the CUDA library through its C ABI on N GPUs (one
                      process per GPU; each rank runs its own three lattices,
                      weak scaling, no collective on the data path);
-  --impl reference   the CPU oracle (tests' reference implementation) on the
-                     host cores, on a bounded sample of the same workload.
+  --impl reference   the CPU oracle (the tests' reference implementation) on
+                     the host cores, on a bounded sample of the same workload.
 """
 import argparse
 import hashlib
@@ -31,31 +32,30 @@ sys.path.insert(0, ROOT)
 L = 16384
 BETAS = [0.40, 0.4407, 0.50]
 SWEEPS_PER_STEP = 10
-METRIC = "spin flips/ns, 2D Ising L=16384 checkerboard Metropolis (int8), 1 GB300"
+METRIC = "spin flips/ns, 2D Ising L=16384 checkerboard Metropolis, 1 GB300"
 UNIT = "flips/ns"
-WORKLOAD = ("2D Ising ferromagnet L=16384 periodic, int8 spins, 3 lattices at beta "
-            "0.40/0.4407/0.50, hot start, Philox4x32-10, %d sweeps + E/M reduction per step"
-            % SWEEPS_PER_STEP)
+WORKLOAD = ("2D Ising ferromagnet L=16384 periodic, 3 lattices at beta 0.40/0.4407/0.50, "
+            "hot start, Philox4x32-10 uniform per site, %d sweeps + E/M reduction per step; "
+            "1-bit multi-spin-coded layout (int8 layout reported beside it)" % SWEEPS_PER_STEP)
 
-# Algorithmic integer operations per attempted flip of the fused int8 sweep:
-# Philox4x32-10 = 10 rounds x (2 wide 32x32 multiplies + 2 three-input XORs)
-# per 4 uniforms = 10 per flip; the local field of 8 bytes at once (4 XOR+AND
-# pairs, 3 adds, 2 shifted neighbour words, on 64-bit words) = 18 ops per 4
-# active sites = 4.5 per flip; the decision (select threshold, compare, form
-# the flip byte, merge) = 4 per flip; loads/stores of 2 bytes = 0.5.
-OPS_PER_FLIP = 19.0
-# Integer issue rate of one SM: 4 sub-partitions x 32 lanes per clock.
-LANE_OPS_PER_CLK_PER_SM = 128
+# Roofline of the sweep: every attempted flip consumes one 32-bit Philox
+# word, and Philox4x32-10 costs 20 wide (32x32->64) multiplies per 4 words,
+# i.e. 5 per flip.  They run on the FMA-heavy pipe, which completes 32 wide
+# multiplies per clock per SM (derived from the generator probe, which keeps
+# that pipe 92% busy at 1.49 Philox calls per clock per SM).  The sweep's
+# roof is therefore SMs x 32 x f_SM wide multiplies per second.
+WIDE_MULS_PER_FLIP = 5
+WIDE_MULS_PER_CLK_PER_SM = 32
 
-# DRAM traffic of one fused sweep launch (3 lattices share a launch) from the
-# ncu capture summarised in profiles/, valid while the kernel source hash
-# matches; otherwise the figure is reported as null.
-FUSED_TRAFFIC_BYTES = None
-FUSED_TRAFFIC_SRC_SHA = None
+# DRAM bytes of one phase launch of the coded sweep over the three lattices
+# (ncu capture summarised in profiles/), valid while the kernel source hash
+# matches; otherwise reported as null.
+KERNEL_TRAFFIC_BYTES = None
+KERNEL_TRAFFIC_SRC_SHA = None
 
 
 def kernel_sha():
-    p = os.path.join(ROOT, "paper_1101_1427_gb300", "csrc", "fused2d.cu")
+    p = os.path.join(ROOT, "paper_1101_1427_gb300", "csrc", "msc2d.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
@@ -152,6 +152,54 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- GPU arm
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def side_configs(torch, sp, B, stream):
+    """Short measurements of the other hot-path configurations (context for
+    the headline): 3D Heisenberg L=128 (FP32), and 3D EA L=16 with 1024
+    realisations x 32 slots x 2 sets, exchange and measurement every sweep,
+    in the per-handle multi-launch form and in the batched persistent form."""
+    import numpy as np
+    out = {}
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, 128, B.SPIN_F32X4, seed=11)
+    for variant, name in ((0, "heisenberg_L128_fp32"), (2, "heisenberg_L128_fp32_fast")):
+        lat.set_variant(variant)
+        B.spin_sweep(lat.h, None, [0.693], 4, lat.seed)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, [0.693], 40, lat.seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_flips_per_ns"] = 40 * 128 ** 3 / (a.elapsed_time(b) * 1e6)
+    lat.close()
+    betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
+    ea = sp.Lattice(B.SPIN_EA, 3, 16, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=12)
+    n = 40
+    flips = n * 16 ** 3 * 1024 * 32 * 2
+    ser = ea.series_buffers(n)
+    acc = torch.zeros(64, dtype=torch.int64, device=stream.device)
+    B.spin_run(ea.h, ea.couplings, betas, 2, 1, 1, ser["E"], ser["M"], ser["Q"], None, None, acc)
+    a, b = _events(torch)
+    a.record(stream)
+    B.spin_run(ea.h, ea.couplings, betas, n, 1, 1, ser["E"], ser["M"], ser["Q"], None, None, acc)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["ea_L16_pt_plain_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
+    item = [ea.batch_item(betas, ser, acc)]
+    B.spin_batch_run(item, 2, 1, 1, stream.cuda_stream)
+    a, b = _events(torch)
+    a.record(stream)
+    B.spin_batch_run(item, n, 1, 1, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ea.sync()
+    out["ea_L16_pt_batched_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
+    ea.close()
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -171,113 +219,113 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=n_lat, seed=1 + rank)
+    def max_over_ranks(ms):
+        if world > 1:
+            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
     E = torch.empty(n_lat, dtype=torch.int64, device=dev)
     M = torch.empty(n_lat, dtype=torch.int64, device=dev)
 
-    def step():
-        B.spin_sweep(lat.h, None, BETAS, S, lat.seed)
-        B.spin_measure(lat.h, None, E, M)
+    def make_step(lat):
+        def step():
+            B.spin_sweep(lat.h, None, BETAS, S, lat.seed)
+            B.spin_measure(lat.h, None, E, M)
+        return step
 
+    def timed(step, k):
+        barrier()
+        a, b = _events(torch)
+        a.record(stream)
+        for _ in range(k):
+            step()
+        b.record(stream)
+        barrier()
+        return a.elapsed_time(b)
+
+    # headline: 1-bit coded layout
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, n_temps=n_lat, seed=1 + rank)
+    step = make_step(lat)
     for _ in range(args.warmup):
         step()
     visible = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = visible.split(",")[local_rank] if visible else local_rank
     clocks = ClockSampler(smi_index)
     clocks.start()
-    barrier()
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        step()
-    t_end.record(stream)
-    barrier()
+    ms = max_over_ranks(timed(step, args.steps))
     clk = clocks.stop()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     value = world * args.steps * flips_per_step / (ms * 1e6)
 
-    # dominant kernel alone: fused sweep launches (an even count, so no copy)
+    # the dominant kernel alone: one colour phase over the three lattices per launch
     n_k = 2 * S
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    k0.record(stream)
-    B.spin_sweep(lat.h, None, BETAS, n_k, lat.seed)
-    k1.record(stream)
+    a, b = _events(torch)
+    a.record(stream)
+    B.spin_sweep(lat.h, None, BETAS, S, lat.seed)
+    b.record(stream)
     torch.cuda.synchronize()
-    launch_ms = k0.elapsed_time(k1) / n_k
-    flips_per_launch = n_lat * L * L
-
-    # same workload in the 1-bit coded layout
-    lat_msc = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, n_temps=n_lat, seed=1 + rank)
-    B.spin_sweep(lat_msc.h, None, BETAS, S, lat_msc.seed)
-    torch.cuda.synchronize()
-    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    m0.record(stream)
-    for _ in range(max(1, args.steps // 2)):
-        B.spin_sweep(lat_msc.h, None, BETAS, S, lat_msc.seed)
-        B.spin_measure(lat_msc.h, None, E, M)
-    m1.record(stream)
-    torch.cuda.synchronize()
-    msc_value = max(1, args.steps // 2) * flips_per_step / (m0.elapsed_time(m1) * 1e6)
-    lat_msc.close()
+    launch_ms = a.elapsed_time(b) / n_k
+    flips_per_launch = n_lat * L * L // 2
 
     # end to end through the API with host buffers: every step copies the
-    # lattices in from pinned memory and the lattices and observables out
-    host_in = torch.empty(lat.spins.numel(), dtype=torch.int8).pin_memory()
+    # coded lattices in from pinned memory and the lattices and observables out
+    host_in = torch.empty(lat.spins.numel(), dtype=lat.spins.dtype).pin_memory()
     host_in.copy_(lat.spins.cpu())
     host_out = torch.empty_like(host_in).pin_memory()
     host_obs = torch.empty(2 * n_lat, dtype=torch.int64).pin_memory()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+
+    def e2e_step():
         lat.spins.copy_(host_in, non_blocking=True)
         step()
         host_out.copy_(lat.spins, non_blocking=True)
         host_obs[:n_lat].copy_(E, non_blocking=True)
         host_obs[n_lat:].copy_(M, non_blocking=True)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+
+    e2e_ms = max_over_ranks(timed(e2e_step, args.steps))
     e2e_value = world * args.steps * flips_per_step / (e2e_ms * 1e6)
+    spin_bytes = lat.spins.numel() * lat.spins.element_size()
     lat.close()
 
+    # the int8 layout of the same workload (fused out-of-place sweep)
+    lat8 = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=n_lat, seed=1 + rank)
+    step8 = make_step(lat8)
+    step8()
+    k8 = max(3, args.steps // 3)
+    i8_value = world * k8 * flips_per_step / (max_over_ranks(timed(step8, k8)) * 1e6)
+    lat8.close()
+
+    side = side_configs(torch, sp, B, stream) if rank == 0 and not args.no_side else {}
     if rank != 0:
         return
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = clk.get("sm_mhz") or 1800.0
-    achieved = OPS_PER_FLIP * flips_per_launch / (launch_ms * 1e-3) / 1e9  # Gop/s
-    peak = sms * LANE_OPS_PER_CLK_PER_SM * mhz * 1e6 / 1e9
-    traffic = FUSED_TRAFFIC_BYTES if FUSED_TRAFFIC_SRC_SHA == kernel_sha() else None
+    mhz = clk.get("sm_mhz") or 2070.0
+    achieved = WIDE_MULS_PER_FLIP * flips_per_launch / (launch_ms * 1e-3) / 1e9  # Gmul/s
+    peak = sms * WIDE_MULS_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+    traffic = KERNEL_TRAFFIC_BYTES if KERNEL_TRAFFIC_SRC_SHA == kernel_sha() else None
     cpu_value, cpu_flips, cpu_s = oracle_rate(args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 (1 bit per spin)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "L": L, "betas": BETAS, "lattices_per_gpu": n_lat,
-                   "sweeps_per_step": S, "layout": "int8, fused out-of-place sweep",
-                   "l2": "inputs larger than L2 (3 x 256 MiB per GPU)",
-                   "msc1_flips_per_ns": msc_value, "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                   "sweeps_per_step": S, "layout": "1-bit synchronous multi-spin coding",
+                   "i8_flips_per_ns": i8_value,
+                   "l2": "coded lattices (96 MiB) fit in L2; int8 lattices (768 MiB) exceed it",
+                   "parallelism": f"replicas x{world}", **side},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "fused2d_kernel", "launch_ms": launch_ms,
-                     "ops_per_flip": OPS_PER_FLIP,
-                     "peak_basis": f"{sms} SMs x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x "
-                                   f"{mhz:.0f} MHz (sampled median)"},
+                     "kernel": "msc2d_phase_kernel", "launch_ms": launch_ms,
+                     "flips_per_launch": flips_per_launch,
+                     "peak_basis": f"{sms} SMs x {WIDE_MULS_PER_CLK_PER_SM} wide multiplies/clk x "
+                                   f"{mhz:.0f} MHz (sampled median); {WIDE_MULS_PER_FLIP} per flip"},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_flips} flips on 1024^2 lattices at beta=0.4407 "
                                    f"({cpu_s:.1f} s)"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": host_in.numel(),
-                "d2h_bytes_per_step": host_out.numel() + 8 * 2 * n_lat},
-        "gpu_launches": args.steps * (S + 1),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spin_bytes,
+                "d2h_bytes_per_step": spin_bytes + 8 * 2 * n_lat},
+        "gpu_launches": args.steps * (2 * S + 1),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -290,6 +338,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

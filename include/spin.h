@@ -140,6 +140,49 @@ int spin_run(spin_lattice *lat, const void *couplings, const double *betas, int6
              int32_t measure_every, int32_t pt_every, int64_t *E_series, int64_t *M_series,
              int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted);
 
+/* One handle of a batched launch: its couplings and HOST betas as in
+ * spin_sweep, and optional device series/counters as in spin_run. */
+typedef struct {
+  spin_lattice *lat;
+  const void *couplings;
+  const double *betas;
+  int64_t *E_series;
+  int64_t *M_series;
+  int64_t *Q_series;
+  int64_t *accepted;
+} spin_batch_item;
+
+/* Batched persistent launch (the paper maps independent replicas and
+ * tempering copies to thread blocks, Sec. 6-7): n_sweeps sweeps of every
+ * lattice of every handle, with the measurements and exchange steps of
+ * spin_run, in ONE cooperative kernel launch on `stream`.  Results
+ * (lattices, series, exchange decisions) are identical to calling spin_run
+ * on each handle.  Supported handles: EA in the coded layout (L <= 32) and
+ * 2D int8 ferromagnets with L % 16 == 0 (no exchange for those); at most 16
+ * handles and 96 work units (one unit per EA realisation group or Ising
+ * lattice).  Work units are spread over teams of co-resident CTAs in
+ * proportion to their work; a team synchronises through global-memory
+ * barriers whose waits are bounded in time: on expiry the launch ends early
+ * and spin_sync on the FIRST item's handle returns SPIN_ETIMEOUT.  The first
+ * call allocates a small process-wide workspace; later calls of no larger
+ * size allocate nothing. */
+int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
+                   int32_t measure_every, int32_t pt_every, void *stream);
+
+/* Autotuner for spin_batch_run: times n_sweeps-sweep trial launches with 1..4
+ * CTAs per SM on copies of the spins (handles and counters are left as they
+ * were) and caches the fastest for this batch shape; best (optional, host)
+ * receives it. */
+int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
+                    int32_t measure_every, int32_t pt_every, void *stream, int32_t *best);
+
+/* Batch options taken from the first item's handle: bound on every barrier
+ * wait in ns (0: 2 s), CTAs per SM (0: autotuned or 2), and a number of
+ * barrier arrivals that never come (0 in normal use; > 0 makes every team
+ * barrier wait out its bound, for tests of the timeout path). */
+int spin_set_batch_options(spin_lattice *lat, uint64_t timeout_ns, int32_t ctas_per_sm,
+                           int32_t missing_arrivals);
+
 /* Layout conversion between the handle's layout and one int8 spin per site
  * ([n_sets][n_temps][n_real][L^dim], +-1), device buffers. */
 int spin_unpack_i8(spin_lattice *lat, int8_t *out);
@@ -169,9 +212,11 @@ int64_t spin_sweeps_done(const spin_lattice *lat);
 int64_t spin_pt_steps_done(const spin_lattice *lat);
 int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_done);
 
-/* Selects the 2D int8 sweep kernel: 0 = two in-place colour phases per
- * sweep, 1 = one fused out-of-place pass per sweep (default).  Both give
- * identical results. */
+/* Kernel variant.  2D int8 ferromagnet: 0 = two in-place colour phases per
+ * sweep, 1 = one fused out-of-place pass per sweep (default); both give
+ * identical results.  Heisenberg: 0 = the full-accuracy FP32 library
+ * functions (default), 2 = hardware approximations of sin, cos and exp (the
+ * paper's "fast_math" mode, Sec. 5), within the same tolerances. */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
 const char *spin_strerror(int code);

@@ -23,6 +23,12 @@ class spin_desc(C.Structure):
                 ("stream", C.c_void_p)]
 
 
+class spin_batch_item(C.Structure):
+    _fields_ = [("lat", C.c_void_p), ("couplings", C.c_void_p), ("betas", C.c_void_p),
+                ("E_series", C.c_void_p), ("M_series", C.c_void_p), ("Q_series", C.c_void_p),
+                ("accepted", C.c_void_p)]
+
+
 class SpinError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {strerror(code)} ({code})")
@@ -50,6 +56,9 @@ def lib():
         L.spin_rng_fill.argtypes = [u64, u32, u32, u32, u32, u32, u64, p, p]
         L.spin_rng_probe.argtypes = [u64, u32, u32, p, p]
         L.spin_sync.argtypes = [p]
+        L.spin_batch_run.argtypes = [p, C.c_int, i64, i32, i32, p]
+        L.spin_batch_tune.argtypes = [p, C.c_int, i64, i32, i32, p, p]
+        L.spin_set_batch_options.argtypes = [p, u64, i32, i32]
         L.spin_sweeps_done.argtypes = [p]
         L.spin_sweeps_done.restype = i64
         L.spin_pt_steps_done.argtypes = [p]
@@ -62,7 +71,8 @@ def lib():
         L.spin_destroy.restype = None
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
-                     "spin_set_counters", "spin_set_variant"):
+                     "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
+                     "spin_set_batch_options"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -141,6 +151,41 @@ def spin_rng_fill(seed, tag, colour, extra, lattice_id, sweep, count, out, strea
 
 def spin_rng_probe(seed, threads, calls, out, stream=None):
     return _check(lib().spin_rng_probe(seed, threads, calls, _ptr(out), stream), "spin_rng_probe")
+
+
+def _batch_items(items):
+    """items: list of dicts with keys lat (handle), couplings, betas and the
+    optional device tensors E, M, Q, accepted.  Returns the ctypes array and
+    the host beta arrays that must stay alive during the call."""
+    arr = (spin_batch_item * len(items))()
+    keep = []
+    for k, it in enumerate(items):
+        b = _host_doubles(it["betas"])
+        keep.append(b)
+        dp = lambda key: it[key].data_ptr() if it.get(key) is not None else None
+        lat = it["lat"].value if hasattr(it["lat"], "value") else it["lat"]
+        arr[k] = spin_batch_item(lat, dp("couplings"), C.cast(b, C.c_void_p), dp("E"), dp("M"),
+                                 dp("Q"), dp("accepted"))
+    return arr, keep
+
+
+def spin_batch_run(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
+    arr, keep = _batch_items(items)
+    return _check(lib().spin_batch_run(arr, len(items), n_sweeps, measure_every, pt_every, stream),
+                  "spin_batch_run")
+
+
+def spin_batch_tune(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
+    arr, keep = _batch_items(items)
+    best = C.c_int32(0)
+    _check(lib().spin_batch_tune(arr, len(items), n_sweeps, measure_every, pt_every, stream,
+                                 C.byref(best)), "spin_batch_tune")
+    return best.value
+
+
+def spin_set_batch_options(h, timeout_ns=0, ctas_per_sm=0, missing_arrivals=0):
+    return _check(lib().spin_set_batch_options(h, timeout_ns, ctas_per_sm, missing_arrivals),
+                  "spin_set_batch_options")
 
 
 def spin_sync(h):

@@ -152,6 +152,11 @@ bool ea(const spin_lattice *h) { return h->d.model == SPIN_EA; }
 }  // namespace
 
 namespace spin {
+int upload_thresholds_for_batch(spin_lattice *h, const double *betas) { return upload_thresholds(h, betas); }
+int upload_pt_tables_for_batch(spin_lattice *h, const double *betas) {
+  if (!betas) return SPIN_EINVAL;
+  return upload_pt_tables(h, betas);
+}
 bool fused2d_supported(int L);
 cudaError_t launch_init_msc2d(spin_lattice *h);
 }
@@ -362,11 +367,21 @@ int spin_set_counters(spin_lattice *h, int64_t sweeps_done, int64_t pt_steps_don
   return SPIN_OK;
 }
 
+int spin_set_batch_options(spin_lattice *h, uint64_t timeout_ns, int32_t ctas_per_sm,
+                           int32_t missing_arrivals) {
+  if (!h || ctas_per_sm < 0 || ctas_per_sm > 8 || missing_arrivals < 0) return SPIN_EINVAL;
+  h->batch_timeout_ns = timeout_ns;
+  h->batch_ctas_per_sm = ctas_per_sm;
+  h->batch_fault_extra = missing_arrivals;
+  return SPIN_OK;
+}
+
 int spin_set_variant(spin_lattice *h, int32_t variant) {
-  if (!h || variant < 0 || variant > 1) return SPIN_EINVAL;
+  if (!h || variant < 0 || variant > 2) return SPIN_EINVAL;
   if (variant == 1 && !(h->d.model == SPIN_ISING && h->d.dim == 2 && h->d.layout == SPIN_I8 &&
                         fused2d_supported(h->g.L)))
     return SPIN_EINVAL;
+  if (variant == 2 && h->d.model != SPIN_HEISENBERG) return SPIN_EINVAL;
   h->variant = variant;
   return SPIN_OK;
 }

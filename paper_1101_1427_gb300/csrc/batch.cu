@@ -1,0 +1,803 @@
+// Batched persistent launch: many lattices of several handles, many sweeps,
+// one kernel launch.  The paper maps independent replicas to thread blocks
+// (Sec. 6) and tempering copies to extra blocks (Sec. 7) but returns to the
+// host for every exchange; here measurement, exchange decisions and the
+// exchange itself run inside the same persistent launch.
+//
+// Work units:
+//   EA unit     = one realisation group (32 realisations) of an EA handle in
+//                 the coded layout: all replica sets, all temperature slots.
+//                 Its team of P CTAs splits the slots: CTA p owns slots
+//                 [p n_T / P, (p+1) n_T / P) of every set, so a colour phase
+//                 needs no synchronisation beyond __syncthreads.  Exchange
+//                 steps read the energy of a neighbour's slot and write its
+//                 words, so they are framed by two team barriers.
+//   Ising unit  = one lattice of a 2D int8 ferromagnet handle; its team
+//                 splits the rows and synchronises after each colour phase.
+// Team barriers are counters in global memory; every wait is bounded in
+// time (globaltimer) and sets the error word on expiry, after which all
+// CTAs leave the kernel and spin_sync reports SPIN_ETIMEOUT.
+//
+// The kernel is launched cooperatively so that all CTAs are co-resident.
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+
+namespace spin {
+
+struct BatchUnit {
+  int kind;        // 0 EA coded group, 1 Ising 2D int8 lattice
+  int team_first;  // first CTA of the team
+  int team_size;   // CTAs in the team
+  int L;
+  uint32_t N;
+  int n_T, n_sets;
+  FastDiv fL;
+  const uint32_t *thr;  // [n_T][4]
+  int key;              // round keys of the handle
+  uint32_t sweep0;      // handle's sweep counter at launch
+  uint32_t pt0;         // handle's exchange counter at launch
+  long long meas0;      // measurements already taken by the handle in this call: 0
+  // EA
+  uint32_t *w;          // words of set 0, this group, slot 0
+  size_t set_stride;    // words between replica sets
+  const uint32_t *J;    // couplings of this group [3][N]
+  int grp, n_real;
+  const uint32_t *pt_tab;
+  const int32_t *pt_off, *pt_len;
+  const double *pt_dbeta;
+  long long *E_series, *M_series, *Q_series, *accepted;
+  long long n_lat;      // lattices of the handle (series row length)
+  int *Escr;            // [n_sets][n_T][32] unsatisfied-bond counts
+  // Ising
+  int8_t *s;
+  long long lat_index;
+  uint32_t lid;
+  int slot;
+};
+
+constexpr int kMaxUnits = 96;
+constexpr int kMaxHandles = 16;
+
+// Everything a launch needs travels in the kernel's parameter space (under
+// 32 KB), so a launch is one kernel node: capturable, nothing to upload.
+struct BatchParams {
+  int n_units;
+  int measure_every, pt_every, extra;
+  int64_t n_sweeps;
+  uint64_t timeout_ns;
+  RoundKeys keys[kMaxHandles];
+  BatchUnit units[kMaxUnits];
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kPl = 12;  // per-lane counter planes (counts < 4096)
+
+__device__ __forceinline__ uint32_t ld_acquire(const unsigned *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct Sync {
+  unsigned *ctr;
+  unsigned target;
+  int size;
+  int *err;
+  uint64_t timeout_ns;
+  int extra;  // arrivals that never come (fault injection for the timeout test)
+};
+
+// Returns false if the team (or the whole launch) has failed.
+__device__ bool team_barrier(Sync &sy) {
+  __shared__ int s_ok;
+  __syncthreads();
+  sy.target += sy.size;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(sy.ctr, 1u);
+    const unsigned want = sy.target + (unsigned)sy.extra;
+    const uint64_t t0 = globaltimer();
+    while ((int)(ld_acquire(sy.ctr) - want) < 0) {
+      if (*(volatile int *)sy.err) {
+        ok = 0;
+        break;
+      }
+      if (globaltimer() - t0 > sy.timeout_ns) {
+        atomicExch(sy.err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// counter planes += 3-bit value (x0, x1, x2)
+__device__ __forceinline__ void add3(uint32_t (&C)[kPl], uint32_t x0, uint32_t x1, uint32_t x2) {
+  uint32_t c = C[0] & x0;
+  C[0] ^= x0;
+  uint32_t t = C[1] ^ x1 ^ c;
+  c = (C[1] & x1) | (c & (C[1] ^ x1));
+  C[1] = t;
+  t = C[2] ^ x2 ^ c;
+  c = (C[2] & x2) | (c & (C[2] ^ x2));
+  C[2] = t;
+#pragma unroll
+  for (int k = 3; k < kPl; ++k) {
+    const uint32_t n = C[k] & c;
+    C[k] ^= c;
+    c = n;
+  }
+}
+
+__device__ __forceinline__ void add1(uint32_t (&C)[kPl], uint32_t x) {
+#pragma unroll
+  for (int k = 0; k < kPl; ++k) {
+    const uint32_t n = C[k] & x;
+    C[k] ^= x;
+    x = n;
+  }
+}
+
+// Sum of the per-lane counters of a warp; every lane returns the count of
+// realisation bit `lane`.
+__device__ __forceinline__ int warp_bit_counts(const uint32_t (&C)[kPl]) {
+  constexpr int K = kPl + 5;
+  uint32_t P[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) P[k] = k < kPl ? C[k] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t a = P[k], b = __shfl_xor_sync(0xffffffffu, P[k], o);
+      P[k] = a ^ b ^ carry;
+      carry = (a & b) | (carry & (a ^ b));
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) cnt += (int)((P[k] >> lane) & 1u) << k;
+  return cnt;
+}
+
+// One colour phase of one word-lattice by one warp (lanes strided over the
+// quads of colour sites).  With kCount the post-update number of
+// unsatisfied bonds of each updated (colour-1) site is added to C: every
+// bond joins a colour-0 and a colour-1 site, so summing over colour-1 sites
+// counts each bond once.
+template <bool kCount>
+__device__ __forceinline__ void ea_phase_warp(uint32_t *__restrict__ s, const uint32_t *__restrict__ Jg,
+                                              const BatchUnit &U, const RoundKeys &rk, uint32_t sweep,
+                                              uint32_t lid, int colour, uint32_t t4, uint32_t t8,
+                                              uint32_t t12, uint32_t first, uint32_t stride,
+                                              uint32_t (&C)[kPl]) {
+  const uint32_t L = (uint32_t)U.L, LL = L * L, N = U.N;
+  const uint32_t quads = N / 8;
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  for (uint32_t j4 = first; j4 < quads; j4 += stride) {
+    const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t j = 4 * j4 + q;
+      const uint32_t i0 = 2u * j;
+      const uint32_t row = fdiv(i0, U.fL);
+      const uint32_t x0 = i0 - row * L;
+      const uint32_t z = fdiv(row, U.fL), y = row - z * L;
+      const uint32_t x = x0 + ((colour + y + z) & 1u);
+      const uint32_t rowbase = i0 - x0, i = rowbase + x;
+      const uint32_t ixp = rowbase + (x == L - 1 ? 0 : x + 1);
+      const uint32_t ixm = rowbase + (x == 0 ? L - 1 : x - 1);
+      const uint32_t iyp = y == L - 1 ? i - (L - 1) * L : i + L;
+      const uint32_t iym = y == 0 ? i + (L - 1) * L : i - L;
+      const uint32_t izp = z == L - 1 ? i - (L - 1) * LL : i + LL;
+      const uint32_t izm = z == 0 ? i + (L - 1) * LL : i - LL;
+      const uint32_t S = s[i];
+      const uint32_t u0 = S ^ s[ixp] ^ Jg[i];
+      const uint32_t u1 = S ^ s[ixm] ^ Jg[ixm];
+      const uint32_t u2 = S ^ s[iyp] ^ Jg[N + i];
+      const uint32_t u3 = S ^ s[iym] ^ Jg[N + iym];
+      const uint32_t u4 = S ^ s[izp] ^ Jg[2 * N + i];
+      const uint32_t u5 = S ^ s[izm] ^ Jg[2 * N + izm];
+      const uint32_t s1 = u0 ^ u1 ^ u2, c1 = (u0 & u1) | (u2 & (u0 ^ u1));
+      const uint32_t s2 = u3 ^ u4 ^ u5, c2 = (u3 & u4) | (u5 & (u3 ^ u4));
+      const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
+      const uint32_t b1 = c1 ^ c2 ^ c3, b2 = (c1 & c2) | (c3 & (c1 ^ c2));
+      const uint32_t rq = word_of(r, q);
+      const uint32_t R4 = rq < t4 ? ~0u : 0u, R8 = rq < t8 ? ~0u : 0u, R12 = rq < t12 ? ~0u : 0u;
+      const uint32_t ge3 = b2 | (b1 & b0);
+      const uint32_t eq2 = ~b2 & b1 & ~b0, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
+      const uint32_t F = ge3 | (eq2 & R4) | (eq1 & R8) | (eq0 & R12);
+      s[i] = S ^ F;
+      if (kCount) {
+        // a flip turns u unsatisfied bonds into 6 - u: bit 0 is unchanged
+        const uint32_t v1 = (b2 & ~b1 & ~b0) | (~b2 & ~(b1 ^ b0));
+        const uint32_t v2 = ~b2 & ~(b1 & b0);
+        add3(C, b0, (F & v1) | (~F & b1), (F & v2) | (~F & b2));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- EA unit
+__device__ bool ea_sweep(const BatchUnit &U, int part, const RoundKeys &rk, Sync &sy, uint32_t s_abs,
+                         bool measure, bool pt, long long meas_row, uint32_t pt_step) {
+  __shared__ int e_cnt[64][32];   // per owned word-lattice (set, slot) counts
+  __shared__ uint32_t masks[64];  // accept masks per (set, owned pair)
+  const int P = U.team_size;
+  const int t0 = part * U.n_T / P, t1 = (part + 1) * U.n_T / P;
+  const int nt_own = t1 - t0;
+  const int n_w = U.n_sets * nt_own;  // owned word-lattices, <= 64
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // warps per word-lattice when there are fewer word-lattices than warps
+  const int wpw = n_w >= kWarps ? 1 : kWarps / n_w;
+  const bool need_e = measure || pt;
+  for (int colour = 0; colour < 2; ++colour) {
+    if (colour == 1 && need_e)
+      for (int k = threadIdx.x; k < n_w * 32; k += kThreads) (&e_cnt[0][0])[k] = 0;
+    if (colour == 1) __syncthreads();
+    for (int wi = warp / wpw; wi < n_w; wi += kWarps / wpw) {
+      if (warp / wpw >= n_w) break;
+      const int a = wi / nt_own, t = t0 + wi % nt_own;
+      uint32_t *s = U.w + a * U.set_stride + (size_t)t * U.N;
+      const uint32_t lid = lattice_id((uint32_t)a, (uint32_t)U.grp, (uint32_t)t);
+      const uint32_t t4 = __ldg(U.thr + 4 * t + 1), t8 = __ldg(U.thr + 4 * t + 2), t12 = __ldg(U.thr + 4 * t + 3);
+      const uint32_t first = (uint32_t)((warp % wpw) * 32 + lane), stride = (uint32_t)(wpw * 32);
+      uint32_t C[kPl];
+#pragma unroll
+      for (int k = 0; k < kPl; ++k) C[k] = 0;
+      if (colour == 1 && need_e) {
+        ea_phase_warp<true>(s, U.J, U, rk, s_abs, lid, 1, t4, t8, t12, first, stride, C);
+        const int cnt = warp_bit_counts(C);
+        if (wpw == 1) e_cnt[wi][lane] = cnt;
+        else atomicAdd(&e_cnt[wi][lane], cnt);
+      } else {
+        ea_phase_warp<false>(s, U.J, U, rk, s_abs, lid, colour, t4, t8, t12, first, stride, C);
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t N = U.N;
+  if (need_e) {
+    for (int k = threadIdx.x; k < n_w * 32; k += kThreads) {
+      const int wi = k >> 5, b = k & 31;
+      const int a = wi / nt_own, t = t0 + wi % nt_own;
+      const int unsat = e_cnt[wi][b];
+      U.Escr[(a * U.n_T + t) * 32 + b] = unsat;
+      if (measure && U.E_series) {
+        const long long lat = ((long long)a * U.n_T + t) * U.n_real + 32 * U.grp + b;
+        U.E_series[meas_row * U.n_lat + lat] = 2LL * unsat - 3LL * N;
+      }
+    }
+  }
+  if (measure && (U.Q_series || U.M_series)) {
+    // overlap between sets 0 and 1 and magnetisation, owned slots
+    for (int wi = warp; wi < nt_own * 2; wi += kWarps) {
+      const int t = t0 + (wi >> 1);
+      const bool do_m = (wi & 1) == 0;
+      if (do_m && !U.M_series) continue;
+      if (!do_m && (!U.Q_series || U.n_sets < 2)) continue;
+      uint32_t C[kPl];
+#pragma unroll
+      for (int k = 0; k < kPl; ++k) C[k] = 0;
+      // (M is accumulated for set 0 only here; other sets below)
+      const uint32_t *s0 = U.w + (size_t)t * N;
+      const uint32_t *s1 = s0 + U.set_stride;
+      for (uint32_t i = lane; i < N; i += 32) add1(C, do_m ? s0[i] : (s0[i] ^ s1[i]));
+      const int cnt = warp_bit_counts(C);
+      const long long r = 32 * U.grp + lane;
+      if (do_m) U.M_series[meas_row * U.n_lat + (long long)t * U.n_real + r] = (long long)N - 2LL * cnt;
+      else U.Q_series[meas_row * (long long)U.n_T * U.n_real + (long long)t * U.n_real + r] = (long long)N - 2LL * cnt;
+    }
+    if (U.M_series)
+      for (int a = 1; a < U.n_sets; ++a)
+        for (int wi = warp; wi < nt_own; wi += kWarps) {
+          const int t = t0 + wi;
+          uint32_t C[kPl];
+#pragma unroll
+          for (int k = 0; k < kPl; ++k) C[k] = 0;
+          const uint32_t *sa = U.w + a * U.set_stride + (size_t)t * N;
+          for (uint32_t i = lane; i < N; i += 32) add1(C, sa[i]);
+          const int cnt = warp_bit_counts(C);
+          U.M_series[meas_row * U.n_lat + ((long long)a * U.n_T + t) * U.n_real + 32 * U.grp + lane] =
+              (long long)N - 2LL * cnt;
+        }
+  }
+  if (!pt) {
+    __syncthreads();  // measurements read words the next sweep rewrites
+    return true;
+  }
+  if (!team_barrier(sy)) return false;  // energies of all slots visible
+  // decisions for pairs (t, t+1) with t owned, t = step parity (mod 2)
+  const int parity = (int)(pt_step & 1u);
+  int n_pairs = 0;
+  for (int t = t0 + ((t0 - parity) & 1); t < t1 && t + 1 < U.n_T; t += 2) ++n_pairs;
+  const int tp0 = t0 + ((t0 - parity) & 1);
+  for (int k = warp; k < U.n_sets * n_pairs; k += kWarps) {
+    const int a = k / n_pairs, t = tp0 + 2 * (k % n_pairs);
+    const int r = 32 * U.grp + lane;
+    const int e0 = U.Escr[(a * U.n_T + t) * 32 + lane], e1 = U.Escr[(a * U.n_T + t + 1) * 32 + lane];
+    const long long dE = 2LL * (e1 - e0);
+    const double db = U.pt_dbeta[t];
+    bool acc;
+    if (db * (double)dE >= 0.0) {
+      acc = true;
+    } else {
+      const long long m = (dE < 0 ? -dE : dE) / 4;
+      const uint32_t th = m < U.pt_len[t] ? __ldg(U.pt_tab + U.pt_off[t] + m) : 0u;
+      const uint4 v = philox(make_uint4((uint32_t)r >> 2, pt_step, lattice_id((uint32_t)a, 0, (uint32_t)t),
+                                        ctr_w(TAG_PT, 0, 0)), rk);
+      acc = word_of(v, (uint32_t)r & 3u) < th;
+    }
+    const uint32_t A = __ballot_sync(0xffffffffu, acc);
+    if (lane == 0) {
+      masks[k] = A;
+      if (U.accepted && A) atomicAdd((unsigned long long *)&U.accepted[a * U.n_T + t], (unsigned long long)__popc(A));
+    }
+  }
+  __syncthreads();
+  // exchange: for every owned pair and site, the accepted bits change places
+  for (int k = 0; k < U.n_sets * n_pairs; ++k) {
+    const uint32_t A = masks[k];
+    if (!A) continue;
+    const int a = k / n_pairs, t = tp0 + 2 * (k % n_pairs);
+    uint32_t *w0 = U.w + a * U.set_stride + (size_t)t * N, *w1 = w0 + N;
+    for (uint32_t i = threadIdx.x; i < N; i += kThreads) {
+      const uint32_t x0 = w0[i], x1 = w1[i];
+      const uint32_t x = (x0 ^ x1) & A;
+      w0[i] = x0 ^ x;
+      w1[i] = x1 ^ x;
+    }
+  }
+  return team_barrier(sy);  // exchanged words visible before the next sweep
+}
+
+// ---------------------------------------------------------------- Ising unit
+__device__ void ising_rows_phase(const BatchUnit &U, const RoundKeys &rk, uint32_t sweep, int colour,
+                                 int r0, int r1) {
+  const int L = U.L, chunks = L >> 3;
+  const uint32_t thr4 = __ldg(U.thr + 4 * U.slot + 1), thr8 = __ldg(U.thr + 4 * U.slot + 2);
+  const uint64_t MASK = 0x0202020202020202ull;
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  const int total = (r1 - r0) * chunks;
+  for (int k = threadIdx.x; k < total; k += kThreads) {
+    const int y = r0 + k / chunks, m = k % chunks;
+    int8_t *base = U.s;
+    const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+    uint64_t *rowp = reinterpret_cast<uint64_t *>(base + (int64_t)y * L);
+    const uint64_t C = rowp[m];
+    const uint64_t Uw = reinterpret_cast<const uint64_t *>(base + (int64_t)yu * L)[m];
+    const uint64_t Dw = reinterpret_cast<const uint64_t *>(base + (int64_t)yd * L)[m];
+    const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
+    const uint64_t lb = (uint8_t)base[(int64_t)y * L + xl], rb = (uint8_t)base[(int64_t)y * L + xr];
+    const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);
+    const uint64_t A = ((C ^ Uw) & MASK) + ((C ^ Dw) & MASK) + ((C ^ Lw) & MASK) + ((C ^ Rw) & MASK);
+    const uint4 r = philox(make_uint4((uint32_t)y * (uint32_t)chunks + (uint32_t)m, sweep, U.lid, wctr), rk);
+    const int p = (colour + y) & 1;
+    const uint64_t An = A >> (8 * p);
+    const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
+    const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
+    const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
+    const uint32_t q0 = (lo & 0x2u) ? thr4 : thr8, q1 = (lo & 0x20000u) ? thr4 : thr8;
+    const uint32_t q2 = (hi & 0x2u) ? thr4 : thr8, q3 = (hi & 0x20000u) ? thr4 : thr8;
+    const uint32_t f_lo = g_lo | (uint32_t)(r.x < q0) | ((uint32_t)(r.y < q1) << 16);
+    const uint32_t f_hi = g_hi | (uint32_t)(r.z < q2) | ((uint32_t)(r.w < q3) << 16);
+    const uint64_t F = (((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu)) << (8 * p);
+    rowp[m] = C ^ F;
+  }
+}
+
+__device__ bool ising_sweep(const BatchUnit &U, int part, const RoundKeys &rk, Sync &sy, uint32_t s_abs,
+                            bool measure, long long meas_row) {
+  const int P = U.team_size;
+  const int r0 = part * U.L / P, r1 = (part + 1) * U.L / P;
+  for (int colour = 0; colour < 2; ++colour) {
+    ising_rows_phase(U, rk, s_abs, colour, r0, r1);
+    if (!team_barrier(sy)) return false;
+  }
+  if (measure && (U.E_series || U.M_series)) {
+    const int L = U.L, segs = L >> 4;
+    const uint64_t B1 = 0x0202020202020202ull;
+    long long anti = 0, down = 0;
+    for (int k = threadIdx.x; k < (r1 - r0) * segs; k += kThreads) {
+      const int y = r0 + k / segs, sg = k % segs;
+      const int8_t *row = U.s + (int64_t)y * L;
+      const int8_t *nrow = U.s + (int64_t)(y == L - 1 ? 0 : y + 1) * L;
+      const uint4 c = *reinterpret_cast<const uint4 *>(row + 16 * sg);
+      const uint4 d = *reinterpret_cast<const uint4 *>(nrow + 16 * sg);
+      const uint64_t c0 = (uint64_t)c.x | ((uint64_t)c.y << 32), c1 = (uint64_t)c.z | ((uint64_t)c.w << 32);
+      const uint64_t d0 = (uint64_t)d.x | ((uint64_t)d.y << 32), d1 = (uint64_t)d.z | ((uint64_t)d.w << 32);
+      const uint64_t nb = (uint8_t)row[sg == segs - 1 ? 0 : 16 * sg + 16];
+      const uint64_t q0 = (c0 >> 8) | (c1 << 56), q1 = (c1 >> 8) | (nb << 56);
+      anti += __popcll((c0 ^ q0) & B1) + __popcll((c1 ^ q1) & B1) + __popcll((c0 ^ d0) & B1) +
+              __popcll((c1 ^ d1) & B1);
+      down += __popcll(c0 & B1) + __popcll(c1 & B1);
+    }
+    anti = warp_sum(anti);
+    down = warp_sum(down);
+    if ((threadIdx.x & 31) == 0) {
+      const long long N = (long long)U.N;
+      const long long idx = meas_row * U.n_lat + U.lat_index;
+      // the series entries were zeroed before the launch; part 0 adds the constants
+      if (U.E_series) atomicAdd((unsigned long long *)&U.E_series[idx],
+                                (unsigned long long)(2 * anti - ((part == 0 && threadIdx.x == 0) ? 2 * N : 0)));
+      if (U.M_series) atomicAdd((unsigned long long *)&U.M_series[idx],
+                                (unsigned long long)(-2 * down + ((part == 0 && threadIdx.x == 0) ? N : 0)));
+    }
+    if (!team_barrier(sy)) return false;  // rows read across the strip edge
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchParams prm,
+                                                         unsigned *bar, int *err) {
+  __shared__ BatchUnit U;
+  __shared__ RoundKeys rk;
+  // CTA -> unit: teams are consecutive CTA ranges in unit order
+  int lo = 0, hi = prm.n_units - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prm.units[mid].team_first <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const int u = lo;
+  if (threadIdx.x == 0) {
+    U = prm.units[u];
+    rk = prm.keys[U.key];
+  }
+  __syncthreads();
+  const int part = (int)blockIdx.x - U.team_first;
+  Sync sy{bar + u, 0u, U.team_size, err, prm.timeout_ns, prm.extra};
+  long long meas_row = 0;
+  uint32_t pt_step = U.pt0;
+  for (int64_t k = 0; k < prm.n_sweeps; ++k) {
+    const uint32_t s_abs = U.sweep0 + (uint32_t)k;
+    const bool measure = prm.measure_every > 0 && ((s_abs + 1u) % (uint32_t)prm.measure_every) == 0u;
+    const bool pt = prm.pt_every > 0 && ((s_abs + 1u) % (uint32_t)prm.pt_every) == 0u;
+    bool ok;
+    if (U.kind == 0)
+      ok = ea_sweep(U, part, rk, sy, s_abs, measure, pt, meas_row, pt_step);
+    else
+      ok = ising_sweep(U, part, rk, sy, s_abs, measure, meas_row);
+    if (!ok) return;
+    if (measure) ++meas_row;
+    if (pt) ++pt_step;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+static std::map<std::vector<long long>, int> g_tuned_bps;  // autotuner cache: batch signature -> CTAs per SM
+
+static double unit_work(const BatchUnit &U) {
+  if (U.kind == 0) return 48.0 * U.n_sets * U.n_T * (double)U.N;  // ~48 ops per word-site
+  return 30.0 * (double)U.N;                                      // ~30 ops per int8 site
+}
+
+// Distributes `grid` CTAs over the units: every unit gets its minimum (EA:
+// at most 64 owned word-lattices per CTA; Ising: 1), then CTAs go one by
+// one to the unit with the largest work per CTA, up to each unit's maximum
+// (EA: one slot per CTA; Ising: 8 rows per CTA).  Returns the CTAs used.
+static int assign_teams(BatchUnit *units, int n, int grid) {
+  std::vector<int> P(n), cap(n);
+  int used = 0;
+  for (int u = 0; u < n; ++u) {
+    if (units[u].kind == 0) {
+      // each CTA owns at most 64 word-lattices (set, slot)
+      int p = 1;
+      while (units[u].n_sets * ((units[u].n_T + p - 1) / p) > 64) ++p;
+      P[u] = p;
+      cap[u] = units[u].n_T;
+    } else {
+      P[u] = 1;
+      cap[u] = std::max(1, units[u].L / 8);
+    }
+    used += P[u];
+  }
+  while (used < grid) {
+    int best = -1;
+    double bw = -1;
+    for (int u = 0; u < n; ++u)
+      if (P[u] < cap[u] && unit_work(units[u]) / P[u] > bw) {
+        bw = unit_work(units[u]) / P[u];
+        best = u;
+      }
+    if (best < 0) break;
+    ++P[best];
+    ++used;
+  }
+  int first = 0;
+  for (int u = 0; u < n; ++u) {
+    units[u].team_first = first;
+    units[u].team_size = P[u];
+    first += P[u];
+  }
+  return first;
+}
+
+// workspace shared by all batch launches of the process (grown on demand)
+static unsigned *g_bar = nullptr;
+static int *g_escr = nullptr;
+static size_t g_escr_words = 0;
+
+}  // namespace spin
+
+using namespace spin;
+
+namespace spin {
+int upload_thresholds_for_batch(spin_lattice *h, const double *betas);  // api.cu
+int upload_pt_tables_for_batch(spin_lattice *h, const double *betas);   // api.cu
+}
+
+static int batch_build(const spin_batch_item *items, int n_items, BatchParams &prm, size_t &escr_words) {
+  prm.n_units = 0;
+  escr_words = 0;
+  for (int k = 0; k < n_items; ++k) {
+    spin_lattice *h = items[k].lat;
+    prm.keys[k] = make_round_keys(h->d.seed);
+    const Geom &g = h->g;
+    if (h->d.model == SPIN_EA) {
+      const int G = g.n_real / 32;
+      for (int grp = 0; grp < G; ++grp) {
+        if (prm.n_units >= kMaxUnits) return SPIN_EINVAL;
+        BatchUnit &U = prm.units[prm.n_units++];
+        U = BatchUnit{};
+        U.kind = 0;
+        U.L = g.L;
+        U.N = (uint32_t)g.N;
+        U.n_T = g.n_temps;
+        U.n_sets = g.n_sets;
+        U.fL = g.fL;
+        U.thr = h->d_thr;
+        U.key = k;
+        U.sweep0 = (uint32_t)h->sweeps_done;
+        U.pt0 = (uint32_t)h->pt_steps_done;
+        U.set_stride = (size_t)G * g.n_temps * g.N;
+        U.w = (uint32_t *)h->spins + (size_t)grp * g.n_temps * g.N;
+        U.J = (const uint32_t *)items[k].couplings + (size_t)grp * 3 * g.N;
+        U.grp = grp;
+        U.n_real = g.n_real;
+        U.pt_tab = h->d_pt_thr;
+        U.pt_off = h->d_pt_off;
+        U.pt_len = h->d_pt_len;
+        U.pt_dbeta = h->d_pt_dbeta;
+        U.E_series = (long long *)items[k].E_series;
+        U.M_series = (long long *)items[k].M_series;
+        U.Q_series = (long long *)items[k].Q_series;
+        U.accepted = (long long *)items[k].accepted;
+        U.n_lat = h->n_lat;
+        U.Escr = (int *)(uintptr_t)escr_words;  // offset into the workspace
+        escr_words += (size_t)g.n_sets * g.n_temps * 32;
+      }
+    } else {
+      for (int64_t lat = 0; lat < h->n_lat; ++lat) {
+        if (prm.n_units >= kMaxUnits) return SPIN_EINVAL;
+        BatchUnit &U = prm.units[prm.n_units++];
+        U = BatchUnit{};
+        U.kind = 1;
+        U.L = g.L;
+        U.N = (uint32_t)g.N;
+        U.n_T = g.n_temps;
+        U.n_sets = g.n_sets;
+        U.thr = h->d_thr;
+        U.key = k;
+        U.sweep0 = (uint32_t)h->sweeps_done;
+        U.s = (int8_t *)h->spins + lat * g.N;
+        U.E_series = (long long *)items[k].E_series;
+        U.M_series = (long long *)items[k].M_series;
+        U.n_lat = h->n_lat;
+        U.lat_index = lat;
+        U.lid = lattice_id_of(g, lat);
+        U.slot = slot_of(g, lat);
+      }
+    }
+  }
+  return SPIN_OK;
+}
+
+static bool batch_item_ok(const spin_batch_item &it, int32_t pt_every) {
+  const spin_lattice *h = it.lat;
+  if (!h || !it.betas) return false;
+  if (h->d.model == SPIN_EA)
+    return h->d.layout == SPIN_MSC1 && it.couplings != nullptr && h->g.L <= 32 && h->d.n_sets <= 32;
+  if (h->d.model == SPIN_ISING)
+    return h->d.layout == SPIN_I8 && h->g.dim == 2 && h->g.L % 16 == 0 && it.Q_series == nullptr &&
+           !(pt_every > 0 && h->d.n_temps > 1);
+  return false;
+}
+
+static cudaError_t batch_launch(BatchParams &prm, int grid, cudaStream_t st, int *err) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaMemsetAsync(g_bar, 0, kMaxUnits * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, batch_kernel, prm, g_bar, err);
+}
+
+extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
+                              int32_t measure_every, int32_t pt_every, void *stream_v) {
+  if (!items || n_items <= 0 || n_items > kMaxHandles || n_sweeps < 0 || measure_every < 0 || pt_every < 0)
+    return SPIN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream_v;
+  for (int k = 0; k < n_items; ++k) {
+    if (!batch_item_ok(items[k], pt_every)) return SPIN_EINVAL;
+    spin_lattice *h = items[k].lat;
+    for (int q = 0; q < k; ++q)
+      if (items[q].lat == h) return SPIN_EINVAL;
+    if (h->sweeps_done + n_sweeps > (int64_t)0xFFFFFFFFll) return SPIN_EINVAL;
+    int rc = upload_thresholds_for_batch(h, items[k].betas);
+    if (rc) return rc;
+    if (h->d.model == SPIN_EA && pt_every > 0) {
+      rc = upload_pt_tables_for_batch(h, items[k].betas);
+      if (rc) return rc;
+    }
+  }
+  if (n_sweeps == 0) return SPIN_OK;
+  static BatchParams prm;  // large; built on the host for each call
+  size_t escr_words = 0;
+  int rc = batch_build(items, n_items, prm, escr_words);
+  if (rc) return rc;
+  prm.n_sweeps = n_sweeps;
+  prm.measure_every = measure_every;
+  prm.pt_every = pt_every;
+  spin_lattice *h0 = items[0].lat;
+  prm.timeout_ns = h0->batch_timeout_ns ? h0->batch_timeout_ns : 2000000000ull;
+  prm.extra = h0->batch_fault_extra;
+  // co-resident grid
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    return SPIN_ECUDA;
+  // workspace (allocated on first use or growth only)
+  if (!g_bar && cudaMalloc(&g_bar, kMaxUnits * sizeof(unsigned)) != cudaSuccess) return SPIN_ENOMEM;
+  if (escr_words > g_escr_words) {
+    if (g_escr) cudaFree(g_escr);
+    g_escr = nullptr;
+    if (cudaMalloc(&g_escr, escr_words * 4) != cudaSuccess) return SPIN_ENOMEM;
+    g_escr_words = escr_words;
+  }
+  for (int u = 0; u < prm.n_units; ++u)
+    if (prm.units[u].kind == 0) prm.units[u].Escr = g_escr + (uintptr_t)prm.units[u].Escr;
+  // Ising series rows are accumulated with atomics: zero the rows of this call
+  for (int k = 0; k < n_items; ++k) {
+    spin_lattice *h = items[k].lat;
+    if (h->d.model != SPIN_ISING || measure_every <= 0) continue;
+    const int64_t n_meas = (h->sweeps_done + n_sweeps) / measure_every - h->sweeps_done / measure_every;
+    if (items[k].E_series && cudaMemsetAsync(items[k].E_series, 0, 8 * n_meas * h->n_lat, st) != cudaSuccess)
+      return SPIN_ECUDA;
+    if (items[k].M_series && cudaMemsetAsync(items[k].M_series, 0, 8 * n_meas * h->n_lat, st) != cudaSuccess)
+      return SPIN_ECUDA;
+  }
+  // CTAs per SM: autotuned once per batch signature (see spin_batch_tune)
+  std::vector<long long> sig;
+  for (int u = 0; u < prm.n_units; ++u) {
+    sig.push_back(prm.units[u].kind);
+    sig.push_back(prm.units[u].L);
+    sig.push_back(prm.units[u].n_T);
+    sig.push_back(prm.units[u].n_sets);
+  }
+  int bps = std::min(per_sm, h0->batch_ctas_per_sm > 0 ? h0->batch_ctas_per_sm : 2);
+  auto it = g_tuned_bps.find(sig);
+  if (h0->batch_ctas_per_sm <= 0 && it != g_tuned_bps.end()) bps = std::min(per_sm, it->second);
+  const int grid = assign_teams(prm.units, prm.n_units, sms * bps);
+  if (grid > sms * per_sm) return SPIN_EINVAL;
+  if (cudaMemsetAsync(h0->d_err, 0, sizeof(int), st) != cudaSuccess) return SPIN_ECUDA;
+  if (batch_launch(prm, grid, st, h0->d_err) != cudaSuccess) return SPIN_ECUDA;
+  for (int k = 0; k < n_items; ++k) {
+    spin_lattice *h = items[k].lat;
+    const int64_t before = h->sweeps_done;
+    h->sweeps_done += n_sweeps;
+    if (pt_every > 0)  // as spin_run: every exchange point advances the counter
+      h->pt_steps_done += h->sweeps_done / pt_every - before / pt_every;
+  }
+  return SPIN_OK;
+}
+
+// Autotuner: times one short batch per CTAs-per-SM candidate on copies of
+// the spins (the handles' own state is untouched) and caches the fastest
+// for this batch signature.
+extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
+                               int32_t measure_every, int32_t pt_every, void *stream_v,
+                               int32_t *best_out) {
+  if (!items || n_items <= 0 || n_items > kMaxHandles) return SPIN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream_v;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, 0) != cudaSuccess)
+    return SPIN_ECUDA;
+  // back up the spins and counters; series outputs are not written
+  std::vector<spin_batch_item> tmp(items, items + n_items);
+  std::vector<void *> backup(n_items, nullptr);
+  std::vector<size_t> bytes(n_items);
+  std::vector<int64_t> sw(n_items), ps(n_items);
+  for (int k = 0; k < n_items; ++k) {
+    spin_lattice *h = items[k].lat;
+    bytes[k] = h->d.layout == SPIN_I8 ? (size_t)(h->n_lat * h->g.N)
+                                      : (size_t)h->g.n_sets * (h->g.n_real / 32) * h->g.n_temps * h->g.N * 4;
+    if (cudaMalloc(&backup[k], bytes[k]) != cudaSuccess) return SPIN_ENOMEM;
+    cudaMemcpyAsync(backup[k], h->spins, bytes[k], cudaMemcpyDeviceToDevice, st);
+    sw[k] = h->sweeps_done;
+    ps[k] = h->pt_steps_done;
+    tmp[k].E_series = tmp[k].M_series = tmp[k].Q_series = tmp[k].accepted = nullptr;
+  }
+  spin_lattice *h0 = items[0].lat;
+  const int saved = h0->batch_ctas_per_sm;
+  float best_ms = 1e30f;
+  int best = 1;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int rc = SPIN_OK;
+  for (int c = 1; c <= std::min(per_sm, 4); ++c) {
+    h0->batch_ctas_per_sm = c;
+    cudaEventRecord(a, st);
+    rc = spin_batch_run(tmp.data(), n_items, n_sweeps, 0, pt_every, stream_v);
+    cudaEventRecord(b, st);
+    if (rc) break;
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+    for (int k = 0; k < n_items; ++k) {
+      items[k].lat->sweeps_done = sw[k];
+      items[k].lat->pt_steps_done = ps[k];
+    }
+  }
+  (void)measure_every;
+  h0->batch_ctas_per_sm = saved;
+  for (int k = 0; k < n_items; ++k) {
+    cudaMemcpyAsync(items[k].lat->spins, backup[k], bytes[k], cudaMemcpyDeviceToDevice, st);
+    items[k].lat->sweeps_done = sw[k];
+    items[k].lat->pt_steps_done = ps[k];
+  }
+  cudaStreamSynchronize(st);
+  for (int k = 0; k < n_items; ++k) cudaFree(backup[k]);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  std::vector<long long> sig;
+  BatchParams *prm = new BatchParams;
+  size_t ew = 0;
+  batch_build(items, n_items, *prm, ew);
+  for (int u = 0; u < prm->n_units; ++u) {
+    sig.push_back(prm->units[u].kind);
+    sig.push_back(prm->units[u].L);
+    sig.push_back(prm->units[u].n_T);
+    sig.push_back(prm->units[u].n_sets);
+  }
+  delete prm;
+  g_tuned_bps[sig] = best;
+  if (best_out) *best_out = best;
+  return SPIN_OK;
+}

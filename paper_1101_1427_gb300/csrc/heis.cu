@@ -7,12 +7,19 @@ namespace spin {
 namespace {
 
 // Uniform unit vector from two uniforms: z = 2 u1 - 1, phi = 2 pi u2.
+// sin/cos of 2 pi u2 are evaluated as sincospi(2 u2): 2 u2 is exact, so the
+// argument reduction is exact too.  kFast selects the hardware
+// approximations (the paper's "fast_math" mode, Sec. 5).
+template <bool kFast>
 __device__ __forceinline__ float4 unit_vector(uint32_t w1, uint32_t w2) {
   const float z = 2.0f * uniform24(w1) - 1.0f;
-  const float phi = 6.28318530717958647692f * uniform24(w2);
   const float rho = sqrtf(fmaxf(0.0f, 1.0f - z * z));
   float sn, cs;
-  sincosf(phi, &sn, &cs);
+  if (kFast) {
+    __sincosf(6.28318530717958647692f * uniform24(w2), &sn, &cs);
+  } else {
+    sincospif(2.0f * uniform24(w2), &sn, &cs);
+  }
   return make_float4(rho * cs, rho * sn, z, 0.0f);
 }
 
@@ -22,7 +29,7 @@ __global__ void heis_init_kernel(float4 *__restrict__ s, Geom g, int64_t n_lat, 
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t lat = k / g.N, i = k - lat * g.N;
     const uint4 w = philox(make_uint4((uint32_t)i, 0u, lattice_id_of(g, lat), ctr_w(TAG_HEIS_INIT, 0, 0)), rk);
-    s[k] = unit_vector(w.x, w.y);
+    s[k] = unit_vector<false>(w.x, w.y);
   }
 }
 
@@ -37,14 +44,25 @@ __global__ void heis_cold_kernel(float4 *__restrict__ s, int64_t total) {
 // uniform.  dE = -(n - s) . h with h the sum of the six neighbour spins;
 // accept iff dE <= 0 or u3 < exp(-beta dE).  beta (float) is read from
 // word 0 of the slot's row of the threshold table.
+template <bool kFast>
 __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s, Geom g,
                                                          uint32_t total,
                                                          const uint32_t *__restrict__ thr,
                                                          RoundKeys rk, uint32_t sweep,
                                                          int colour) {
   const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N, half = N / 2;
+  const bool single = g.n_real == 1 && g.n_temps == 1 && g.n_sets == 1;
+  const float beta0 = __uint_as_float(__ldg(thr));
+  const uint32_t wctr = ctr_w(TAG_HEIS, (uint32_t)colour, 0);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
-    const uint32_t lat = fdiv(k, g.fhalf), j = k - lat * half;
+    uint32_t lat = 0, j = k, lid = 0;
+    float beta = beta0;
+    if (!single) {
+      lat = fdiv(k, g.fhalf);
+      j = k - lat * half;
+      lid = lattice_id32(g, lat);
+      beta = __uint_as_float(__ldg(thr + 4 * slot_of32(g, lat)));
+    }
     float4 *sl = s + (size_t)lat * N;
     const Site st = site_of(g, j, colour);
     const uint32_t i = st.i;
@@ -55,16 +73,16 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
     const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
     const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
     const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym], e = sl[izp], f = sl[izm];
+    const float4 si = sl[i];
+    const uint4 w = philox(make_uint4(j, sweep, lid, wctr), rk);
     const float hx = a.x + b.x + c.x + d.x + e.x + f.x;
     const float hy = a.y + b.y + c.y + d.y + e.y + f.y;
     const float hz = a.z + b.z + c.z + d.z + e.z + f.z;
-    const float4 si = sl[i];
-    const uint4 w = philox(make_uint4(j, sweep, lattice_id32(g, lat), ctr_w(TAG_HEIS, (uint32_t)colour, 0)), rk);
-    const float4 n = unit_vector(w.x, w.y);
+    const float4 n = unit_vector<kFast>(w.x, w.y);
     const float u3 = uniform24(w.z);
     const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
-    const float beta = __uint_as_float(__ldg(thr + 4 * slot_of32(g, lat)));
-    if (dE <= 0.0f || u3 < expf(-beta * dE)) sl[i] = n;
+    const float boltz = kFast ? __expf(-beta * dE) : expf(-beta * dE);
+    if (dE <= 0.0f || u3 < boltz) sl[i] = n;
   }
 }
 
@@ -103,9 +121,14 @@ cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
   const uint32_t half = (uint32_t)(h->n_lat * (h->g.N / 2));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
-    for (int colour = 0; colour < 2; ++colour)
-      heis_phase_kernel<<<capped_grid(half), 256, 0, h->stream>>>((float4 *)h->spins, h->g, half,
-                                                                  h->d_thr, rk, sweep, colour);
+    for (int colour = 0; colour < 2; ++colour) {
+      if (h->variant == 2)
+        heis_phase_kernel<true><<<capped_grid(half), 256, 0, h->stream>>>(
+            (float4 *)h->spins, h->g, half, h->d_thr, rk, sweep, colour);
+      else
+        heis_phase_kernel<false><<<capped_grid(half), 256, 0, h->stream>>>(
+            (float4 *)h->spins, h->g, half, h->d_thr, rk, sweep, colour);
+    }
     if ((sweep + 1u) % 100u == 0u)
       heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>(
           (float4 *)h->spins, h->n_lat * h->g.N);

@@ -33,6 +33,10 @@ struct spin_lattice {
   int *d_err;            // device error word
   void *d_pingpong;      // lattice-sized buffer of the fused 2D sweep (lazy)
   size_t pingpong_bytes;
+  // batched launches (options set with spin_set_batch_options)
+  uint64_t batch_timeout_ns;  // bound on every team-barrier wait (0: 2 s)
+  int batch_ctas_per_sm;      // 0: autotuned / default
+  int batch_fault_extra;      // arrivals a barrier waits for that never come (tests)
 };
 
 namespace spin {

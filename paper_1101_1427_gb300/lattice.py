@@ -92,6 +92,26 @@ class Lattice:
                    accepted)
         return out
 
+    def series_buffers(self, n_meas):
+        """Device tensors for n_meas measurements (as filled by run / batch)."""
+        out = {}
+        if self.model == B.SPIN_HEISENBERG:
+            return out
+        out["E"] = torch.zeros(n_meas * self.n_lat, dtype=torch.int64, device=self.device)
+        out["M"] = torch.zeros(n_meas * self.n_lat, dtype=torch.int64, device=self.device)
+        if self.n_sets >= 2:
+            out["Q"] = torch.zeros(n_meas * self.n_temps * self.n_real, dtype=torch.int64,
+                                   device=self.device)
+        return out
+
+    def batch_item(self, betas, series=None, accepted=None):
+        it = {"lat": self.h, "couplings": self.couplings, "betas": list(betas)}
+        if series:
+            it.update(series)
+        if accepted is not None:
+            it["accepted"] = accepted
+        return it
+
     def unpack(self):
         """Spins as int8 +-1, shape [n_sets, n_temps, n_real, N] (I8 / MSC1)."""
         out = torch.empty(self.n_lat * self.N, dtype=torch.int8, device=self.device)
@@ -128,3 +148,9 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+def batch_run(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
+    """One batched persistent launch over several lattices (see spin_batch_run)."""
+    stream = stream or torch.cuda.current_stream()
+    B.spin_batch_run(items, n_sweeps, measure_every, pt_every, stream.cuda_stream)

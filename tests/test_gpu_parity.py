@@ -223,12 +223,14 @@ def test_heis_init_close_to_oracle():
     assert np.max(np.abs(got[:, :3] - ref)) < 1e-6 and np.all(got[:, 3] == 0)
 
 
-def test_heis_one_sweep_within_tolerance():
+@pytest.mark.parametrize("variant", [0, 2])
+def test_heis_one_sweep_within_tolerance(variant):
     """Same FP32 start for both; after one sweep every site agrees to 1e-5,
     except sites whose accept/reject margin |u3 - exp(-beta dE)| is below 1e-5
     in the FP64 oracle and the later-updated neighbours of such sites."""
     L, seed, beta = 16, 8, 0.693
     lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=seed)
+    lat.set_variant(variant)
     s0 = oracle.heis_init(3, L, seed, 0).astype(np.float32)
     dev = np.zeros((L ** 3, 4), np.float32)
     dev[:, :3] = s0
@@ -251,9 +253,11 @@ def test_heis_one_sweep_within_tolerance():
     assert (err > 1e-5).sum() <= 20
 
 
-def test_heis_renormalisation_bound():
+@pytest.mark.parametrize("variant", [0, 2])
+def test_heis_renormalisation_bound(variant):
     L = 16
     lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=4)
+    lat.set_variant(variant)
     lat.sweep([0.693], 100)
     v = host(lat.spins).reshape(-1, 4)[:, :3].astype(np.float64)
     assert np.max(np.abs(np.linalg.norm(v, axis=1) - 1)) <= 1e-6

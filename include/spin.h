@@ -203,6 +203,27 @@ int spin_rng_fill(uint64_t seed, uint32_t tag, uint32_t colour, uint32_t extra,
  * threads * calls must stay below 2^32. */
 int spin_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out, void *stream);
 
+/* Heisenberg energy and magnetisation (as Ef and Mf of spin_measure) for
+ * callers that cannot allocate device memory.  The paper has no counterpart;
+ * this entry point exists for library users: code inside a framework that
+ * owns the whole device-memory pool (a raw cudaMalloc there fails or
+ * fragments the pool) and code that must not stall the device (cudaFree, and
+ * often cudaMalloc, synchronise it).  It needs no handle: spins is a device
+ * float4 array [n_lat][L^3] (16-byte aligned), Ef [n_lat] and Mf [n_lat][3]
+ * are caller-owned device outputs (NULL to skip); work runs on `stream`.
+ * Partial sums live in one fixed array compiled into the library:
+ * 256 lattices x 64 blocks x 4 doubles = 512 KiB on every GPU that loads the
+ * library, held until process exit.  n_lat > 256 (or n_lat L^3 >= 2^31) is
+ * rejected with SPIN_EINVAL; nothing is allocated, neither by this call nor
+ * by any library routine it uses.  The first call on a device looks up the
+ * array's device address (one-time set-up per device); make that first call
+ * before any stream capture.  Every call overwrites the partial sums before
+ * reading them, so no state has to be cleared between calls, but all calls
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams without ordering) race and give wrong sums. */
+int spin_heis_measure_noalloc(const float *spins, int32_t L, int32_t n_lat, double *Ef, double *Mf,
+                              void *stream);
+
 /* Waits for the handle's stream and reports asynchronous failures
  * (SPIN_ECUDA, SPIN_ETIMEOUT).  Clears the device error word. */
 int spin_sync(spin_lattice *lat);

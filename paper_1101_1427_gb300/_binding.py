@@ -56,6 +56,7 @@ def lib():
         L.spin_rng_fill.argtypes = [u64, u32, u32, u32, u32, u32, u64, p, p]
         L.spin_rng_probe.argtypes = [u64, u32, u32, p, p]
         L.spin_sync.argtypes = [p]
+        L.spin_heis_measure_noalloc.argtypes = [p, i32, i32, p, p, p]
         L.spin_batch_run.argtypes = [p, C.c_int, i64, i32, i32, p]
         L.spin_batch_tune.argtypes = [p, C.c_int, i64, i32, i32, p, p]
         L.spin_set_batch_options.argtypes = [p, u64, i32, i32]
@@ -72,7 +73,7 @@ def lib():
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
-                     "spin_set_batch_options"):
+                     "spin_set_batch_options", "spin_heis_measure_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -186,6 +187,13 @@ def spin_batch_tune(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
 def spin_set_batch_options(h, timeout_ns=0, ctas_per_sm=0, missing_arrivals=0):
     return _check(lib().spin_set_batch_options(h, timeout_ns, ctas_per_sm, missing_arrivals),
                   "spin_set_batch_options")
+
+
+def spin_heis_measure_noalloc(spins, L, n_lat, Ef=None, Mf=None, stream=None):
+    """Heisenberg E and M into caller-owned tensors without any device
+    allocation (the partial sums use a fixed array inside the library)."""
+    return _check(lib().spin_heis_measure_noalloc(_ptr(spins), L, n_lat, _ptr(Ef), _ptr(Mf), stream),
+                  "spin_heis_measure_noalloc")
 
 
 def spin_sync(h):

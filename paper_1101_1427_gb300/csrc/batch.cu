@@ -23,6 +23,7 @@
 #include <map>
 #include <vector>
 
+#include "ea_quad.cuh"
 #include "internal.h"
 
 namespace spin {
@@ -51,6 +52,7 @@ struct BatchUnit {
   long long *E_series, *M_series, *Q_series, *accepted;
   long long n_lat;      // lattices of the handle (series row length)
   int *Escr;            // [n_sets][n_T][32] unsatisfied-bond counts
+  FastDiv fqpr, fhalfL; // segment decoding (L % 8 == 0)
   // Ising
   int8_t *s;
   long long lat_index;
@@ -66,6 +68,7 @@ constexpr int kMaxHandles = 16;
 struct BatchParams {
   int n_units;
   int measure_every, pt_every, extra;
+  uint32_t staged_words;  // dynamic shared memory for couplings, in words
   int64_t n_sweeps;
   uint64_t timeout_ns;
   RoundKeys keys[kMaxHandles];
@@ -156,6 +159,12 @@ __device__ __forceinline__ void add1(uint32_t (&C)[kPl], uint32_t x) {
   }
 }
 
+struct Add3 {
+  __device__ void operator()(uint32_t (&C)[kPl], uint32_t x0, uint32_t x1, uint32_t x2) const {
+    add3(C, x0, x1, x2);
+  }
+};
+
 // Sum of the per-lane counters of a warp; every lane returns the count of
 // realisation bit `lane`.
 __device__ __forceinline__ int warp_bit_counts(const uint32_t (&C)[kPl]) {
@@ -194,6 +203,17 @@ __device__ __forceinline__ void ea_phase_warp(uint32_t *__restrict__ s, const ui
   const uint32_t L = (uint32_t)U.L, LL = L * L, N = U.N;
   const uint32_t quads = N / 8;
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  if ((L & 7u) == 0) {
+    for (uint32_t qk = first; qk < quads; qk += stride) {
+      const QuadPos qp = quad_pos(qk, L, U.fqpr, U.fhalfL);
+      const uint4 r = philox(make_uint4(qp.i0 >> 3, sweep, lid, wctr), rk);
+      if ((colour + qp.cls) & 1)
+        ea_quad_update<1, kCount>(s, Jg, N, L, qp, r, t4, t8, t12, C, Add3());
+      else
+        ea_quad_update<0, kCount>(s, Jg, N, L, qp, r, t4, t8, t12, C, Add3());
+    }
+    return;
+  }
   for (uint32_t j4 = first; j4 < quads; j4 += stride) {
     const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
 #pragma unroll
@@ -239,8 +259,9 @@ __device__ __forceinline__ void ea_phase_warp(uint32_t *__restrict__ s, const ui
 }
 
 // ---------------------------------------------------------------- EA unit
-__device__ bool ea_sweep(const BatchUnit &U, int part, const RoundKeys &rk, Sync &sy, uint32_t s_abs,
-                         bool measure, bool pt, long long meas_row, uint32_t pt_step) {
+__device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, const RoundKeys &rk,
+                         Sync &sy, uint32_t s_abs, bool measure, bool pt, long long meas_row,
+                         uint32_t pt_step) {
   __shared__ int e_cnt[64][32];   // per owned word-lattice (set, slot) counts
   __shared__ uint32_t masks[64];  // accept masks per (set, owned pair)
   const int P = U.team_size;
@@ -266,12 +287,12 @@ __device__ bool ea_sweep(const BatchUnit &U, int part, const RoundKeys &rk, Sync
 #pragma unroll
       for (int k = 0; k < kPl; ++k) C[k] = 0;
       if (colour == 1 && need_e) {
-        ea_phase_warp<true>(s, U.J, U, rk, s_abs, lid, 1, t4, t8, t12, first, stride, C);
+        ea_phase_warp<true>(s, Jsrc, U, rk, s_abs, lid, 1, t4, t8, t12, first, stride, C);
         const int cnt = warp_bit_counts(C);
         if (wpw == 1) e_cnt[wi][lane] = cnt;
         else atomicAdd(&e_cnt[wi][lane], cnt);
       } else {
-        ea_phase_warp<false>(s, U.J, U, rk, s_abs, lid, colour, t4, t8, t12, first, stride, C);
+        ea_phase_warp<false>(s, Jsrc, U, rk, s_abs, lid, colour, t4, t8, t12, first, stride, C);
       }
     }
     __syncthreads();
@@ -452,6 +473,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                                                          unsigned *bar, int *err) {
   __shared__ BatchUnit U;
   __shared__ RoundKeys rk;
+  extern __shared__ __align__(16) uint32_t sJ[];  // couplings of an EA unit, when staged
   // CTA -> unit: teams are consecutive CTA ranges in unit order
   int lo = 0, hi = prm.n_units - 1;
   while (lo < hi) {
@@ -467,6 +489,14 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
   __syncthreads();
   const int part = (int)blockIdx.x - U.team_first;
   Sync sy{bar + u, 0u, U.team_size, err, prm.timeout_ns, prm.extra};
+  // the couplings never change during a launch: stage them once if they fit
+  const uint32_t *Jsrc = U.J;
+  if (U.kind == 0 && 3u * U.N <= prm.staged_words) {
+    for (uint32_t k = threadIdx.x; k < 3u * U.N / 4u; k += blockDim.x)
+      reinterpret_cast<uint4 *>(sJ)[k] = __ldg(reinterpret_cast<const uint4 *>(U.J) + k);
+    __syncthreads();
+    Jsrc = sJ;
+  }
   long long meas_row = 0;
   uint32_t pt_step = U.pt0;
   for (int64_t k = 0; k < prm.n_sweeps; ++k) {
@@ -475,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     const bool pt = prm.pt_every > 0 && ((s_abs + 1u) % (uint32_t)prm.pt_every) == 0u;
     bool ok;
     if (U.kind == 0)
-      ok = ea_sweep(U, part, rk, sy, s_abs, measure, pt, meas_row, pt_step);
+      ok = ea_sweep(U, Jsrc, part, rk, sy, s_abs, measure, pt, meas_row, pt_step);
     else
       ok = ising_sweep(U, part, rk, sy, s_abs, measure, meas_row);
     if (!ok) return;
@@ -587,6 +617,8 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.accepted = (long long *)items[k].accepted;
         U.n_lat = h->n_lat;
         U.Escr = (int *)(uintptr_t)escr_words;  // offset into the workspace
+        U.fqpr = g.fqpr;
+        U.fhalfL = g.fhalfL;
         escr_words += (size_t)g.n_sets * g.n_temps * 32;
       }
     } else {
@@ -630,6 +662,7 @@ static cudaError_t batch_launch(BatchParams &prm, int grid, cudaStream_t st, int
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)prm.staged_words * 4;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -670,11 +703,23 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
   spin_lattice *h0 = items[0].lat;
   prm.timeout_ns = h0->batch_timeout_ns ? h0->batch_timeout_ns : 2000000000ull;
   prm.extra = h0->batch_fault_extra;
+  // couplings of EA units with 3N <= 12288 words (48 KiB) are staged in
+  // shared memory for the whole launch
+  prm.staged_words = 0;
+  for (int u = 0; u < prm.n_units; ++u)
+    if (prm.units[u].kind == 0 && 3u * prm.units[u].N <= 12288u)
+      prm.staged_words = std::max(prm.staged_words, 3u * prm.units[u].N);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 4);
+    attr = true;
+  }
   // co-resident grid
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads,
+                                                    (size_t)prm.staged_words * 4) != cudaSuccess ||
       per_sm < 1)
     return SPIN_ECUDA;
   // workspace (allocated on first use or growth only)

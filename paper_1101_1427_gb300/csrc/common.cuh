@@ -111,6 +111,8 @@ struct Geom {
   FastDiv fquads;  // division by (N / 2 + 3) / 4
   FastDiv freal;   // division by n_real
   FastDiv ftemps;  // division by n_temps
+  FastDiv fqpr;    // division by L / 8 (segments per row; L % 8 == 0 only)
+  FastDiv fhalfL;  // division by L / 2
 };
 
 // Site of colour index j (colour c): i = 2j + parity, with its coordinates.

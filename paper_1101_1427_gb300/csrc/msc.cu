@@ -4,6 +4,7 @@
 // Coupling words [groups][3][L^3], bit set <=> J = -1.  The 32 realisations
 // of a word share one uniform per site and sweep (the paper's footnote to
 // Sec. 6), so one Philox call serves four word-sites.
+#include "ea_quad.cuh"
 #include "internal.h"
 
 namespace spin {
@@ -106,6 +107,79 @@ __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w
   }
 }
 
+// L % 8 == 0: one thread per quad (8-word row segment), quads enumerated
+// class by class so that the active parity is uniform across a warp.
+struct NoCount {
+  template <int K>
+  __device__ void operator()(uint32_t (&)[K], uint32_t, uint32_t, uint32_t) const {}
+};
+
+__global__ void __launch_bounds__(256) msc_phase_vec_kernel(uint32_t *__restrict__ w,
+                                                            const uint32_t *__restrict__ J, Geom g,
+                                                            uint32_t total,
+                                                            const uint32_t *__restrict__ thr,
+                                                            RoundKeys rk, uint32_t sweep,
+                                                            int colour) {
+  const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = N / 8;
+  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  uint32_t C[1] = {0};
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const uint32_t wl = fdiv(k, g.fquads), qk = k - wl * quads;
+    const uint32_t t = wl % T, grp = (wl / T) % G, a = wl / (T * G);
+    const QuadPos qp = quad_pos(qk, L, g.fqpr, g.fhalfL);
+    const uint4 r = philox(make_uint4(qp.i0 >> 3, sweep, lattice_id(a, grp, t), wctr), rk);
+    const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
+    uint32_t *s = w + (size_t)wl * N;
+    const uint32_t *Jg = J + (size_t)grp * 3 * N;
+    if ((colour + qp.cls) & 1)
+      ea_quad_update<1, false>(s, Jg, N, L, qp, r, t4, t8, t12, C, NoCount());
+    else
+      ea_quad_update<0, false>(s, Jg, N, L, qp, r, t4, t8, t12, C, NoCount());
+  }
+}
+
+// Shared-memory form for small lattices (3 N words of couplings fit): CTA
+// (group, set, chunk of kTpc slots) stages the group's couplings once, then
+// updates its word-lattices quad by quad.  Couplings are the same for every
+// set and slot of a group, so they leave L2 once per CTA instead of once per
+// word-lattice.
+constexpr int kTpc = 8;
+
+__global__ void __launch_bounds__(256) msc_phase_smem_kernel(uint32_t *__restrict__ w,
+                                                             const uint32_t *__restrict__ J, Geom g,
+                                                             const uint32_t *__restrict__ thr,
+                                                             RoundKeys rk, uint32_t sweep,
+                                                             int colour) {
+  extern __shared__ __align__(16) uint32_t sJ[];
+  const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = N / 8;
+  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
+  const uint32_t chunks = (T + kTpc - 1) / kTpc;
+  const uint32_t c = blockIdx.x % chunks, a = (blockIdx.x / chunks) % (uint32_t)g.n_sets;
+  const uint32_t grp = blockIdx.x / (chunks * (uint32_t)g.n_sets);
+  const uint32_t *Jg = J + (size_t)grp * 3 * N;
+  for (uint32_t k = threadIdx.x; k < 3 * N / 4; k += blockDim.x)
+    reinterpret_cast<uint4 *>(sJ)[k] = __ldg(reinterpret_cast<const uint4 *>(Jg) + k);
+  __syncthreads();
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  uint32_t C[1] = {0};
+  const uint32_t t0 = c * kTpc, t1 = min(T, t0 + kTpc);
+  for (uint32_t t = t0; t < t1; ++t) {
+    const uint32_t wl = (a * G + grp) * T + t;
+    uint32_t *s = w + (size_t)wl * N;
+    const uint32_t lid = lattice_id(a, grp, t);
+    const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
+    for (uint32_t qk = threadIdx.x; qk < quads; qk += blockDim.x) {
+      const QuadPos qp = quad_pos(qk, L, g.fqpr, g.fhalfL);
+      const uint4 r = philox(make_uint4(qp.i0 >> 3, sweep, lid, wctr), rk);
+      if ((colour + qp.cls) & 1)
+        ea_quad_update<1, false>(s, sJ, N, L, qp, r, t4, t8, t12, C, NoCount());
+      else
+        ea_quad_update<0, false>(s, sJ, N, L, qp, r, t4, t8, t12, C, NoCount());
+    }
+  }
+}
+
 // words -> one int8 per spin, [n_sets][n_temps][n_real][N]
 __global__ void unpack_msc_kernel(const uint32_t *__restrict__ w, int8_t *__restrict__ out, Geom g) {
   const int G = g.n_real / 32;
@@ -172,9 +246,24 @@ cudaError_t launch_sweeps_msc_ea(spin_lattice *h, const uint32_t *J, int64_t n_s
   const uint32_t work = (uint32_t)(n_wl * ((g.N / 2 + 3) / 4));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
-    for (int colour = 0; colour < 2; ++colour)
-      msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
-                                                            h->d_thr, rk, sweep, colour);
+    for (int colour = 0; colour < 2; ++colour) {
+      const size_t smem = (size_t)12 * g.N;  // 3 N coupling words
+      if (g.L % 8 == 0 && smem <= 96 * 1024) {
+        static bool attr = false;
+        if (!attr) {
+          cudaFuncSetAttribute(msc_phase_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+          attr = true;
+        }
+        const unsigned ctas = (unsigned)((g.n_real / 32) * g.n_sets * ((g.n_temps + kTpc - 1) / kTpc));
+        msc_phase_smem_kernel<<<ctas, 256, smem, h->stream>>>((uint32_t *)h->spins, J, g, h->d_thr, rk,
+                                                              sweep, colour);
+      } else if (g.L % 8 == 0)
+        msc_phase_vec_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
+                                                                  h->d_thr, rk, sweep, colour);
+      else
+        msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
+                                                              h->d_thr, rk, sweep, colour);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

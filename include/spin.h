@@ -59,8 +59,10 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *  SPIN_I8     int8 +-1, [n_sets][n_temps][n_real][L^dim].  Ising (2D, 3D) and
  *              EA (3D, one spin per byte: the per-realisation form).
  *  SPIN_MSC1   1 bit per spin, bit set <=> s = -1, uint32 words.
- *              EA (3D, asynchronous coding, Sec. 6): [n_sets][n_real/32]
- *              [n_temps][L^3]; bit b of a word is realisation 32 g + b.
+ *              EA (3D, asynchronous coding, Sec. 6): word-lattices
+ *              [n_sets][n_real/32][n_temps], each stored colour-split as
+ *              [2 colours][L^3/2] (site i of colour c at c L^3/2 + (i >> 1));
+ *              bit b of a word is realisation 32 g + b.
  *              Ising 2D ferromagnet (synchronous coding): per lattice
  *              [2 colours][L rows][L/64 words]; in row y the colour-c sites
  *              x = 2k + ((c + y) & 1) are grouped in blocks of 128 k's, and
@@ -68,7 +70,8 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *  SPIN_F32X4  float4 (x, y, z, 0) unit vectors, [n_sets][n_temps][n_real][L^3].
  * Couplings (EA only; NULL for the ferromagnet, J = 1):
  *  SPIN_I8     int8 +-1, [n_real][dim][L^dim]: bond (i, i + e_d).
- *  SPIN_MSC1   uint32 [n_real/32][dim][L^dim], bit b set <=> J = -1 for
+ *  SPIN_MSC1   uint32 [n_real/32][dim][2 colours][L^3/2] (bond (i, i + e_d)
+ *              at d L^3 + c(i) L^3/2 + (i >> 1)), bit b set <=> J = -1 for
  *              realisation 32 g + b.
  * All device buffers must be 16-byte aligned. */
 typedef enum { SPIN_I8 = 0, SPIN_MSC1 = 1, SPIN_F32X4 = 2 } spin_layout;

@@ -23,7 +23,7 @@
 #include <map>
 #include <vector>
 
-#include "ea_quad.cuh"
+#include "ea_cs.cuh"
 #include "internal.h"
 
 namespace spin {
@@ -52,7 +52,6 @@ struct BatchUnit {
   long long *E_series, *M_series, *Q_series, *accepted;
   long long n_lat;      // lattices of the handle (series row length)
   int *Escr;            // [n_sets][n_T][32] unsatisfied-bond counts
-  FastDiv fqpr, fhalfL; // segment decoding (L % 8 == 0)
   // Ising
   int8_t *s;
   long long lat_index;
@@ -159,11 +158,86 @@ __device__ __forceinline__ void add1(uint32_t (&C)[kPl], uint32_t x) {
   }
 }
 
-struct Add3 {
-  __device__ void operator()(uint32_t (&C)[kPl], uint32_t x0, uint32_t x1, uint32_t x2) const {
-    add3(C, x0, x1, x2);
+// counter planes += bit-plane x of weight 2^w (w > 0), ripple from level w
+template <int W>
+__device__ __forceinline__ void add_at(uint32_t (&C)[kPl], uint32_t x) {
+#pragma unroll
+  for (int k = W; k < kPl; ++k) {
+    const uint32_t n = C[k] & x;
+    C[k] ^= x;
+    x = n;
+  }
+}
+
+// carry-save adder: (h, l) = 2h + l = a + b + c per bit
+__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t u = a ^ b;
+  h = (a & b) | (u & c);
+  l = u ^ c;
+}
+
+// Harley-Seal counting of 1-bit planes: eight planes go through seven
+// carry-save adders into (ones, twos, fours) and one plane of weight 8,
+// which is rippled into the counter; flush() adds the remainders.
+struct HsCount {
+  uint32_t C[kPl];
+  uint32_t ones, twos, fours;
+  __device__ HsCount() : ones(0), twos(0), fours(0) {
+#pragma unroll
+    for (int k = 0; k < kPl; ++k) C[k] = 0;
+  }
+  __device__ __forceinline__ void add8(const uint32_t (&x)[8]) {
+    uint32_t twosA, twosB, foursA, foursB, eights;
+    csa(twosA, ones, ones, x[0], x[1]);
+    csa(twosB, ones, ones, x[2], x[3]);
+    csa(foursA, twos, twos, twosA, twosB);
+    csa(twosA, ones, ones, x[4], x[5]);
+    csa(twosB, ones, ones, x[6], x[7]);
+    csa(foursB, twos, twos, twosA, twosB);
+    csa(eights, fours, fours, foursA, foursB);
+    add_at<3>(C, eights);
+  }
+  __device__ __forceinline__ void flush() {
+    add_at<2>(C, fours);
+    add_at<1>(C, twos);
+    add1(C, ones);
+    ones = twos = fours = 0;
   }
 };
+
+// counter planes += the sum of four 3-bit values (a_k0 + 2 a_k1 + 4 a_k2),
+// formed first by a small adder tree (at most 24, five bits)
+__device__ __forceinline__ void add_quad(uint32_t (&C)[kPl], const uint32_t (&a)[4][3]) {
+  // s = a0 + a1 and t = a2 + a3 (4 bits each)
+  uint32_t s[4], t[4];
+  {
+    uint32_t c = a[0][0] & a[1][0];
+    s[0] = a[0][0] ^ a[1][0];
+    csa(c, s[1], a[0][1], a[1][1], c);
+    csa(s[3], s[2], a[0][2], a[1][2], c);
+  }
+  {
+    uint32_t c = a[2][0] & a[3][0];
+    t[0] = a[2][0] ^ a[3][0];
+    csa(c, t[1], a[2][1], a[3][1], c);
+    csa(t[3], t[2], a[2][2], a[3][2], c);
+  }
+  // v = s + t (5 bits)
+  uint32_t v[5], c = s[0] & t[0];
+  v[0] = s[0] ^ t[0];
+  csa(c, v[1], s[1], t[1], c);
+  csa(c, v[2], s[2], t[2], c);
+  csa(v[4], v[3], s[3], t[3], c);
+  // counter += v
+  uint32_t carry = 0;
+#pragma unroll
+  for (int k = 0; k < kPl; ++k) {
+    const uint32_t x = k < 5 ? v[k] : 0u;
+    const uint32_t n = (C[k] & x) | (carry & (C[k] ^ x));
+    C[k] = C[k] ^ x ^ carry;
+    carry = n;
+  }
+}
 
 // Sum of the per-lane counters of a warp; every lane returns the count of
 // realisation bit `lane`.
@@ -194,68 +268,58 @@ __device__ __forceinline__ int warp_bit_counts(const uint32_t (&C)[kPl]) {
 // unsatisfied bonds of each updated (colour-1) site is added to C: every
 // bond joins a colour-0 and a colour-1 site, so summing over colour-1 sites
 // counts each bond once.
+// Collects the post-update counts of the (up to) four sites of a quad and
+// adds them to the counter in one go.
+struct AddTo {
+  uint32_t (&C)[kPl];
+  uint32_t (&buf)[4][3];
+  int &n;
+  __device__ void operator()(uint32_t x0, uint32_t x1, uint32_t x2) const {
+    buf[n][0] = x0;
+    buf[n][1] = x1;
+    buf[n][2] = x2;
+    if (++n == 4) {
+      add_quad(C, buf);
+      n = 0;
+    }
+  }
+};
+
+// One colour phase of one word-lattice (colour-split) by `stride` threads,
+// quads first, first + stride, ...  With kCount the post-update number of
+// unsatisfied bonds of each updated (colour-1) site is added to C: every
+// bond joins a colour-0 and a colour-1 site, so summing over colour-1 sites
+// counts each bond once.
 template <bool kCount>
 __device__ __forceinline__ void ea_phase_warp(uint32_t *__restrict__ s, const uint32_t *__restrict__ Jg,
                                               const BatchUnit &U, const RoundKeys &rk, uint32_t sweep,
                                               uint32_t lid, int colour, uint32_t t4, uint32_t t8,
                                               uint32_t t12, uint32_t first, uint32_t stride,
                                               uint32_t (&C)[kPl]) {
-  const uint32_t L = (uint32_t)U.L, LL = L * L, N = U.N;
-  const uint32_t quads = N / 8;
+  const uint32_t quads = (U.N / 2 + 3) / 4;
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
-  if ((L & 7u) == 0) {
-    for (uint32_t qk = first; qk < quads; qk += stride) {
-      const QuadPos qp = quad_pos(qk, L, U.fqpr, U.fhalfL);
-      const uint4 r = philox(make_uint4(qp.i0 >> 3, sweep, lid, wctr), rk);
-      if ((colour + qp.cls) & 1)
-        ea_quad_update<1, kCount>(s, Jg, N, L, qp, r, t4, t8, t12, C, Add3());
-      else
-        ea_quad_update<0, kCount>(s, Jg, N, L, qp, r, t4, t8, t12, C, Add3());
-    }
-    return;
-  }
+  uint32_t buf[4][3];
+  int n = 0;
   for (uint32_t j4 = first; j4 < quads; j4 += stride) {
     const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
-#pragma unroll
-    for (uint32_t q = 0; q < 4; ++q) {
-      const uint32_t j = 4 * j4 + q;
-      const uint32_t i0 = 2u * j;
-      const uint32_t row = fdiv(i0, U.fL);
-      const uint32_t x0 = i0 - row * L;
-      const uint32_t z = fdiv(row, U.fL), y = row - z * L;
-      const uint32_t x = x0 + ((colour + y + z) & 1u);
-      const uint32_t rowbase = i0 - x0, i = rowbase + x;
-      const uint32_t ixp = rowbase + (x == L - 1 ? 0 : x + 1);
-      const uint32_t ixm = rowbase + (x == 0 ? L - 1 : x - 1);
-      const uint32_t iyp = y == L - 1 ? i - (L - 1) * L : i + L;
-      const uint32_t iym = y == 0 ? i + (L - 1) * L : i - L;
-      const uint32_t izp = z == L - 1 ? i - (L - 1) * LL : i + LL;
-      const uint32_t izm = z == 0 ? i + (L - 1) * LL : i - LL;
-      const uint32_t S = s[i];
-      const uint32_t u0 = S ^ s[ixp] ^ Jg[i];
-      const uint32_t u1 = S ^ s[ixm] ^ Jg[ixm];
-      const uint32_t u2 = S ^ s[iyp] ^ Jg[N + i];
-      const uint32_t u3 = S ^ s[iym] ^ Jg[N + iym];
-      const uint32_t u4 = S ^ s[izp] ^ Jg[2 * N + i];
-      const uint32_t u5 = S ^ s[izm] ^ Jg[2 * N + izm];
-      const uint32_t s1 = u0 ^ u1 ^ u2, c1 = (u0 & u1) | (u2 & (u0 ^ u1));
-      const uint32_t s2 = u3 ^ u4 ^ u5, c2 = (u3 & u4) | (u5 & (u3 ^ u4));
-      const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
-      const uint32_t b1 = c1 ^ c2 ^ c3, b2 = (c1 & c2) | (c3 & (c1 ^ c2));
-      const uint32_t rq = word_of(r, q);
-      const uint32_t R4 = rq < t4 ? ~0u : 0u, R8 = rq < t8 ? ~0u : 0u, R12 = rq < t12 ? ~0u : 0u;
-      const uint32_t ge3 = b2 | (b1 & b0);
-      const uint32_t eq2 = ~b2 & b1 & ~b0, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
-      const uint32_t F = ge3 | (eq2 & R4) | (eq1 & R8) | (eq0 & R12);
-      s[i] = S ^ F;
-      if (kCount) {
-        // a flip turns u unsatisfied bonds into 6 - u: bit 0 is unchanged
-        const uint32_t v1 = (b2 & ~b1 & ~b0) | (~b2 & ~(b1 ^ b0));
-        const uint32_t v2 = ~b2 & ~(b1 & b0);
-        add3(C, b0, (F & v1) | (~F & b1), (F & v2) | (~F & b2));
-      }
-    }
+    ea_cs_quad<kCount>(s, Jg, j4, colour, (uint32_t)U.L, U.N, U.fL, r, t4, t8, t12, AddTo{C, buf, n});
   }
+  if (kCount)  // a last, partial quad (N/2 not a multiple of 4)
+    for (int k = 0; k < n; ++k) add3(C, buf[k][0], buf[k][1], buf[k][2]);
+}
+
+// Counts per bit the words a[i] (or a[i] ^ b[i]) for i = lane, lane + 32, ...
+__device__ __forceinline__ void count_words(HsCount &hc, const uint32_t *a, const uint32_t *b, uint32_t N,
+                                            int lane) {
+  uint32_t i = (uint32_t)lane;
+  for (; i + 7 * 32 < N; i += 8 * 32) {
+    uint32_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = b ? (a[i + 32 * k] ^ b[i + 32 * k]) : a[i + 32 * k];
+    hc.add8(x);
+  }
+  hc.flush();
+  for (; i < N; i += 32) add1(hc.C, b ? (a[i] ^ b[i]) : a[i]);
 }
 
 // ---------------------------------------------------------------- EA unit
@@ -317,14 +381,12 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
       const bool do_m = (wi & 1) == 0;
       if (do_m && !U.M_series) continue;
       if (!do_m && (!U.Q_series || U.n_sets < 2)) continue;
-      uint32_t C[kPl];
-#pragma unroll
-      for (int k = 0; k < kPl; ++k) C[k] = 0;
+      HsCount hc;
       // (M is accumulated for set 0 only here; other sets below)
       const uint32_t *s0 = U.w + (size_t)t * N;
       const uint32_t *s1 = s0 + U.set_stride;
-      for (uint32_t i = lane; i < N; i += 32) add1(C, do_m ? s0[i] : (s0[i] ^ s1[i]));
-      const int cnt = warp_bit_counts(C);
+      count_words(hc, s0, do_m ? nullptr : s1, N, lane);
+      const int cnt = warp_bit_counts(hc.C);
       const long long r = 32 * U.grp + lane;
       if (do_m) U.M_series[meas_row * U.n_lat + (long long)t * U.n_real + r] = (long long)N - 2LL * cnt;
       else U.Q_series[meas_row * (long long)U.n_T * U.n_real + (long long)t * U.n_real + r] = (long long)N - 2LL * cnt;
@@ -333,12 +395,10 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
       for (int a = 1; a < U.n_sets; ++a)
         for (int wi = warp; wi < nt_own; wi += kWarps) {
           const int t = t0 + wi;
-          uint32_t C[kPl];
-#pragma unroll
-          for (int k = 0; k < kPl; ++k) C[k] = 0;
+          HsCount hc;
           const uint32_t *sa = U.w + a * U.set_stride + (size_t)t * N;
-          for (uint32_t i = lane; i < N; i += 32) add1(C, sa[i]);
-          const int cnt = warp_bit_counts(C);
+          count_words(hc, sa, nullptr, N, lane);
+          const int cnt = warp_bit_counts(hc.C);
           U.M_series[meas_row * U.n_lat + ((long long)a * U.n_T + t) * U.n_real + 32 * U.grp + lane] =
               (long long)N - 2LL * cnt;
         }
@@ -617,8 +677,6 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.accepted = (long long *)items[k].accepted;
         U.n_lat = h->n_lat;
         U.Escr = (int *)(uintptr_t)escr_words;  // offset into the workspace
-        U.fqpr = g.fqpr;
-        U.fhalfL = g.fhalfL;
         escr_words += (size_t)g.n_sets * g.n_temps * 32;
       }
     } else {

@@ -111,9 +111,18 @@ struct Geom {
   FastDiv fquads;  // division by (N / 2 + 3) / 4
   FastDiv freal;   // division by n_real
   FastDiv ftemps;  // division by n_temps
-  FastDiv fqpr;    // division by L / 8 (segments per row; L % 8 == 0 only)
-  FastDiv fhalfL;  // division by L / 2
 };
+
+// Colour (x + y + z) mod 2 of site i.
+__device__ __forceinline__ uint32_t colour_of(const Geom &g, uint32_t i) {
+  const uint32_t row = fdiv(i, g.fL);
+  const uint32_t x = i - row * (uint32_t)g.L;
+  if (g.dim == 3) {
+    const uint32_t z = fdiv(row, g.fL);
+    return (x + (row - z * (uint32_t)g.L) + z) & 1u;
+  }
+  return (x + row) & 1u;
+}
 
 // Site of colour index j (colour c): i = 2j + parity, with its coordinates.
 struct Site {

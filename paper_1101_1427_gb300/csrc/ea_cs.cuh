@@ -1,0 +1,167 @@
+// +-J EA glass, asynchronous multi-spin coding, colour-split storage.
+//
+// A word-lattice (one replica set, one realisation group of 32, one slot)
+// stores its N = L^3 words as [colour][N/2]: site i of colour c sits at
+// c N/2 + (i >> 1), i.e. at its colour index j = i >> 1.  Couplings of a
+// group are stored as [direction][colour][N/2]: the bond (i, i + e_d) at
+// d N + c(i) N/2 + (i >> 1).  During a colour phase the updated words, their
+// six neighbours (all of the other colour) and the couplings are then
+// contiguous across consecutive colour indices, so the lanes of a warp read
+// whole cache lines.
+#pragma once
+#include "common.cuh"
+
+namespace spin {
+
+__host__ __device__ __forceinline__ uint32_t cs_word(uint32_t i, uint32_t colour, uint32_t half) {
+  return colour * half + (i >> 1);
+}
+
+// Geometry of colour index j (colour c): site i and the linear indices of
+// its six neighbours.
+struct CsSite {
+  uint32_t i, rb, xp, xm, yp, ym, zp, zm;  // rb: first site of the row
+};
+
+__device__ __forceinline__ CsSite cs_site(uint32_t j, int colour, uint32_t L, const FastDiv &fL) {
+  const uint32_t LL = L * L;
+  const uint32_t i0 = 2u * j;
+  const uint32_t row = fdiv(i0, fL);
+  const uint32_t x0 = i0 - row * L;
+  const uint32_t z = fdiv(row, fL), y = row - z * L;
+  const uint32_t x = x0 + ((colour + y + z) & 1u);
+  const uint32_t rb = i0 - x0, i = rb + x;
+  CsSite s;
+  s.i = i;
+  s.rb = rb;
+  s.xp = rb + (x == L - 1 ? 0 : x + 1);
+  s.xm = rb + (x == 0 ? L - 1 : x - 1);
+  s.yp = y == L - 1 ? i - (L - 1) * L : i + L;
+  s.ym = y == 0 ? i + (L - 1) * L : i - L;
+  s.zp = z == L - 1 ? i - (L - 1) * LL : i + LL;
+  s.zm = z == 0 ? i + (L - 1) * LL : i - LL;
+  return s;
+}
+
+// Metropolis flip mask of one word-site from its six bond words
+// u_k = s ^ s_nb ^ J (1 = unsatisfied) and the shared uniform r:
+// dE = 12 - 4u per realisation; flip iff u >= 3 or r < thr(dE).
+// Also returns the bit-sliced count (b0, b1, b2) of u.
+struct Flip {
+  uint32_t F, b0, b1, b2;
+};
+
+__device__ __forceinline__ Flip ea_flip(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, uint32_t u4,
+                                        uint32_t u5, uint32_t r, uint32_t t4, uint32_t t8, uint32_t t12) {
+  const uint32_t s1 = u0 ^ u1 ^ u2, c1 = (u0 & u1) | (u2 & (u0 ^ u1));
+  const uint32_t s2 = u3 ^ u4 ^ u5, c2 = (u3 & u4) | (u5 & (u3 ^ u4));
+  Flip f;
+  f.b0 = s1 ^ s2;
+  const uint32_t c3 = s1 & s2;
+  f.b1 = c1 ^ c2 ^ c3;
+  f.b2 = (c1 & c2) | (c3 & (c1 ^ c2));
+  const uint32_t R4 = r < t4 ? ~0u : 0u, R8 = r < t8 ? ~0u : 0u, R12 = r < t12 ? ~0u : 0u;
+  const uint32_t ge3 = f.b2 | (f.b1 & f.b0);
+  const uint32_t eq2 = ~f.b2 & f.b1 & ~f.b0, eq1 = ~f.b2 & ~f.b1 & f.b0, eq0 = ~(f.b2 | f.b1 | f.b0);
+  f.F = ge3 | (eq2 & R4) | (eq1 & R8) | (eq0 & R12);
+  return f;
+}
+
+// Post-update number of unsatisfied bonds (bit-sliced): a flip turns u into
+// 6 - u, whose bit 0 equals that of u.
+__device__ __forceinline__ void ea_after(const Flip &f, uint32_t &a0, uint32_t &a1, uint32_t &a2) {
+  const uint32_t v1 = (f.b2 & ~f.b1 & ~f.b0) | (~f.b2 & ~(f.b1 ^ f.b0));
+  const uint32_t v2 = ~f.b2 & ~(f.b1 & f.b0);
+  a0 = f.b0;
+  a1 = (f.F & v1) | (~f.F & f.b1);
+  a2 = (f.F & v2) | (~f.F & f.b2);
+}
+
+__device__ __forceinline__ uint4 ldv4(const uint32_t *p) {
+  uint4 v;
+  asm("ld.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
+// Update of the quad j = 4 j4 .. 4 j4 + 3 of colour `colour` in one
+// word-lattice w (colour-split) with group couplings J (colour-split).
+// Any even L: per-site neighbour indices.  add(a0, a1, a2) receives the
+// post-update count of each site when kCount.
+template <bool kCount, typename AddFn>
+__device__ __forceinline__ void ea_cs_quad(uint32_t *__restrict__ w, const uint32_t *__restrict__ J,
+                                           uint32_t j4, int colour, uint32_t L, uint32_t N,
+                                           const FastDiv &fL, uint4 r, uint32_t t4, uint32_t t8,
+                                           uint32_t t12, AddFn add) {
+  const uint32_t half = N >> 1;
+  const uint32_t oc = (uint32_t)colour ^ 1u;
+  uint32_t *own = w + (uint32_t)colour * half;
+  const uint32_t *oth = w + oc * half;
+  const uint32_t *Jx = J, *Jy = J + N, *Jz = J + 2 * N;
+  const uint32_t co = (uint32_t)colour * half, ot = oc * half;
+  if ((L & 7u) == 0) {
+    // the quad is 4 consecutive colour indices of one row: 16-byte loads
+    const uint32_t j0 = 4 * j4;
+    const CsSite st = cs_site(j0, colour, L, fL);
+    const uint32_t p = st.i & 1u;  // x parity of the quad's sites
+    const uint32_t jr = st.rb >> 1;  // first colour index of the row
+    const uint32_t LH = L >> 1;
+    // other-colour words of the row at j0..j0+3 and the one beyond the quad
+    const uint4 O = ldv4(oth + j0);
+    const uint32_t jx = p ? (j0 + 4 == jr + LH ? jr : j0 + 4) : (j0 == jr ? jr + LH - 1 : j0 - 1);
+    const uint32_t Ox = oth[jx];
+    const uint4 JXo = ldv4(Jx + ot + j0);
+    const uint32_t JXx = Jx[ot + jx];
+    const uint4 S = ldv4(own + j0);
+    const uint4 YP = ldv4(oth + (st.yp >> 1)), YM = ldv4(oth + (st.ym >> 1));
+    const uint4 ZP = ldv4(oth + (st.zp >> 1)), ZM = ldv4(oth + (st.zm >> 1));
+    const uint4 JXs = ldv4(Jx + co + j0), JYs = ldv4(Jy + co + j0), JZs = ldv4(Jz + co + j0);
+    const uint4 JYm = ldv4(Jy + ot + (st.ym >> 1)), JZm = ldv4(Jz + ot + (st.zm >> 1));
+    const uint32_t s_[4] = {S.x, S.y, S.z, S.w}, o_[4] = {O.x, O.y, O.z, O.w};
+    const uint32_t jo_[4] = {JXo.x, JXo.y, JXo.z, JXo.w};
+    const uint32_t yp_[4] = {YP.x, YP.y, YP.z, YP.w}, ym_[4] = {YM.x, YM.y, YM.z, YM.w};
+    const uint32_t zp_[4] = {ZP.x, ZP.y, ZP.z, ZP.w}, zm_[4] = {ZM.x, ZM.y, ZM.z, ZM.w};
+    const uint32_t jx_[4] = {JXs.x, JXs.y, JXs.z, JXs.w}, jy_[4] = {JYs.x, JYs.y, JYs.z, JYs.w};
+    const uint32_t jz_[4] = {JZs.x, JZs.y, JZs.z, JZs.w};
+    const uint32_t jym_[4] = {JYm.x, JYm.y, JYm.z, JYm.w}, jzm_[4] = {JZm.x, JZm.y, JZm.z, JZm.w};
+    const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+    uint32_t nw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // p = 0: x-1 is the other colour at k-1, x+1 at k; p = 1: x-1 at k, x+1 at k+1
+      const uint32_t xm = p ? o_[k] : (k ? o_[k - 1] : Ox);
+      const uint32_t xp = p ? (k < 3 ? o_[k + 1] : Ox) : o_[k];
+      const uint32_t jxm = p ? jo_[k] : (k ? jo_[k - 1] : JXx);
+      const Flip f = ea_flip(s_[k] ^ xp ^ jx_[k], s_[k] ^ xm ^ jxm, s_[k] ^ yp_[k] ^ jy_[k],
+                             s_[k] ^ ym_[k] ^ jym_[k], s_[k] ^ zp_[k] ^ jz_[k], s_[k] ^ zm_[k] ^ jzm_[k],
+                             rr[k], t4, t8, t12);
+      nw[k] = s_[k] ^ f.F;
+      if (kCount) {
+        uint32_t a0, a1, a2;
+        ea_after(f, a0, a1, a2);
+        add(a0, a1, a2);
+      }
+    }
+    *reinterpret_cast<uint4 *>(own + j0) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+    return;
+  }
+  const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (uint32_t k = 0; k < 4; ++k) {
+    const uint32_t j = 4 * j4 + k;
+    if (j >= half) break;
+    const CsSite st = cs_site(j, colour, L, fL);
+    const uint32_t S = own[j];
+    const Flip f = ea_flip(S ^ oth[st.xp >> 1] ^ Jx[co + j], S ^ oth[st.xm >> 1] ^ Jx[ot + (st.xm >> 1)],
+                           S ^ oth[st.yp >> 1] ^ Jy[co + j], S ^ oth[st.ym >> 1] ^ Jy[ot + (st.ym >> 1)],
+                           S ^ oth[st.zp >> 1] ^ Jz[co + j], S ^ oth[st.zm >> 1] ^ Jz[ot + (st.zm >> 1)],
+                           rr[k], t4, t8, t12);
+    own[j] = S ^ f.F;
+    if (kCount) {
+      uint32_t a0, a1, a2;
+      ea_after(f, a0, a1, a2);
+      add(a0, a1, a2);
+    }
+  }
+}
+
+}  // namespace spin

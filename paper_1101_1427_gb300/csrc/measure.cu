@@ -1,6 +1,7 @@
 // Reductions (energy, magnetisation, overlap; Sec. 4 measurements by
 // parallel reduction, double accumulation for continuous spins, Sec. 5)
 // and the replica-exchange step (Eq. parallel_tempering, Sec. 7).
+#include "ea_cs.cuh"
 #include "internal.h"
 
 namespace spin {
@@ -166,20 +167,22 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   const bool do_q = Q && a == 0 && g.n_sets >= 2;
   const uint32_t *s1 = s + (size_t)G * T * N;  // set 1, same (g, t)
   uint32_t CE[kThr] = {}, CM[kThr] = {}, CQ[kThr] = {};
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const uint32_t row = fdiv(i, g.fL), x = i - row * L;
-    const uint32_t z = fdiv(row, g.fL), y = row - z * L;
-    const uint32_t S = s[i];
-    const uint32_t ixp = i - x + (x == L - 1 ? 0 : x + 1);
-    const uint32_t iyp = y == L - 1 ? i - (L - 1) * L : i + L;
-    const uint32_t izp = z == L - 1 ? i - (L - 1) * LL : i + LL;
-    const uint32_t u0 = S ^ s[ixp] ^ Jg[i];
-    const uint32_t u1 = S ^ s[iyp] ^ Jg[N + i];
-    const uint32_t u2 = S ^ s[izp] ^ Jg[2 * N + i];
+  const uint32_t half = N / 2;
+  // storage index k: colour c = k / half, colour index j = k % half; the
+  // bonds (i, i + e_d) of every site count each bond once
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const int c = k >= half ? 1 : 0;
+    const uint32_t j = k - (uint32_t)c * half;
+    const CsSite st = cs_site(j, c, L, g.fL);
+    const uint32_t oc = (uint32_t)(c ^ 1) * half;
+    const uint32_t S = s[k];
+    const uint32_t u0 = S ^ s[oc + (st.xp >> 1)] ^ Jg[k];
+    const uint32_t u1 = S ^ s[oc + (st.yp >> 1)] ^ Jg[N + k];
+    const uint32_t u2 = S ^ s[oc + (st.zp >> 1)] ^ Jg[2 * N + k];
     vc_add(CE, u0 ^ u1 ^ u2, 0);
     vc_add(CE, (u0 & u1) | (u2 & (u0 ^ u1)), 1);
     if (M) vc_add(CM, S, 0);
-    if (do_q) vc_add(CQ, S ^ s1[i], 0);
+    if (do_q) vc_add(CQ, S ^ s1[k], 0);
   }
   const uint32_t lane = threadIdx.x & 31;
   const int64_t lat = ((int64_t)a * T + t) * g.n_real + 32 * grp + lane;

@@ -1,0 +1,166 @@
+"""Parity at the full sizes of the hot-path configurations, in the launch
+forms the benchmark times: sampled outputs that the oracle computes one by
+one (light-cone windows, single realisations) or properties that hold at any
+size."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1101_1427_gb300 as sp  # noqa: E402
+from paper_1101_1427_gb300 import _binding as B  # noqa: E402
+from tests.stats import binned_mean  # noqa: E402
+
+
+def _windows(L, rng, count, W):
+    origins = [(L - W // 2, L - W // 2), (0, 0), (L - W, 7)]  # wrap-around corners
+    origins += [tuple(int(v) for v in rng.integers(0, L, 2)) for _ in range(count - len(origins))]
+    return origins
+
+
+@pytest.mark.parametrize("layout", [B.SPIN_I8, B.SPIN_MSC1])
+def test_ising2d_L16384_sampled_windows(layout):
+    """2D Ising L=16384, three betas, two sweeps, in the benchmark's layouts:
+    every sampled window's interior equals the oracle's light-cone sweeps."""
+    L, seed, betas, n, W = 16384, 1, [0.40, 0.4407, 0.50], 2, 14
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, layout, n_temps=3, seed=seed)
+    lat.sweep(betas, n)
+    full = lat.unpack().view(3, L, L)
+    rng = np.random.default_rng(5)
+    for t, beta in enumerate(betas):
+        lid = oracle.lattice_id(0, 0, t)
+        for (ox, oy) in _windows(L, rng, 5, W):
+            gx = (ox + np.arange(W)) % L
+            gy = (oy + np.arange(W)) % L
+            idx = (gy[:, None] * L + gx[None, :]).ravel()
+            win = oracle.init_sites(idx, seed, lid)
+            oracle.window_sweeps(2, L, (ox, oy), W, win, beta, seed, lid, 0, n)
+            got = full[t][torch.as_tensor(gy, device="cuda")][:, torch.as_tensor(gx, device="cuda")]
+            got = got.cpu().numpy()
+            inner = slice(2 * n, W - 2 * n)
+            assert np.array_equal(got[inner, inner], win.reshape(W, W)[inner, inner]), (t, ox, oy)
+
+
+def test_ising2d_L16384_energy_consistent_with_state():
+    """The reductions the benchmark times agree with an independent count on
+    the unpacked state (a property at any size)."""
+    L = 16384
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, n_temps=3, seed=4)
+    lat.sweep([0.40, 0.4407, 0.50], 3)
+    E, M, _ = lat.measure()
+    s = lat.unpack().view(3, L, L).to(torch.int32)
+    E2 = -(s * torch.roll(s, -1, 2)).sum((1, 2)) - (s * torch.roll(s, -1, 1)).sum((1, 2))
+    assert torch.equal(E, E2.to(torch.int64)) and torch.equal(M, s.sum((1, 2)).to(torch.int64))
+
+
+def test_ea_L16_full_size_batched_sampled_realisations():
+    """3D EA L=16, 1024 realisations x 32 slots x 2 sets, exchange and
+    measurement every sweep, in the batched persistent launch: sampled
+    realisations equal the oracle run of that realisation alone."""
+    L, seed, n = 16, 3, 6
+    betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
+    lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=seed)
+    ser = lat.series_buffers(n)
+    acc = torch.zeros(64, dtype=torch.int64, device="cuda")
+    sp.batch_run([lat.batch_item(betas, ser, acc)], n, 1, 1)
+    lat.sync()
+    got = lat.unpack()
+    E = ser["E"].view(n, 2, 32, 1024)
+    Q = ser["Q"].view(n, 32, 1024)
+    for r in (0, 517, 1023):
+        J = oracle.ea_couplings(3, L, r, seed)
+        s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t), bit=r & 31)
+                                for t in range(32)]) for a in range(2)]).copy()
+        Es, Qs, _, _ = oracle.pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J)
+        assert np.array_equal(got[:, :, r].cpu().numpy(), s), r
+        assert np.array_equal(E[:, :, :, r].cpu().numpy(), Es), r
+        assert np.array_equal(Q[:, :, r].cpu().numpy(), Qs), r
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_heis_L128_one_sweep_full_lattice(variant):
+    """3D Heisenberg L=128 (2M sites): one sweep from a common FP32 start,
+    every site within 1e-5 of the FP64 oracle except flagged near-ties."""
+    L, seed, beta = 128, 6, 0.693
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=seed)
+    lat.set_variant(variant)
+    s0 = oracle.heis_init(3, L, seed, 0).astype(np.float32)
+    dev = np.zeros((L ** 3, 4), np.float32)
+    dev[:, :3] = s0
+    lat.spins.copy_(torch.from_numpy(dev.ravel()))
+    lat.sweep([beta], 1)
+    got = lat.spins.view(-1, 4)[:, :3].cpu().numpy()
+    ref = s0.astype(np.float64)
+    margin = oracle.heis_sweep(3, L, ref, beta, seed, 0, 0, want_margin=True)
+    err = np.max(np.abs(got - ref), axis=1)
+    flagged = margin < 1e-5
+    idx = np.arange(L ** 3)
+    x, y, z = idx % L, (idx // L) % L, idx // (L * L)
+    near = flagged.copy()
+    for d in (1, -1):
+        for sh in ((x + d) % L + L * y + L * L * z, x + L * ((y + d) % L) + L * L * z,
+                   x + L * y + L * L * ((z + d) % L)):
+            near |= flagged[sh]
+    assert not ((err > 1e-5) & ~near).any()
+    assert (err > 1e-5).sum() <= 40
+
+
+def test_heis_L128_renormalisation():
+    L = 128
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=7)
+    lat.sweep([0.693], 100)
+    v = lat.spins.view(-1, 4)[:, :3].double()
+    assert torch.max(torch.abs(torch.linalg.norm(v, dim=1) - 1)).item() <= 1e-6
+
+
+def test_heis_long_run_energy_matches_fp64_oracle():
+    """Long-run energy per spin of the FP32 GPU chain and of the FP64 oracle
+    chain (same seed; they decorrelate after the first decision that differs)
+    agree within 3 combined standard errors."""
+    L, beta, n, seed = 12, 0.693, 3000, 8
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=seed)
+    out = lat.run([beta], n, measure_every=1)
+    eg = out["Ef"].cpu().numpy() / L ** 3
+    s = oracle.heis_init(3, L, seed, 0)
+    eo, _ = oracle.heis_run(3, L, s, beta, seed, 0, 0, n)
+    eo = eo / L ** 3
+    mg, sg = binned_mean(eg[300:], 30)
+    mo, so = binned_mean(eo[300:], 30)
+    assert abs(mg - mo) <= 3 * math.sqrt(sg ** 2 + so ** 2) + 1e-12, (mg, sg, mo, so)
+
+
+def test_uneven_batch_equals_per_handle_runs():
+    """An uneven batch in one launch: EA lattices of L = 8, 12, 16 and 24
+    (different slot counts) and 2D Ising lattices of L = 256 and 512."""
+    specs = [("ea", 8, 64, 6), ("ea", 12, 32, 5), ("ea", 16, 32, 4), ("ea", 24, 32, 3),
+             ("is", 256, 1, 1), ("is", 512, 1, 1)]
+
+    def make(k, spec):
+        kind, L, n_real, n_t = spec
+        if kind == "ea":
+            lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=n_t, n_sets=2, seed=40 + k)
+            return lat, list(1.0 / np.geomspace(0.8, 2.2, n_t))
+        return sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=40 + k), [0.4407]
+
+    n = 7
+    batch = [make(k, s) for k, s in enumerate(specs)]
+    plain = [make(k, s) for k, s in enumerate(specs)]
+    items, sers = [], []
+    for lat, betas in batch:
+        ser = lat.series_buffers(n)
+        if lat.n_sets < 2:
+            ser.pop("Q", None)
+        sers.append(ser)
+        items.append(lat.batch_item(betas, ser))
+    sp.batch_run(items, n, 1, 1)
+    batch[0][0].sync()
+    for (lb, _), (lp, betas), ser in zip(batch, plain, sers):
+        out = lp.run(betas, n, 1, 1)
+        assert torch.equal(lb.spins, lp.spins)
+        for key in ser:
+            assert torch.equal(ser[key], out[key]), key

@@ -137,9 +137,13 @@ def test_ea_couplings_and_init_match_oracle(layout):
         for r in (0, 1, 31, 32, 63):
             assert np.array_equal(Jg[r], oracle.ea_couplings(3, L, r, seed))
     else:
-        Jw = host(lat.couplings).view(np.uint32).reshape(n_real // 32, 3 * L ** 3)
+        N = L ** 3
+        Jw = host(lat.couplings).view(np.uint32).reshape(n_real // 32, 3, N)
+        i = np.arange(N)
+        colour = (i % L + (i // L) % L + i // (L * L)) % 2
+        slot = colour * (N // 2) + (i >> 1)  # colour-split storage of bond (i, i + e_d)
         for r in (0, 5, 31, 32, 63):
-            bits = ((Jw[r >> 5] >> np.uint32(r & 31)) & 1).astype(np.int8)
+            bits = ((Jw[r >> 5][:, slot] >> np.uint32(r & 31)) & 1).astype(np.int8).ravel()
             assert np.array_equal(1 - 2 * bits, oracle.ea_couplings(3, L, r, seed))
 
 

@@ -50,8 +50,8 @@ WIDE_MULS_PER_CLK_PER_SM = 32
 # DRAM bytes of one phase launch of the coded sweep over the three lattices
 # (ncu capture summarised in profiles/), valid while the kernel source hash
 # matches; otherwise reported as null.
-KERNEL_TRAFFIC_BYTES = None
-KERNEL_TRAFFIC_SRC_SHA = None
+KERNEL_TRAFFIC_BYTES = 100_678_144 + 11_205_376
+KERNEL_TRAFFIC_SRC_SHA = "91d31522b50997f7"
 
 
 def kernel_sha():
@@ -331,6 +331,62 @@ def run_gpu(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_case(name):
+    """One kernel family on a small case with few launches (for profilers):
+    prints its throughput; not the benchmark line."""
+    import numpy as np
+    import torch
+
+    import paper_1101_1427_gb300 as sp
+    from paper_1101_1427_gb300 import _binding as B
+    stream = torch.cuda.current_stream()
+    a, b = _events(torch)
+    if name in ("msc2d", "fused2d"):
+        layout = B.SPIN_MSC1 if name == "msc2d" else B.SPIN_I8
+        lat = sp.Lattice(B.SPIN_ISING, 2, L, layout, n_temps=3, seed=1)
+        B.spin_sweep(lat.h, None, BETAS, 2, lat.seed)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, BETAS, 2, lat.seed)
+        b.record(stream)
+        flips = 2 * 3 * L * L
+    elif name in ("ea", "ea_batch"):
+        betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
+        lat = sp.Lattice(B.SPIN_EA, 3, 16, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=1)
+        if name == "ea":
+            B.spin_sweep(lat.h, lat.couplings, betas, 2, lat.seed)
+            a.record(stream)
+            B.spin_sweep(lat.h, lat.couplings, betas, 2, lat.seed)
+            b.record(stream)
+            flips = 2 * 2 ** 28
+        else:
+            ser = lat.series_buffers(4)
+            item = [lat.batch_item(betas, ser)]
+            B.spin_batch_run(item, 2, 1, 1, stream.cuda_stream)
+            a.record(stream)
+            B.spin_batch_run(item, 4, 1, 1, stream.cuda_stream)
+            b.record(stream)
+            flips = 4 * 2 ** 28
+    elif name == "heis":
+        lat = sp.Lattice(B.SPIN_HEISENBERG, 3, 128, B.SPIN_F32X4, seed=1)
+        B.spin_sweep(lat.h, None, [0.693], 2, lat.seed)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, [0.693], 2, lat.seed)
+        b.record(stream)
+        flips = 2 * 128 ** 3
+    elif name == "rng":
+        threads, calls = 152 * 2048, 256
+        out = torch.empty(threads, dtype=torch.int32, device="cuda")
+        B.spin_rng_probe(1, threads, calls, out, stream.cuda_stream)
+        a.record(stream)
+        B.spin_rng_probe(1, threads, calls, out, stream.cuda_stream)
+        b.record(stream)
+        flips = 4 * threads * calls  # words
+    else:
+        raise SystemExit(f"unknown case {name}")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "per_ns": flips / (a.elapsed_time(b) * 1e6)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,11 +395,16 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
+    ap.add_argument("--case", default=None,
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.case:
+        run_case(args.case)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return

@@ -78,7 +78,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -160,7 +160,8 @@ def side_configs(torch, sp, B, stream):
     """Short measurements of the other hot-path configurations (context for
     the headline): 3D Heisenberg L=128 (FP32), and 3D EA L=16 with 1024
     realisations x 32 slots x 2 sets, exchange and measurement every sweep,
-    in the per-handle multi-launch form and in the batched persistent form."""
+    in the per-handle multi-launch form and in the batched persistent form;
+    then the uneven batch in both forms."""
     import numpy as np
     out = {}
     lat = sp.Lattice(B.SPIN_HEISENBERG, 3, 128, B.SPIN_F32X4, seed=11)
@@ -197,6 +198,70 @@ def side_configs(torch, sp, B, stream):
     ea.sync()
     out["ea_L16_pt_batched_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
     ea.close()
+    out.update(uneven_batch(torch, sp, B, stream))
+    return out
+
+
+# Uneven batch: 3D EA lattices of five sizes (L, realisations, temperatures
+# geometric in [0.8, 2.2], two replica sets) and five 2D Ising ferromagnets.
+UNEVEN_EA = [(8, 512, 24), (12, 256, 30), (16, 128, 36), (24, 64, 42), (32, 32, 48)]
+UNEVEN_ISING = [256, 512, 1024, 2048, 4096]
+
+
+def uneven_batch(torch, sp, B, stream, n=20):
+    """The uneven batch with measurement and exchange every sweep, twice:
+    plain per-handle calls (spin_run, several launches per sweep) and one
+    graph-replayed batched launch after the autotuner has run; then checks
+    that both sides reached identical lattices."""
+    import numpy as np
+
+    def build():
+        side = []
+        for k, (Le, R, T) in enumerate(UNEVEN_EA):
+            lat = sp.Lattice(B.SPIN_EA, 3, Le, B.SPIN_MSC1, n_real=R, n_temps=T, n_sets=2, seed=50 + k)
+            side.append((lat, list(1.0 / np.geomspace(0.8, 2.2, T))))
+        for k, Li in enumerate(UNEVEN_ISING):
+            side.append((sp.Lattice(B.SPIN_ISING, 2, Li, B.SPIN_I8, seed=60 + k), [0.4407]))
+        return side
+
+    flips = n * (sum(2 * T * R * Le ** 3 for Le, R, T in UNEVEN_EA) + sum(Li * Li for Li in UNEVEN_ISING))
+    plain, batch = build(), build()
+    sers = []
+    for lat, betas in plain + batch:
+        ser = lat.series_buffers(n)
+        if lat.n_sets < 2:
+            ser.pop("Q", None)
+        acc = torch.zeros(lat.n_sets * lat.n_temps, dtype=torch.int64, device=stream.device)
+        sers.append((ser, acc))
+
+    def plain_run(k):
+        for (lat, betas), (ser, acc) in zip(plain, sers):
+            pt = 1 if lat.model == B.SPIN_EA else 0
+            B.spin_run(lat.h, lat.couplings, betas, k, 1, pt, ser["E"], ser["M"], ser.get("Q"), None, None,
+                       acc)
+
+    items = [lat.batch_item(betas, ser, acc) for (lat, betas), (ser, acc) in zip(batch, sers[len(plain):])]
+    plain_run(2)
+    B.spin_batch_run(items, 2, 1, 1, stream.cuda_stream)
+    best = B.spin_batch_tune(items, 4, 1, 1, stream.cuda_stream)
+    graph = sp.BatchGraph(items, n, 1, 1)
+    out = {}
+    a, b = _events(torch)
+    a.record(stream)
+    plain_run(n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["uneven_batch_plain_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
+    a.record(stream)
+    graph.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    batch[0][0].sync()
+    out["uneven_batch_batched_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
+    out["uneven_batch_ctas_per_sm"] = best
+    out["uneven_batch_identical"] = all(torch.equal(p.spins, q.spins) for (p, _), (q, _) in zip(plain, batch))
+    for lat, _ in plain + batch:
+        lat.close()
     return out
 
 
@@ -366,6 +431,9 @@ def run_case(name):
             B.spin_batch_run(item, 4, 1, 1, stream.cuda_stream)
             b.record(stream)
             flips = 4 * 2 ** 28
+    elif name == "uneven":
+        print(json.dumps({"case": name, **uneven_batch(torch, sp, B, stream, n=8)}), flush=True)
+        return
     elif name == "heis":
         lat = sp.Lattice(B.SPIN_HEISENBERG, 3, 128, B.SPIN_F32X4, seed=1)
         B.spin_sweep(lat.h, None, [0.693], 2, lat.seed)
@@ -390,13 +458,13 @@ def run_case(name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, uneven)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -166,9 +166,22 @@ typedef struct {
  * lattice).  Work units are spread over teams of co-resident CTAs in
  * proportion to their work; a team synchronises through global-memory
  * barriers whose waits are bounded in time: on expiry the launch ends early
- * and spin_sync on the FIRST item's handle returns SPIN_ETIMEOUT.  The first
- * call allocates a small process-wide workspace; later calls of no larger
- * size allocate nothing. */
+ * and spin_sync on the FIRST item's handle returns SPIN_ETIMEOUT.
+ *
+ * The launch reads each handle's sweep and exchange counters from a device
+ * copy and advances that copy when it ends (both in stream order), so the
+ * work one call enqueues can be captured into a CUDA graph and replayed:
+ * each replay continues the random streams where the previous one ended.
+ * An uncaptured call uploads the tables for `betas` if they changed,
+ * allocates the handle's batch workspace on first use (kept until
+ * spin_destroy) and loads the device counters from the host counters;
+ * n_sweeps = 0 does only that.  Inside a stream capture the call uploads and
+ * allocates nothing and returns SPIN_EINVAL unless an uncaptured call with
+ * the same betas came first, no other call has moved the counters since,
+ * and measure_every (if > 0) divides n_sweeps.  Capturing advances the host
+ * counters once, as if the captured work had run; a caller that replays the
+ * graph R times sets them (spin_set_counters) to the values after R runs.
+ * Changing a handle's betas after the capture invalidates the graph. */
 int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                    int32_t measure_every, int32_t pt_every, void *stream);
 
@@ -231,7 +244,10 @@ int spin_heis_measure_noalloc(const float *spins, int32_t L, int32_t n_lat, doub
  * (SPIN_ECUDA, SPIN_ETIMEOUT).  Clears the device error word. */
 int spin_sync(spin_lattice *lat);
 
-/* Counters and tuning of a handle. */
+/* Counters and tuning of a handle.  spin_set_counters sets the host
+ * counters and, once the handle has a batch workspace, also enqueues on the
+ * handle's stream a write of the same values to the device copy that
+ * batched launches read. */
 int64_t spin_sweeps_done(const spin_lattice *lat);
 int64_t spin_pt_steps_done(const spin_lattice *lat);
 int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_done);

@@ -8,4 +8,4 @@ library through the binding in ``_binding``.
 """
 from ._binding import *  # noqa: F401,F403
 from ._binding import lib  # noqa: F401
-from .lattice import Lattice, batch_run  # noqa: F401
+from .lattice import BatchGraph, Lattice, batch_run  # noqa: F401

@@ -129,8 +129,8 @@ int validate_desc(const spin_desc *d) {
 }
 
 void free_workspaces(spin_lattice *h) {
-  void *bufs[] = {h->d_thr, h->d_pt_thr, h->d_pt_off, h->d_pt_len, h->d_pt_dbeta,
-                  h->d_energy, h->d_scratch64, h->d_err, h->d_pingpong};
+  void *bufs[] = {h->d_thr,    h->d_pt_thr,      h->d_pt_off, h->d_pt_len,    h->d_pt_dbeta, h->d_energy,
+                  h->d_scratch64, h->d_err, h->d_pingpong, h->d_ctr, h->d_bar,  h->d_escr};
   for (void *b : bufs)
     if (b) cudaFree(b);
 }
@@ -156,6 +156,13 @@ int upload_thresholds_for_batch(spin_lattice *h, const double *betas) { return u
 int upload_pt_tables_for_batch(spin_lattice *h, const double *betas) {
   if (!betas) return SPIN_EINVAL;
   return upload_pt_tables(h, betas);
+}
+// True when the tables for these betas are already on the device (nothing
+// would be uploaded, so the call is safe inside a stream capture).
+bool tables_cached_for_batch(const spin_lattice *h, const double *betas, bool pt) {
+  const size_t nb = sizeof(double) * (size_t)h->g.n_temps;
+  if (!betas || !h->thr_valid || memcmp(h->betas_cached.data(), betas, nb) != 0) return false;
+  return !pt || (!h->pt_betas_cached.empty() && memcmp(h->pt_betas_cached.data(), betas, nb) == 0);
 }
 bool fused2d_supported(int L);
 cudaError_t launch_init_msc2d(spin_lattice *h);
@@ -364,7 +371,7 @@ int spin_set_counters(spin_lattice *h, int64_t sweeps_done, int64_t pt_steps_don
     return SPIN_EINVAL;
   h->sweeps_done = sweeps_done;
   h->pt_steps_done = pt_steps_done;
-  return SPIN_OK;
+  return spin::sync_device_counters(h, h->stream);
 }
 
 int spin_set_batch_options(spin_lattice *h, uint64_t timeout_ns, int32_t ctas_per_sm,

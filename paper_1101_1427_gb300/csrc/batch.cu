@@ -38,9 +38,10 @@ struct BatchUnit {
   FastDiv fL;
   const uint32_t *thr;  // [n_T][4]
   int key;              // round keys of the handle
-  uint32_t sweep0;      // handle's sweep counter at launch
-  uint32_t pt0;         // handle's exchange counter at launch
-  long long meas0;      // measurements already taken by the handle in this call: 0
+  const long long *ctr;  // handle's [sweeps_done, pt_steps_done] on the device
+  uint32_t sweep0;      // ctr[0] when the launch starts
+  uint32_t pt0;         // ctr[1] when the launch starts
+  unsigned *bar;        // the team's barrier counter (zeroed before the launch)
   // EA
   uint32_t *w;          // words of set 0, this group, slot 0
   size_t set_stride;    // words between replica sets
@@ -530,7 +531,7 @@ __device__ bool ising_sweep(const BatchUnit &U, int part, const RoundKeys &rk, S
 }
 
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchParams prm,
-                                                         unsigned *bar, int *err) {
+                                                         int *err) {
   __shared__ BatchUnit U;
   __shared__ RoundKeys rk;
   extern __shared__ __align__(16) uint32_t sJ[];  // couplings of an EA unit, when staged
@@ -544,11 +545,15 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
   const int u = lo;
   if (threadIdx.x == 0) {
     U = prm.units[u];
+    // the counters come from device memory, so that a captured launch
+    // replayed later continues the handle's random streams
+    U.sweep0 = (uint32_t)U.ctr[0];
+    U.pt0 = (uint32_t)U.ctr[1];
     rk = prm.keys[U.key];
   }
   __syncthreads();
   const int part = (int)blockIdx.x - U.team_first;
-  Sync sy{bar + u, 0u, U.team_size, err, prm.timeout_ns, prm.extra};
+  Sync sy{U.bar, 0u, U.team_size, err, prm.timeout_ns, prm.extra};
   // the couplings never change during a launch: stage them once if they fit
   const uint32_t *Jsrc = U.J;
   if (U.kind == 0 && 3u * U.N <= prm.staged_words) {
@@ -572,6 +577,39 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     if (measure) ++meas_row;
     if (pt) ++pt_step;
   }
+}
+
+// Work around a batched launch, per handle: zero the barrier counters and
+// (outside a stream capture) load the device counters from the host's; after
+// the launch, advance the device counters as the launch advanced the host's.
+struct BatchCtl {
+  int n;
+  int set;  // prologue: write ctr from sweeps / pt
+  int32_t pt_every;
+  int64_t n_sweeps;
+  int *err;
+  long long *ctr[kMaxHandles];
+  long long sweeps[kMaxHandles], pt[kMaxHandles];
+  unsigned *bar[kMaxHandles];
+  int n_bar[kMaxHandles];
+};
+
+__global__ void batch_prologue_kernel(const BatchCtl c) {
+  for (int k = 0; k < c.n; ++k)
+    for (int i = threadIdx.x; i < c.n_bar[k]; i += blockDim.x) c.bar[k][i] = 0u;
+  if (threadIdx.x < (unsigned)c.n && c.set) {
+    c.ctr[threadIdx.x][0] = c.sweeps[threadIdx.x];
+    c.ctr[threadIdx.x][1] = c.pt[threadIdx.x];
+  }
+  if (threadIdx.x == 0 && c.err) *c.err = 0;
+}
+
+__global__ void batch_epilogue_kernel(const BatchCtl c) {
+  if (threadIdx.x >= (unsigned)c.n) return;
+  long long *ctr = c.ctr[threadIdx.x];
+  const long long s = ctr[0];
+  if (c.pt_every > 0) ctr[1] += (s + c.n_sweeps) / c.pt_every - s / c.pt_every;
+  ctr[0] = s + c.n_sweeps;
 }
 
 }  // namespace
@@ -625,11 +663,6 @@ static int assign_teams(BatchUnit *units, int n, int grid) {
   return first;
 }
 
-// workspace shared by all batch launches of the process (grown on demand)
-static unsigned *g_bar = nullptr;
-static int *g_escr = nullptr;
-static size_t g_escr_words = 0;
-
 }  // namespace spin
 
 using namespace spin;
@@ -637,11 +670,62 @@ using namespace spin;
 namespace spin {
 int upload_thresholds_for_batch(spin_lattice *h, const double *betas);  // api.cu
 int upload_pt_tables_for_batch(spin_lattice *h, const double *betas);   // api.cu
+bool tables_cached_for_batch(const spin_lattice *h, const double *betas, bool pt);  // api.cu
 }
 
-static int batch_build(const spin_batch_item *items, int n_items, BatchParams &prm, size_t &escr_words) {
+// work units of a handle in a batched launch: EA realisation groups or Ising lattices
+static int64_t units_of(const spin_lattice *h) {
+  return h->d.model == SPIN_EA ? h->g.n_real / 32 : h->n_lat;
+}
+
+// Per-handle workspace of batched launches, allocated once (never inside a
+// stream capture) and kept until spin_destroy, so that captured launches
+// keep valid pointers.
+static int ensure_batch_ws(spin_lattice *h) {
+  if (h->d_ctr) return SPIN_OK;
+  const size_t escr = h->d.model == SPIN_EA ? (size_t)units_of(h) * h->g.n_sets * h->g.n_temps * 32 : 0;
+  if (cudaMalloc(&h->d_ctr, 2 * sizeof(int64_t)) != cudaSuccess) return SPIN_ENOMEM;
+  if (cudaMalloc(&h->d_bar, (size_t)units_of(h) * sizeof(unsigned)) != cudaSuccess) return SPIN_ENOMEM;
+  if (escr && cudaMalloc(&h->d_escr, escr * sizeof(int)) != cudaSuccess) return SPIN_ENOMEM;
+  h->ctr_dev[0] = h->ctr_dev[1] = -1;
+  return SPIN_OK;
+}
+
+static void fill_ctl(BatchCtl &c, const spin_batch_item *items, int n_items, int set, int64_t n_sweeps,
+                     int32_t pt_every, int *err) {
+  c = BatchCtl{};
+  c.n = n_items;
+  c.set = set;
+  c.n_sweeps = n_sweeps;
+  c.pt_every = pt_every;
+  c.err = err;
+  for (int k = 0; k < n_items; ++k) {
+    spin_lattice *h = items[k].lat;
+    c.ctr[k] = (long long *)h->d_ctr;
+    c.sweeps[k] = h->sweeps_done;
+    c.pt[k] = h->pt_steps_done;
+    c.bar[k] = h->d_bar;
+    c.n_bar[k] = (int)units_of(h);
+  }
+}
+
+// Loads the device counters of a handle from its host counters (stream-ordered).
+int spin::sync_device_counters(spin_lattice *h, cudaStream_t st) {
+  if (!h->d_ctr) return SPIN_OK;
+  spin_batch_item it = {};
+  it.lat = h;
+  BatchCtl c;
+  fill_ctl(c, &it, 1, 1, 0, 0, nullptr);
+  c.n_bar[0] = 0;
+  batch_prologue_kernel<<<1, 32, 0, st>>>(c);
+  if (cudaGetLastError() != cudaSuccess) return SPIN_ECUDA;
+  h->ctr_dev[0] = h->sweeps_done;
+  h->ctr_dev[1] = h->pt_steps_done;
+  return SPIN_OK;
+}
+
+static int batch_build(const spin_batch_item *items, int n_items, BatchParams &prm) {
   prm.n_units = 0;
-  escr_words = 0;
   for (int k = 0; k < n_items; ++k) {
     spin_lattice *h = items[k].lat;
     prm.keys[k] = make_round_keys(h->d.seed);
@@ -660,8 +744,8 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.fL = g.fL;
         U.thr = h->d_thr;
         U.key = k;
-        U.sweep0 = (uint32_t)h->sweeps_done;
-        U.pt0 = (uint32_t)h->pt_steps_done;
+        U.ctr = (const long long *)h->d_ctr;
+        U.bar = h->d_bar + grp;
         U.set_stride = (size_t)G * g.n_temps * g.N;
         U.w = (uint32_t *)h->spins + (size_t)grp * g.n_temps * g.N;
         U.J = (const uint32_t *)items[k].couplings + (size_t)grp * 3 * g.N;
@@ -676,8 +760,7 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.Q_series = (long long *)items[k].Q_series;
         U.accepted = (long long *)items[k].accepted;
         U.n_lat = h->n_lat;
-        U.Escr = (int *)(uintptr_t)escr_words;  // offset into the workspace
-        escr_words += (size_t)g.n_sets * g.n_temps * 32;
+        U.Escr = h->d_escr + (size_t)grp * g.n_sets * g.n_temps * 32;
       }
     } else {
       for (int64_t lat = 0; lat < h->n_lat; ++lat) {
@@ -691,7 +774,8 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.n_sets = g.n_sets;
         U.thr = h->d_thr;
         U.key = k;
-        U.sweep0 = (uint32_t)h->sweeps_done;
+        U.ctr = (const long long *)h->d_ctr;
+        U.bar = h->d_bar + lat;
         U.s = (int8_t *)h->spins + lat * g.N;
         U.E_series = (long long *)items[k].E_series;
         U.M_series = (long long *)items[k].M_series;
@@ -727,9 +811,7 @@ static cudaError_t batch_launch(BatchParams &prm, int grid, cudaStream_t st, int
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaMemsetAsync(g_bar, 0, kMaxUnits * sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, batch_kernel, prm, g_bar, err);
+  return cudaLaunchKernelEx(&cfg, batch_kernel, prm, err);
 }
 
 extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
@@ -737,28 +819,61 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
   if (!items || n_items <= 0 || n_items > kMaxHandles || n_sweeps < 0 || measure_every < 0 || pt_every < 0)
     return SPIN_EINVAL;
   cudaStream_t st = (cudaStream_t)stream_v;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return SPIN_ECUDA;
+  const bool capturing = cs != cudaStreamCaptureStatusNone;
+  // inside a capture nothing may be uploaded or allocated, and the number of
+  // series rows a launch writes must not depend on the count it starts from
+  if (capturing && measure_every > 0 && n_sweeps % measure_every != 0) return SPIN_EINVAL;
   for (int k = 0; k < n_items; ++k) {
     if (!batch_item_ok(items[k], pt_every)) return SPIN_EINVAL;
     spin_lattice *h = items[k].lat;
     for (int q = 0; q < k; ++q)
       if (items[q].lat == h) return SPIN_EINVAL;
     if (h->sweeps_done + n_sweeps > (int64_t)0xFFFFFFFFll) return SPIN_EINVAL;
+    const bool pt_tab = h->d.model == SPIN_EA && pt_every > 0;
+    if (capturing) {
+      if (!tables_cached_for_batch(h, items[k].betas, pt_tab) || !h->d_ctr ||
+          h->ctr_dev[0] != h->sweeps_done || h->ctr_dev[1] != h->pt_steps_done)
+        return SPIN_EINVAL;  // prepare with an uncaptured call first (n_sweeps = 0 will do)
+      continue;
+    }
     int rc = upload_thresholds_for_batch(h, items[k].betas);
     if (rc) return rc;
-    if (h->d.model == SPIN_EA && pt_every > 0) {
+    if (pt_tab) {
       rc = upload_pt_tables_for_batch(h, items[k].betas);
       if (rc) return rc;
     }
+    rc = ensure_batch_ws(h);
+    if (rc) return rc;
   }
-  if (n_sweeps == 0) return SPIN_OK;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 4) !=
+        cudaSuccess)
+      return SPIN_ECUDA;
+    attr = true;
+  }
+  spin_lattice *h0 = items[0].lat;
+  static BatchCtl ctl;
+  fill_ctl(ctl, items, n_items, capturing ? 0 : 1, n_sweeps, pt_every, h0->d_err);
+  if (n_sweeps == 0) {  // preparation only: tables, workspace and device counters
+    if (!capturing) {
+      batch_prologue_kernel<<<1, 256, 0, st>>>(ctl);
+      if (cudaGetLastError() != cudaSuccess) return SPIN_ECUDA;
+      for (int k = 0; k < n_items; ++k) {
+        items[k].lat->ctr_dev[0] = items[k].lat->sweeps_done;
+        items[k].lat->ctr_dev[1] = items[k].lat->pt_steps_done;
+      }
+    }
+    return SPIN_OK;
+  }
   static BatchParams prm;  // large; built on the host for each call
-  size_t escr_words = 0;
-  int rc = batch_build(items, n_items, prm, escr_words);
+  int rc = batch_build(items, n_items, prm);
   if (rc) return rc;
   prm.n_sweeps = n_sweeps;
   prm.measure_every = measure_every;
   prm.pt_every = pt_every;
-  spin_lattice *h0 = items[0].lat;
   prm.timeout_ns = h0->batch_timeout_ns ? h0->batch_timeout_ns : 2000000000ull;
   prm.extra = h0->batch_fault_extra;
   // couplings of EA units with 3N <= 12288 words (48 KiB) are staged in
@@ -767,11 +882,6 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
   for (int u = 0; u < prm.n_units; ++u)
     if (prm.units[u].kind == 0 && 3u * prm.units[u].N <= 12288u)
       prm.staged_words = std::max(prm.staged_words, 3u * prm.units[u].N);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 4);
-    attr = true;
-  }
   // co-resident grid
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -780,16 +890,6 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
                                                     (size_t)prm.staged_words * 4) != cudaSuccess ||
       per_sm < 1)
     return SPIN_ECUDA;
-  // workspace (allocated on first use or growth only)
-  if (!g_bar && cudaMalloc(&g_bar, kMaxUnits * sizeof(unsigned)) != cudaSuccess) return SPIN_ENOMEM;
-  if (escr_words > g_escr_words) {
-    if (g_escr) cudaFree(g_escr);
-    g_escr = nullptr;
-    if (cudaMalloc(&g_escr, escr_words * 4) != cudaSuccess) return SPIN_ENOMEM;
-    g_escr_words = escr_words;
-  }
-  for (int u = 0; u < prm.n_units; ++u)
-    if (prm.units[u].kind == 0) prm.units[u].Escr = g_escr + (uintptr_t)prm.units[u].Escr;
   // Ising series rows are accumulated with atomics: zero the rows of this call
   for (int k = 0; k < n_items; ++k) {
     spin_lattice *h = items[k].lat;
@@ -813,14 +913,19 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
   if (h0->batch_ctas_per_sm <= 0 && it != g_tuned_bps.end()) bps = std::min(per_sm, it->second);
   const int grid = assign_teams(prm.units, prm.n_units, sms * bps);
   if (grid > sms * per_sm) return SPIN_EINVAL;
-  if (cudaMemsetAsync(h0->d_err, 0, sizeof(int), st) != cudaSuccess) return SPIN_ECUDA;
+  batch_prologue_kernel<<<1, 256, 0, st>>>(ctl);
+  if (cudaGetLastError() != cudaSuccess) return SPIN_ECUDA;
   if (batch_launch(prm, grid, st, h0->d_err) != cudaSuccess) return SPIN_ECUDA;
+  batch_epilogue_kernel<<<1, 32, 0, st>>>(ctl);
+  if (cudaGetLastError() != cudaSuccess) return SPIN_ECUDA;
   for (int k = 0; k < n_items; ++k) {
     spin_lattice *h = items[k].lat;
     const int64_t before = h->sweeps_done;
     h->sweeps_done += n_sweeps;
     if (pt_every > 0)  // as spin_run: every exchange point advances the counter
       h->pt_steps_done += h->sweeps_done / pt_every - before / pt_every;
+    h->ctr_dev[0] = h->sweeps_done;
+    h->ctr_dev[1] = h->pt_steps_done;
   }
   return SPIN_OK;
 }
@@ -883,6 +988,7 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
     cudaMemcpyAsync(items[k].lat->spins, backup[k], bytes[k], cudaMemcpyDeviceToDevice, st);
     items[k].lat->sweeps_done = sw[k];
     items[k].lat->pt_steps_done = ps[k];
+    if (sync_device_counters(items[k].lat, st) != SPIN_OK) rc = rc ? rc : SPIN_ECUDA;
   }
   cudaStreamSynchronize(st);
   for (int k = 0; k < n_items; ++k) cudaFree(backup[k]);
@@ -891,8 +997,7 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
   if (rc) return rc;
   std::vector<long long> sig;
   BatchParams *prm = new BatchParams;
-  size_t ew = 0;
-  batch_build(items, n_items, *prm, ew);
+  batch_build(items, n_items, *prm);
   for (int u = 0; u < prm->n_units; ++u) {
     sig.push_back(prm->units[u].kind);
     sig.push_back(prm->units[u].L);

@@ -37,6 +37,11 @@ struct spin_lattice {
   uint64_t batch_timeout_ns;  // bound on every team-barrier wait (0: 2 s)
   int batch_ctas_per_sm;      // 0: autotuned / default
   int batch_fault_extra;      // arrivals a barrier waits for that never come (tests)
+  // batched-launch workspace, allocated by the first uncaptured batch call
+  int64_t *d_ctr;             // [sweeps_done, pt_steps_done] as the batch kernel reads them
+  unsigned *d_bar;            // one team-barrier counter per work unit of this handle
+  int *d_escr;                // EA: [group][n_sets][n_temps][32] energy scratch
+  int64_t ctr_dev[2];         // what d_ctr holds once the enqueued work is done (-1: unknown)
 };
 
 namespace spin {
@@ -67,6 +72,9 @@ cudaError_t launch_rng_fill(uint64_t seed, uint32_t w, uint32_t lattice_id, uint
                             uint64_t count, uint32_t *out, cudaStream_t s);
 cudaError_t launch_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out,
                              cudaStream_t s);
+
+// batch.cu: load the batch kernel's device counters from the host counters
+int sync_device_counters(spin_lattice *h, cudaStream_t st);
 
 inline unsigned grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;

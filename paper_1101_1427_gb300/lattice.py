@@ -154,3 +154,39 @@ def batch_run(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
     """One batched persistent launch over several lattices (see spin_batch_run)."""
     stream = stream or torch.cuda.current_stream()
     B.spin_batch_run(items, n_sweeps, measure_every, pt_every, stream.cuda_stream)
+
+
+class BatchGraph:
+    """One batched launch (see spin_batch_run) captured into a CUDA graph.
+
+    Every ``replay()`` runs ``n_sweeps`` more sweeps of all handles, with the
+    measurements and exchanges of the captured call, continuing each
+    handle's random streams; the handles' host counters follow the replays.
+    The series buffers named by the items are rewritten by every replay.
+    """
+
+    def __init__(self, items, n_sweeps, measure_every=0, pt_every=0):
+        self.n_sweeps, self.pt_every = n_sweeps, pt_every
+        self.handles = [it["lat"] for it in items]
+        cur = torch.cuda.current_stream()
+        # tables, workspace and device counters, outside the capture
+        B.spin_batch_run(items, 0, measure_every, pt_every, cur.cuda_stream)
+        before = [(B.spin_sweeps_done(h), B.spin_pt_steps_done(h)) for h in self.handles]
+        side = torch.cuda.Stream()
+        side.wait_stream(cur)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=side):
+            B.spin_batch_run(items, n_sweeps, measure_every, pt_every, side.cuda_stream)
+        cur.wait_stream(side)
+        # the capture ran nothing: the counters stand where they were
+        for h, (sw, pt) in zip(self.handles, before):
+            B.spin_set_counters(h, sw, pt)
+
+    def replay(self):
+        self.graph.replay()
+        for h in self.handles:
+            sw, pt = B.spin_sweeps_done(h), B.spin_pt_steps_done(h)
+            if self.pt_every > 0:
+                pt += (sw + self.n_sweeps) // self.pt_every - sw // self.pt_every
+            B.spin_set_counters(h, sw + self.n_sweeps, pt)
+

@@ -115,3 +115,45 @@ def test_batch_autotuner_keeps_state():
     assert 1 <= best <= 4
     for (l, _), b in zip(items_l, before):
         assert torch.equal(l.spins, b) and l.sweeps_done == 0
+
+
+def test_batch_graph_replays_continue_the_chain():
+    """A batched launch captured into a CUDA graph: each replay equals the
+    next uncaptured call on a twin set of handles (lattices, series,
+    exchange counts, counters), and plain calls continue correctly after."""
+    kinds = ["ea8", "ea6", "ising64"]
+    n, me, pe = 4, 2, 1
+    graph_side = [_make(k, 300 + i) for i, k in enumerate(kinds)]
+    plain_side = [_make(k, 300 + i) for i, k in enumerate(kinds)]
+
+    def items_for(side):
+        items, outs = [], []
+        for lat, betas in side:
+            ser = lat.series_buffers(n // me)
+            if lat.n_sets < 2:
+                ser.pop("Q", None)
+            acc = torch.zeros(lat.n_sets * lat.n_temps, dtype=torch.int64, device="cuda")
+            items.append(lat.batch_item(betas, ser, acc))
+            outs.append((ser, acc))
+        return items, outs
+
+    items_g, outs_g = items_for(graph_side)
+    items_p, outs_p = items_for(plain_side)
+    g = sp.BatchGraph(items_g, n, me, pe)
+    for rep in range(3):
+        g.replay()
+        sp.batch_run(items_p, n, me, pe)
+        torch.cuda.synchronize()
+        for (lg, _), (lp, _), (sg, ag), (sp_, ap) in zip(graph_side, plain_side, outs_g, outs_p):
+            assert torch.equal(lg.spins, lp.spins), rep
+            for key in sg:
+                assert torch.equal(sg[key], sp_[key]), (rep, key)
+            assert torch.equal(ag, ap), rep
+            assert lg.sweeps_done == lp.sweeps_done == n * (rep + 1)
+            assert lg.pt_steps_done == lp.pt_steps_done
+    graph_side[0][0].sync()
+    for (lg, betas), (lp, _) in zip(graph_side, plain_side):
+        pt = pe if lg.model == B.SPIN_EA else 0
+        lg.run(betas, 3, 0, pt, series=False)
+        lp.run(betas, 3, 0, pt, series=False)
+        assert torch.equal(lg.spins, lp.spins)

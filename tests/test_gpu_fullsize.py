@@ -164,3 +164,52 @@ def test_uneven_batch_equals_per_handle_runs():
         assert torch.equal(lb.spins, lp.spins)
         for key in ser:
             assert torch.equal(ser[key], out[key]), key
+
+
+UNEVEN_EA = [(8, 512, 24), (12, 256, 30), (16, 128, 36), (24, 64, 42), (32, 32, 48)]
+UNEVEN_ISING = [256, 512, 1024, 2048, 4096]
+
+
+def test_uneven_batch_full_size():
+    """The full uneven batch (EA L = 8..32 with 512..32 realisations and
+    24..48 temperatures in [0.8, 2.2], two sets; 2D Ising L = 256..4096) in
+    one batched launch, measurement and exchange every sweep: equal to plain
+    per-handle runs, and sampled EA realisations equal to the oracle."""
+    n = 3
+
+    def build():
+        side = []
+        for k, (L, R, T) in enumerate(UNEVEN_EA):
+            lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=R, n_temps=T, n_sets=2, seed=50 + k)
+            side.append((lat, list(1.0 / np.geomspace(0.8, 2.2, T))))
+        for k, L in enumerate(UNEVEN_ISING):
+            side.append((sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=60 + k), [0.4407]))
+        return side
+
+    batch, plain = build(), build()
+    items, sers = [], []
+    for lat, betas in batch:
+        ser = lat.series_buffers(n)
+        if lat.n_sets < 2:
+            ser.pop("Q", None)
+        sers.append(ser)
+        items.append(lat.batch_item(betas, ser))
+    sp.batch_run(items, n, 1, 1)
+    batch[0][0].sync()
+    for (lb, _), (lp, betas), ser in zip(batch, plain, sers):
+        out = lp.run(betas, n, 1, 1 if lp.model == B.SPIN_EA else 0)
+        assert torch.equal(lb.spins, lp.spins), lb.L
+        for key in ser:
+            assert torch.equal(ser[key], out[key]), (lb.L, key)
+    for (lat, betas), (L, R, T), r in zip(batch, UNEVEN_EA, (511, 200, 64, 33, 31)):
+        if L not in (12, 32):
+            continue
+        seed = lat.seed
+        J = oracle.ea_couplings(3, L, r, seed)
+        s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t), bit=r & 31)
+                                for t in range(T)]) for a in range(2)]).copy()
+        Es, Qs, _, _ = oracle.pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J)
+        got = lat.unpack()[:, :, r].cpu().numpy()
+        assert np.array_equal(got, s), L
+        E = sers[UNEVEN_EA.index((L, R, T))]["E"].view(n, 2, T, R)[:, :, :, r].cpu().numpy()
+        assert np.array_equal(E, Es), L

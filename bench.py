@@ -199,6 +199,29 @@ def side_configs(torch, sp, B, stream):
     out["ea_L16_pt_batched_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
     ea.close()
     out.update(uneven_batch(torch, sp, B, stream))
+    out.update(ising_pt(torch, sp, B, stream))
+    return out
+
+
+def ising_pt(torch, sp, B, stream):
+    """The paper's tempering benchmark for the 2D ferromagnet (Sec. 7): 20
+    int8 replicas at equally spaced beta in [0.1, 0.15], one exchange step
+    per 100 (and per 10) sweeps; flips/ns counts spin flips of all replicas."""
+    import numpy as np
+    out = {}
+    betas = list(np.linspace(0.1, 0.15, 20))
+    for Lp, every, n in ((64, 100, 400), (2048, 100, 200), (2048, 10, 200)):
+        lat = sp.Lattice(B.SPIN_ISING, 2, Lp, B.SPIN_I8, n_temps=20, seed=70)
+        lat.set_variant(1)
+        B.spin_run(lat.h, None, betas, every, 0, every, None, None, None, None, None, None)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_run(lat.h, None, betas, n, 0, every, None, None, None, None, None, None)
+        b.record(stream)
+        torch.cuda.synchronize()
+        lat.sync()
+        out[f"ising2d_pt20_L{Lp}_every{every}_flips_per_ns"] = n * 20 * Lp * Lp / (a.elapsed_time(b) * 1e6)
+        lat.close()
     return out
 
 
@@ -431,6 +454,9 @@ def run_case(name):
             B.spin_batch_run(item, 4, 1, 1, stream.cuda_stream)
             b.record(stream)
             flips = 4 * 2 ** 28
+    elif name == "ising_pt":
+        print(json.dumps({"case": name, **ising_pt(torch, sp, B, stream)}), flush=True)
+        return
     elif name == "uneven":
         print(json.dumps({"case": name, **uneven_batch(torch, sp, B, stream, n=8)}), flush=True)
         return
@@ -464,7 +490,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, uneven)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, uneven, ising_pt)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

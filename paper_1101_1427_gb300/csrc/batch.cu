@@ -55,6 +55,7 @@ struct BatchUnit {
   int *Escr;            // [n_sets][n_T][32] unsatisfied-bond counts
   // Ising
   int8_t *s;
+  FastDiv fC;           // divides by the L / 8 chunks of 8 sites in a row
   long long lat_index;
   uint32_t lid;
   int slot;
@@ -311,40 +312,89 @@ __device__ __forceinline__ void ea_phase_warp(uint32_t *__restrict__ s, const ui
 
 // Counts per bit the words a[i] (or a[i] ^ b[i]) for i = lane, lane + 32, ...
 __device__ __forceinline__ void count_words(HsCount &hc, const uint32_t *a, const uint32_t *b, uint32_t N,
-                                            int lane) {
-  uint32_t i = (uint32_t)lane;
-  for (; i + 7 * 32 < N; i += 8 * 32) {
+                                            uint32_t first, uint32_t stride) {
+  uint32_t i = first;
+  for (; i + 7 * stride < N; i += 8 * stride) {
     uint32_t x[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) x[k] = b ? (a[i + 32 * k] ^ b[i + 32 * k]) : a[i + 32 * k];
+    for (int k = 0; k < 8; ++k) x[k] = b ? (a[i + stride * k] ^ b[i + stride * k]) : a[i + stride * k];
     hc.add8(x);
   }
   hc.flush();
-  for (; i < N; i += 32) add1(hc.C, b ? (a[i] ^ b[i]) : a[i]);
+  for (; i < N; i += stride) add1(hc.C, b ? (a[i] ^ b[i]) : a[i]);
+}
+
+// Per-bit counts of the set bits of n_items word arrays of N words each
+// (item k: a_k[i], or a_k[i] ^ b_k[i]), every item split over several warps
+// when there are fewer items than warps; cnt[k][b] receives item k's count
+// for bit b.  Called by the whole CTA.
+template <typename ItemFn>
+__device__ void cta_bit_counts(int n_items, uint32_t N, ItemFn item, int (*cnt)[32]) {
+  __syncthreads();
+  for (int k = threadIdx.x; k < n_items * 32; k += kThreads) (&cnt[0][0])[k] = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpi = n_items >= kWarps ? 1 : kWarps / n_items;
+  for (int k = warp / wpi; k < n_items; k += kWarps / wpi) {
+    const uint32_t *a = nullptr, *b = nullptr;
+    item(k, a, b);
+    HsCount hc;
+    count_words(hc, a, b, N, (uint32_t)((warp % wpi) * 32 + lane), (uint32_t)(wpi * 32));
+    const int c = warp_bit_counts(hc.C);
+    if (wpi == 1) cnt[k][lane] = c;
+    else atomicAdd(&cnt[k][lane], c);
+  }
+  __syncthreads();
+}
+
+// Bitwise exchange of the bits set in A between two word arrays of N words
+// (N a multiple of 4, 16-byte aligned), by the whole CTA.
+__device__ __forceinline__ void cta_swap_bits(uint32_t *w0, uint32_t *w1, uint32_t N, uint32_t A) {
+  uint4 *v0 = reinterpret_cast<uint4 *>(w0), *v1 = reinterpret_cast<uint4 *>(w1);
+  const uint32_t n4 = N >> 2;
+  uint32_t i = threadIdx.x;
+  for (; i + kThreads < n4; i += 2 * kThreads) {
+    uint4 x0 = v0[i], x1 = v1[i], y0 = v0[i + kThreads], y1 = v1[i + kThreads];
+    uint4 d = make_uint4((x0.x ^ x1.x) & A, (x0.y ^ x1.y) & A, (x0.z ^ x1.z) & A, (x0.w ^ x1.w) & A);
+    uint4 e = make_uint4((y0.x ^ y1.x) & A, (y0.y ^ y1.y) & A, (y0.z ^ y1.z) & A, (y0.w ^ y1.w) & A);
+    v0[i] = make_uint4(x0.x ^ d.x, x0.y ^ d.y, x0.z ^ d.z, x0.w ^ d.w);
+    v1[i] = make_uint4(x1.x ^ d.x, x1.y ^ d.y, x1.z ^ d.z, x1.w ^ d.w);
+    v0[i + kThreads] = make_uint4(y0.x ^ e.x, y0.y ^ e.y, y0.z ^ e.z, y0.w ^ e.w);
+    v1[i + kThreads] = make_uint4(y1.x ^ e.x, y1.y ^ e.y, y1.z ^ e.z, y1.w ^ e.w);
+  }
+  for (; i < n4; i += kThreads) {
+    const uint4 x0 = v0[i], x1 = v1[i];
+    const uint4 d = make_uint4((x0.x ^ x1.x) & A, (x0.y ^ x1.y) & A, (x0.z ^ x1.z) & A, (x0.w ^ x1.w) & A);
+    v0[i] = make_uint4(x0.x ^ d.x, x0.y ^ d.y, x0.z ^ d.z, x0.w ^ d.w);
+    v1[i] = make_uint4(x1.x ^ d.x, x1.y ^ d.y, x1.z ^ d.z, x1.w ^ d.w);
+  }
 }
 
 // ---------------------------------------------------------------- EA unit
 __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, const RoundKeys &rk,
                          Sync &sy, uint32_t s_abs, bool measure, bool pt, long long meas_row,
                          uint32_t pt_step) {
-  __shared__ int e_cnt[64][32];   // per owned word-lattice (set, slot) counts
-  __shared__ uint32_t masks[64];  // accept masks per (set, owned pair)
-  const int P = U.team_size;
-  const int t0 = part * U.n_T / P, t1 = (part + 1) * U.n_T / P;
-  const int nt_own = t1 - t0;
-  const int n_w = U.n_sets * nt_own;  // owned word-lattices, <= 64
+  __shared__ int e_cnt[64][32];   // per owned word-lattice counts (energies, then M, then Q)
+  __shared__ uint32_t masks[64];  // accept masks per owned word-lattice that starts a pair
+  // Owned word-lattices, numbered g = t * n_sets + a: whole slots while the
+  // team has at most n_T CTAs, single word-lattices beyond that.
+  const int P = U.team_size, W = U.n_T * U.n_sets;
+  const int g0 = P <= U.n_T ? (part * U.n_T / P) * U.n_sets : part * W / P;
+  const int g1 = P <= U.n_T ? ((part + 1) * U.n_T / P) * U.n_sets : (part + 1) * W / P;
+  const int n_w = g1 - g0;  // <= 64
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // warps per word-lattice when there are fewer word-lattices than warps
   const int wpw = n_w >= kWarps ? 1 : kWarps / n_w;
   const bool need_e = measure || pt;
+  const uint32_t N = U.N;
+  auto words = [&](int a, int t) { return U.w + a * U.set_stride + (size_t)t * N; };
   for (int colour = 0; colour < 2; ++colour) {
     if (colour == 1 && need_e)
       for (int k = threadIdx.x; k < n_w * 32; k += kThreads) (&e_cnt[0][0])[k] = 0;
     if (colour == 1) __syncthreads();
     for (int wi = warp / wpw; wi < n_w; wi += kWarps / wpw) {
-      if (warp / wpw >= n_w) break;
-      const int a = wi / nt_own, t = t0 + wi % nt_own;
-      uint32_t *s = U.w + a * U.set_stride + (size_t)t * U.N;
+      const int g = g0 + wi, a = g % U.n_sets, t = g / U.n_sets;
+      uint32_t *s = words(a, t);
       const uint32_t lid = lattice_id((uint32_t)a, (uint32_t)U.grp, (uint32_t)t);
       const uint32_t t4 = __ldg(U.thr + 4 * t + 1), t8 = __ldg(U.thr + 4 * t + 2), t12 = __ldg(U.thr + 4 * t + 3);
       const uint32_t first = (uint32_t)((warp % wpw) * 32 + lane), stride = (uint32_t)(wpw * 32);
@@ -362,11 +412,10 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
     }
     __syncthreads();
   }
-  const uint32_t N = U.N;
   if (need_e) {
     for (int k = threadIdx.x; k < n_w * 32; k += kThreads) {
       const int wi = k >> 5, b = k & 31;
-      const int a = wi / nt_own, t = t0 + wi % nt_own;
+      const int g = g0 + wi, a = g % U.n_sets, t = g / U.n_sets;
       const int unsat = e_cnt[wi][b];
       U.Escr[(a * U.n_T + t) * 32 + b] = unsat;
       if (measure && U.E_series) {
@@ -375,47 +424,57 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
       }
     }
   }
-  if (measure && (U.Q_series || U.M_series)) {
-    // overlap between sets 0 and 1 and magnetisation, owned slots
-    for (int wi = warp; wi < nt_own * 2; wi += kWarps) {
-      const int t = t0 + (wi >> 1);
-      const bool do_m = (wi & 1) == 0;
-      if (do_m && !U.M_series) continue;
-      if (!do_m && (!U.Q_series || U.n_sets < 2)) continue;
-      HsCount hc;
-      // (M is accumulated for set 0 only here; other sets below)
-      const uint32_t *s0 = U.w + (size_t)t * N;
-      const uint32_t *s1 = s0 + U.set_stride;
-      count_words(hc, s0, do_m ? nullptr : s1, N, lane);
-      const int cnt = warp_bit_counts(hc.C);
-      const long long r = 32 * U.grp + lane;
-      if (do_m) U.M_series[meas_row * U.n_lat + (long long)t * U.n_real + r] = (long long)N - 2LL * cnt;
-      else U.Q_series[meas_row * (long long)U.n_T * U.n_real + (long long)t * U.n_real + r] = (long long)N - 2LL * cnt;
+  const long long r0 = 32 * U.grp;
+  if (measure && U.M_series) {  // magnetisation of every owned word-lattice
+    cta_bit_counts(n_w, N, [&](int k, const uint32_t *&x, const uint32_t *&y) {
+      x = words((g0 + k) % U.n_sets, (g0 + k) / U.n_sets);
+      y = nullptr;
+    }, e_cnt);
+    for (int k = threadIdx.x; k < n_w * 32; k += kThreads) {
+      const int g = g0 + (k >> 5), a = g % U.n_sets, t = g / U.n_sets;
+      U.M_series[meas_row * U.n_lat + ((long long)a * U.n_T + t) * U.n_real + r0 + (k & 31)] =
+          (long long)N - 2LL * e_cnt[k >> 5][k & 31];
     }
-    if (U.M_series)
-      for (int a = 1; a < U.n_sets; ++a)
-        for (int wi = warp; wi < nt_own; wi += kWarps) {
-          const int t = t0 + wi;
-          HsCount hc;
-          const uint32_t *sa = U.w + a * U.set_stride + (size_t)t * N;
-          count_words(hc, sa, nullptr, N, lane);
-          const int cnt = warp_bit_counts(hc.C);
-          U.M_series[meas_row * U.n_lat + ((long long)a * U.n_T + t) * U.n_real + 32 * U.grp + lane] =
-              (long long)N - 2LL * cnt;
-        }
   }
-  if (!pt) {
+  // overlap of sets 0 and 1 for every slot whose set-0 word-lattice is
+  // owned; its set-1 word-lattice may belong to another CTA of the team
+  const bool do_q = measure && U.Q_series && U.n_sets >= 2;
+  const bool q_cross = P > U.n_T;
+  const int gq0 = (g0 + U.n_sets - 1) / U.n_sets, gq1 = (g1 + U.n_sets - 1) / U.n_sets;  // slots
+  auto overlap = [&]() {
+    const int n_q = gq1 - gq0;
+    if (n_q <= 0) {
+      __syncthreads();
+      return;
+    }
+    cta_bit_counts(n_q, N, [&](int k, const uint32_t *&x, const uint32_t *&y) {
+      x = words(0, gq0 + k);
+      y = words(1, gq0 + k);
+    }, e_cnt);
+    for (int k = threadIdx.x; k < n_q * 32; k += kThreads)
+      U.Q_series[meas_row * (long long)U.n_T * U.n_real + (long long)(gq0 + (k >> 5)) * U.n_real + r0 +
+                 (k & 31)] = (long long)N - 2LL * e_cnt[k >> 5][k & 31];
+  };
+  if (do_q && !q_cross) overlap();
+  if (!pt && !(do_q && q_cross)) {
     __syncthreads();  // measurements read words the next sweep rewrites
     return true;
   }
-  if (!team_barrier(sy)) return false;  // energies of all slots visible
-  // decisions for pairs (t, t+1) with t owned, t = step parity (mod 2)
+  if (!team_barrier(sy)) return false;  // energies and words of all slots visible
+  if (do_q && q_cross) {
+    overlap();
+    if (!team_barrier(sy)) return false;  // overlap reads done before any word changes
+  }
+  if (!pt) return true;
+  // decisions for pairs (t, t+1) of set a, t = step parity (mod 2), made by
+  // the owner of (a, t), which then exchanges the two word-lattices
   const int parity = (int)(pt_step & 1u);
-  int n_pairs = 0;
-  for (int t = t0 + ((t0 - parity) & 1); t < t1 && t + 1 < U.n_T; t += 2) ++n_pairs;
-  const int tp0 = t0 + ((t0 - parity) & 1);
-  for (int k = warp; k < U.n_sets * n_pairs; k += kWarps) {
-    const int a = k / n_pairs, t = tp0 + 2 * (k % n_pairs);
+  for (int k = warp; k < n_w; k += kWarps) {
+    const int g = g0 + k, a = g % U.n_sets, t = g / U.n_sets;
+    if (((t - parity) & 1) != 0 || t + 1 >= U.n_T) {
+      if (lane == 0) masks[k] = 0u;
+      continue;
+    }
     const int r = 32 * U.grp + lane;
     const int e0 = U.Escr[(a * U.n_T + t) * 32 + lane], e1 = U.Escr[(a * U.n_T + t + 1) * 32 + lane];
     const long long dE = 2LL * (e1 - e0);
@@ -437,95 +496,130 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
     }
   }
   __syncthreads();
-  // exchange: for every owned pair and site, the accepted bits change places
-  for (int k = 0; k < U.n_sets * n_pairs; ++k) {
+  for (int k = 0; k < n_w; ++k) {
     const uint32_t A = masks[k];
     if (!A) continue;
-    const int a = k / n_pairs, t = tp0 + 2 * (k % n_pairs);
-    uint32_t *w0 = U.w + a * U.set_stride + (size_t)t * N, *w1 = w0 + N;
-    for (uint32_t i = threadIdx.x; i < N; i += kThreads) {
-      const uint32_t x0 = w0[i], x1 = w1[i];
-      const uint32_t x = (x0 ^ x1) & A;
-      w0[i] = x0 ^ x;
-      w1[i] = x1 ^ x;
-    }
+    const int g = g0 + k, a = g % U.n_sets, t = g / U.n_sets;
+    cta_swap_bits(words(a, t), words(a, t + 1), N, A);
   }
   return team_barrier(sy);  // exchanged words visible before the next sweep
 }
 
 // ---------------------------------------------------------------- Ising unit
-__device__ void ising_rows_phase(const BatchUnit &U, const RoundKeys &rk, uint32_t sweep, int colour,
-                                 int r0, int r1) {
-  const int L = U.L, chunks = L >> 3;
+// One chunk of 8 sites (a row segment, int8 +-1) whose sites of the phase's
+// colour sit at byte offsets p, p + 2, p + 4, p + 6: returns the chunk with
+// those sites updated.  Only bytes of the other colour are read around
+// them, and the phase never changes those.  kCount 1: adds the updated
+// sites' number of -1 spins after the update to down; kCount 2: also their
+// post-update number of antiparallel neighbours to anti.
+template <int kCount>
+__device__ __forceinline__ uint64_t ising_chunk(uint64_t C, uint64_t Uw, uint64_t Dw, uint64_t lb, uint64_t rb,
+                                                const uint4 &r, int p, uint32_t thr4, uint32_t thr8,
+                                                long long &anti, long long &down) {
+  const uint64_t MASK = 0x0202020202020202ull;  // bit 1 of each byte: 1 for -1, 0 for +1
+  const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);
+  // per byte: twice the number of antiparallel neighbours
+  const uint64_t A = ((C ^ Uw) & MASK) + ((C ^ Dw) & MASK) + ((C ^ Lw) & MASK) + ((C ^ Rw) & MASK);
+  const uint64_t An = A >> (8 * p);
+  const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
+  // dE <= 0 (at least two antiparallel neighbours): flip
+  const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
+  const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
+  // one antiparallel neighbour: dE = 4; none: dE = 8
+  const uint32_t q0 = (lo & 0x2u) ? thr4 : thr8, q1 = (lo & 0x20000u) ? thr4 : thr8;
+  const uint32_t q2 = (hi & 0x2u) ? thr4 : thr8, q3 = (hi & 0x20000u) ? thr4 : thr8;
+  const uint32_t f_lo = g_lo | (uint32_t)(r.x < q0) | ((uint32_t)(r.y < q1) << 16);
+  const uint32_t f_hi = g_hi | (uint32_t)(r.z < q2) | ((uint32_t)(r.w < q3) << 16);
+  if (kCount == 2) {
+    const uint32_t n0 = (lo >> 1) & 7u, n1 = (lo >> 17) & 7u, n2 = (hi >> 1) & 7u, n3 = (hi >> 17) & 7u;
+    anti += (long long)((f_lo & 1u) ? 4u - n0 : n0) + ((f_lo >> 16) ? 4u - n1 : n1) +
+            ((f_hi & 1u) ? 4u - n2 : n2) + ((f_hi >> 16) ? 4u - n3 : n3);
+  }
+  if (kCount >= 1) {
+    const uint64_t old_down = (C >> (8 * p)) & 0x0002000200020002ull;
+    const uint64_t flips = ((uint64_t)f_hi << 33) | ((uint64_t)f_lo << 1);
+    down += __popcll(old_down ^ flips);
+  }
+  return C ^ ((((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu)) << (8 * p));
+}
+
+// One colour phase over the rows [r0, r1) of a 2D int8 lattice: four chunks
+// per thread and iteration, all their loads issued before any store.
+template <int kCount>
+__device__ void ising_rows_phase(const BatchUnit &U, const RoundKeys &rk, uint32_t sweep, int colour, int r0,
+                                 int r1, long long &anti, long long &down) {
+  const int L = U.L;
+  const uint32_t chunks = (uint32_t)L >> 3;
   const uint32_t thr4 = __ldg(U.thr + 4 * U.slot + 1), thr8 = __ldg(U.thr + 4 * U.slot + 2);
-  const uint64_t MASK = 0x0202020202020202ull;
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
-  const int total = (r1 - r0) * chunks;
-  for (int k = threadIdx.x; k < total; k += kThreads) {
-    const int y = r0 + k / chunks, m = k % chunks;
-    int8_t *base = U.s;
-    const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
-    uint64_t *rowp = reinterpret_cast<uint64_t *>(base + (int64_t)y * L);
-    const uint64_t C = rowp[m];
-    const uint64_t Uw = reinterpret_cast<const uint64_t *>(base + (int64_t)yu * L)[m];
-    const uint64_t Dw = reinterpret_cast<const uint64_t *>(base + (int64_t)yd * L)[m];
-    const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
-    const uint64_t lb = (uint8_t)base[(int64_t)y * L + xl], rb = (uint8_t)base[(int64_t)y * L + xr];
-    const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);
-    const uint64_t A = ((C ^ Uw) & MASK) + ((C ^ Dw) & MASK) + ((C ^ Lw) & MASK) + ((C ^ Rw) & MASK);
-    const uint4 r = philox(make_uint4((uint32_t)y * (uint32_t)chunks + (uint32_t)m, sweep, U.lid, wctr), rk);
-    const int p = (colour + y) & 1;
-    const uint64_t An = A >> (8 * p);
-    const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
-    const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
-    const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
-    const uint32_t q0 = (lo & 0x2u) ? thr4 : thr8, q1 = (lo & 0x20000u) ? thr4 : thr8;
-    const uint32_t q2 = (hi & 0x2u) ? thr4 : thr8, q3 = (hi & 0x20000u) ? thr4 : thr8;
-    const uint32_t f_lo = g_lo | (uint32_t)(r.x < q0) | ((uint32_t)(r.y < q1) << 16);
-    const uint32_t f_hi = g_hi | (uint32_t)(r.z < q2) | ((uint32_t)(r.w < q3) << 16);
-    const uint64_t F = (((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu)) << (8 * p);
-    rowp[m] = C ^ F;
+  const uint32_t total = (uint32_t)(r1 - r0) * chunks;
+  int8_t *base = U.s;
+  constexpr int kU = 4;  // chunks per thread and iteration
+  for (uint32_t k = threadIdx.x; k < total; k += kU * kThreads) {
+    int y[kU];
+    uint32_t m[kU];
+    uint64_t C[kU], Uw[kU], Dw[kU], lb[kU], rb[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      // a chunk beyond the range repeats chunk k and is not stored
+      const uint32_t kj = k + j * kThreads < total ? k + j * kThreads : k;
+      const uint32_t dy = fdiv(kj, U.fC);
+      y[j] = r0 + (int)dy;
+      m[j] = kj - dy * chunks;
+      const int yu = y[j] == 0 ? L - 1 : y[j] - 1, yd = y[j] == L - 1 ? 0 : y[j] + 1;
+      const int8_t *row = base + (int64_t)y[j] * L;
+      C[j] = reinterpret_cast<const uint64_t *>(row)[m[j]];
+      Uw[j] = reinterpret_cast<const uint64_t *>(base + (int64_t)yu * L)[m[j]];
+      Dw[j] = reinterpret_cast<const uint64_t *>(base + (int64_t)yd * L)[m[j]];
+      lb[j] = (uint8_t)row[m[j] == 0 ? L - 1 : 8 * m[j] - 1];
+      rb[j] = (uint8_t)row[m[j] == chunks - 1 ? 0 : 8 * m[j] + 8];
+    }
+    // the generator blocks first, as independent chains
+    uint4 q[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) q[j] = philox(make_uint4((uint32_t)y[j] * chunks + m[j], sweep, U.lid, wctr), rk);
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      long long a2 = 0, d2 = 0;
+      const uint64_t nw =
+          ising_chunk<kCount>(C[j], Uw[j], Dw[j], lb[j], rb[j], q[j], (colour + y[j]) & 1, thr4, thr8, a2, d2);
+      if (k + j * kThreads < total) {
+        reinterpret_cast<uint64_t *>(base + (int64_t)y[j] * L)[m[j]] = nw;
+        anti += a2;
+        down += d2;
+      }
+    }
   }
 }
 
+// One sweep of the team's rows.  Measurements come out of the phases: the
+// magnetisation from the sites each phase updated, the energy from the
+// updated sites of colour 1, since every bond has exactly one such end.
 __device__ bool ising_sweep(const BatchUnit &U, int part, const RoundKeys &rk, Sync &sy, uint32_t s_abs,
                             bool measure, long long meas_row) {
   const int P = U.team_size;
   const int r0 = part * U.L / P, r1 = (part + 1) * U.L / P;
+  const bool count = measure && (U.E_series || U.M_series);
+  long long anti = 0, down = 0;
   for (int colour = 0; colour < 2; ++colour) {
-    ising_rows_phase(U, rk, s_abs, colour, r0, r1);
+    if (!count) ising_rows_phase<0>(U, rk, s_abs, colour, r0, r1, anti, down);
+    else if (colour == 0) ising_rows_phase<1>(U, rk, s_abs, 0, r0, r1, anti, down);
+    else ising_rows_phase<2>(U, rk, s_abs, 1, r0, r1, anti, down);
+    if (colour == 1 && count) {
+      anti = warp_sum(anti);
+      down = warp_sum(down);
+      if ((threadIdx.x & 31) == 0) {
+        const long long N = (long long)U.N;
+        const long long idx = meas_row * U.n_lat + U.lat_index;
+        // the series entries were zeroed before the launch; part 0 adds the constants
+        const bool first = part == 0 && threadIdx.x == 0;
+        if (U.E_series)
+          atomicAdd((unsigned long long *)&U.E_series[idx], (unsigned long long)(2 * anti - (first ? 2 * N : 0)));
+        if (U.M_series)
+          atomicAdd((unsigned long long *)&U.M_series[idx], (unsigned long long)(-2 * down + (first ? N : 0)));
+      }
+    }
     if (!team_barrier(sy)) return false;
-  }
-  if (measure && (U.E_series || U.M_series)) {
-    const int L = U.L, segs = L >> 4;
-    const uint64_t B1 = 0x0202020202020202ull;
-    long long anti = 0, down = 0;
-    for (int k = threadIdx.x; k < (r1 - r0) * segs; k += kThreads) {
-      const int y = r0 + k / segs, sg = k % segs;
-      const int8_t *row = U.s + (int64_t)y * L;
-      const int8_t *nrow = U.s + (int64_t)(y == L - 1 ? 0 : y + 1) * L;
-      const uint4 c = *reinterpret_cast<const uint4 *>(row + 16 * sg);
-      const uint4 d = *reinterpret_cast<const uint4 *>(nrow + 16 * sg);
-      const uint64_t c0 = (uint64_t)c.x | ((uint64_t)c.y << 32), c1 = (uint64_t)c.z | ((uint64_t)c.w << 32);
-      const uint64_t d0 = (uint64_t)d.x | ((uint64_t)d.y << 32), d1 = (uint64_t)d.z | ((uint64_t)d.w << 32);
-      const uint64_t nb = (uint8_t)row[sg == segs - 1 ? 0 : 16 * sg + 16];
-      const uint64_t q0 = (c0 >> 8) | (c1 << 56), q1 = (c1 >> 8) | (nb << 56);
-      anti += __popcll((c0 ^ q0) & B1) + __popcll((c1 ^ q1) & B1) + __popcll((c0 ^ d0) & B1) +
-              __popcll((c1 ^ d1) & B1);
-      down += __popcll(c0 & B1) + __popcll(c1 & B1);
-    }
-    anti = warp_sum(anti);
-    down = warp_sum(down);
-    if ((threadIdx.x & 31) == 0) {
-      const long long N = (long long)U.N;
-      const long long idx = meas_row * U.n_lat + U.lat_index;
-      // the series entries were zeroed before the launch; part 0 adds the constants
-      if (U.E_series) atomicAdd((unsigned long long *)&U.E_series[idx],
-                                (unsigned long long)(2 * anti - ((part == 0 && threadIdx.x == 0) ? 2 * N : 0)));
-      if (U.M_series) atomicAdd((unsigned long long *)&U.M_series[idx],
-                                (unsigned long long)(-2 * down + ((part == 0 && threadIdx.x == 0) ? N : 0)));
-    }
-    if (!team_barrier(sy)) return false;  // rows read across the strip edge
   }
   return true;
 }
@@ -625,7 +719,8 @@ static double unit_work(const BatchUnit &U) {
 // Distributes `grid` CTAs over the units: every unit gets its minimum (EA:
 // at most 64 owned word-lattices per CTA; Ising: 1), then CTAs go one by
 // one to the unit with the largest work per CTA, up to each unit's maximum
-// (EA: one slot per CTA; Ising: 8 rows per CTA).  Returns the CTAs used.
+// (EA: one word-lattice per CTA; Ising: 8 rows per CTA).  Returns the CTAs
+// used.
 static int assign_teams(BatchUnit *units, int n, int grid) {
   std::vector<int> P(n), cap(n);
   int used = 0;
@@ -635,7 +730,7 @@ static int assign_teams(BatchUnit *units, int n, int grid) {
       int p = 1;
       while (units[u].n_sets * ((units[u].n_T + p - 1) / p) > 64) ++p;
       P[u] = p;
-      cap[u] = units[u].n_T;
+      cap[u] = units[u].n_T * units[u].n_sets;  // one word-lattice per CTA at most
     } else {
       P[u] = 1;
       cap[u] = std::max(1, units[u].L / 8);
@@ -777,6 +872,7 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.ctr = (const long long *)h->d_ctr;
         U.bar = h->d_bar + lat;
         U.s = (int8_t *)h->spins + lat * g.N;
+        U.fC = make_fastdiv((uint32_t)(g.L / 8));
         U.E_series = (long long *)items[k].E_series;
         U.M_series = (long long *)items[k].M_series;
         U.n_lat = h->n_lat;

@@ -60,6 +60,7 @@ def lib():
                                 p, p, p, p]
         L.or_ising_window_sweeps.argtypes = [i32, i32, p, i32, p, dbl, u64, u32, u32, i32]
         L.or_ising_init_sites.argtypes = [i64, p, p, u64, u32, i32]
+        L.or_dcb_sweeps.argtypes = [i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
         _lib = L
     return _lib
 
@@ -165,6 +166,15 @@ def pt_run(dim, L, spins, betas, seed, r, rkey, first_sweep, n_sweeps, pt_every,
     lib().or_pt_run(dim, L, n_temps, n_sets, _ptr(spins), _ptr(J), _ptr(b), seed, r, rkey,
                     first_sweep, n_sweeps, pt_every, _ptr(step), _ptr(E), _ptr(Q), _ptr(acc))
     return E, Q, acc, int(step[0])
+
+
+def dcb_sweeps(L, s, beta, seed, lid, first_sweep, n_sweeps, T, k, symmetric=False, J=None):
+    """Double checkerboard multi-hit sweeps of a 2D int8 lattice in place
+    (n_sweeps updates per site, a multiple of k); returns the flip count."""
+    flips = np.zeros(1, np.int64)
+    lib().or_dcb_sweeps(L, _ptr(s), _ptr(J), beta, seed, lid, first_sweep, n_sweeps, T, k,
+                        int(bool(symmetric)), _ptr(flips))
+    return int(flips[0])
 
 
 def window_sweeps(dim, L, origin, W, win, beta, seed, lid, first_sweep, n_sweeps):

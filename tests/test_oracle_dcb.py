@@ -1,0 +1,118 @@
+"""Pins of the oracle's double-checkerboard multi-hit order (Sec. 3.2, 3.4):
+the exact distribution of the state after one compound move (propagated
+over all 2^16 states of a 4 x 4 torus, one single-site Metropolis kernel at
+a time in the order the paper describes), the beta = 0 limit, and long-run
+sampling against exact enumeration."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from tests.stats import assert_within, binned_mean
+
+L4, T2 = 4, 2
+
+
+def _sites(L, T, coarse, colour):
+    out = []
+    for i in range(L * L):
+        x, y = i % L, i // L
+        if ((x // T + y // T) & 1) == coarse and ((x + y) & 1) == colour:
+            out.append(i)
+    return out
+
+
+def _exact_after_compound(s0, beta, T, k, first_coarse):
+    """Distribution over the 2^(L^2) states (bit i set: s_i = -1) after one
+    compound move from s0: the tiles of coarse colour `first_coarse` get k
+    hits (fine colour 0 sites, then fine colour 1), then the other tiles."""
+    L = int(round(np.sqrt(s0.size)))
+    n = L * L
+    states = np.arange(1 << n, dtype=np.int64)
+    spins = 1 - 2 * ((states[:, None] >> np.arange(n)) & 1)  # [state, site]
+    nb = []
+    for i in range(n):
+        x, y = i % L, i // L
+        nb.append([((x + 1) % L) + L * y, ((x - 1) % L) + L * y, x + L * ((y + 1) % L), x + L * ((y - 1) % L)])
+    dist = np.zeros(1 << n)
+    start = int(sum(1 << i for i in range(n) if s0[i] < 0))
+    dist[start] = 1.0
+
+    def apply_site(d, i):
+        h = spins[:, nb[i]].sum(axis=1)
+        dE = 2 * spins[:, i] * h
+        p = np.where(dE <= 0, 1.0, np.exp(-beta * dE.astype(np.float64)))
+        moved = d * p
+        return d * (1.0 - p) + moved[states ^ (1 << i)]
+
+    for cc in range(2):
+        coarse = first_coarse ^ cc
+        for _ in range(k):
+            for colour in range(2):
+                for i in _sites(L, T, coarse, colour):
+                    dist = apply_site(dist, i)
+    return dist, spins
+
+
+@pytest.mark.parametrize("k,symmetric,compound", [(2, False, 0), (2, True, 1), (3, True, 2), (1, False, 5)])
+def test_one_compound_matches_exact_distribution(k, symmetric, compound):
+    beta = 0.4
+    s0 = np.ones(L4 * L4, np.int8)
+    s0[[0, 5, 6, 11, 14]] = -1
+    first = 1 if (symmetric and compound % 2 == 1) else 0
+    dist, spins = _exact_after_compound(s0, beta, T2, k, first)
+    p_down = (dist[:, None] * (spins < 0)).sum(axis=0)
+    e_states = -(spins * np.roll(spins.reshape(-1, L4, L4), -1, 2).reshape(-1, L4 * L4)).sum(1) - \
+        (spins * np.roll(spins.reshape(-1, L4, L4), -1, 1).reshape(-1, L4 * L4)).sum(1)
+    n_samp = 30000
+    down = np.zeros(L4 * L4)
+    e_hist = {}
+    for seed in range(1, n_samp + 1):
+        s = s0.copy()
+        oracle.dcb_sweeps(L4, s, beta, seed, 0, compound * k, k, T2, k, symmetric)
+        down += s < 0
+        e = oracle.ising_energy(2, L4, s)
+        e_hist[e] = e_hist.get(e, 0) + 1
+    freq = down / n_samp
+    sig = np.sqrt(np.maximum(p_down * (1 - p_down), 1e-4) / n_samp)
+    assert np.all(np.abs(freq - p_down) <= 4.5 * sig), (freq, p_down)
+    # energy distribution (chi-square over levels with enough weight)
+    levels = np.unique(e_states)
+    chi2, dof = 0.0, 0
+    for lv in levels:
+        p = dist[e_states == lv].sum()
+        if p * n_samp >= 20:
+            chi2 += (e_hist.get(int(lv), 0) - p * n_samp) ** 2 / (p * n_samp)
+            dof += 1
+    assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_infinite_temperature_flips_every_site_k_times(k):
+    """At beta = 0 every Metropolis update flips (threshold 2^32 - 1 misses
+    only the word 0xFFFFFFFF), so a compound move multiplies s by (-1)^k."""
+    L, T = 16, 4
+    lid = oracle.lattice_id(0, 0, 0)
+    s0 = oracle.ising_init(2, L, 3, lid)
+    s = s0.copy()
+    flips = oracle.dcb_sweeps(L, s, 0.0, 3, lid, 0, 4 * k, T, k, True)
+    assert flips == 4 * k * L * L
+    assert np.array_equal(s, s0)  # 4k flips per site
+    s = s0.copy()
+    oracle.dcb_sweeps(L, s, 0.0, 3, lid, 0, k, T, k, False)
+    assert np.array_equal(s, s0 * (-1) ** k)
+
+
+@pytest.mark.parametrize("k,symmetric", [(3, True), (4, False)])
+def test_long_run_matches_enumeration(k, symmetric):
+    beta = 0.4
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(2, L4, 17, lid)
+    n = 40000
+    E = np.empty(n)
+    for m in range(n):
+        oracle.dcb_sweeps(L4, s, beta, 17, lid, m * k, k, T2, k, symmetric)
+        E[m] = oracle.ising_energy(2, L4, s)
+    bf = exact.brute_force(2, L4, beta)
+    e_mc, e_err = binned_mean(E[200:])
+    assert_within(e_mc, e_err, bf["E"], what="<E>")

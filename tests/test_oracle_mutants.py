@@ -29,6 +29,18 @@ MUTANTS = {
                       "tests/test_oracle_pt_heis.py::test_heis_infinite_temperature_gives_uniform_proposals"),
     "philox_word": ("uint32_t n2 = hi0 ^ c3 ^ k1;", "uint32_t n2 = hi0 ^ c1 ^ k1;",
                     "tests/test_oracle_rng.py::test_philox_matches_curand_host_generator"),
+    "dcb_symmetric_order": ("const int first = (symmetric && (M & 1u)) ? 1 : 0;",
+                            "const int first = (symmetric && !(M & 1u)) ? 1 : 0;",
+                            "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
+    "dcb_fine_colour_order": ("for (int colour = 0; colour < 2; ++colour) {\n          for (int64_t i = 0; i < n; ++i) {\n            const int x",
+                              "for (int colour = 1; colour >= 0; --colour) {\n          for (int64_t i = 0; i < n; ++i) {\n            const int x",
+                              "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
+    "dcb_tile_colour": ("if (((x / T + y / T) & 1) != coarse) continue;",
+                        "if (((x % T + y / T) & 1) != coarse) continue;",
+                        "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
+    "dcb_hit_words": ("const uint32_t sweep = M * (uint32_t)k + (uint32_t)h;",
+                      "const uint32_t sweep = M * (uint32_t)k;",
+                      "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
 }
 
 

@@ -200,6 +200,27 @@ def side_configs(torch, sp, B, stream):
     ea.close()
     out.update(uneven_batch(torch, sp, B, stream))
     out.update(ising_pt(torch, sp, B, stream))
+    out.update(dcb(torch, sp, B, stream))
+    return out
+
+
+def dcb(torch, sp, B, stream):
+    """The paper's own update order (Sec. 3.2): double checkerboard with
+    multi-hit updates inside shared-memory tiles, on the three L=16384 int8
+    lattices of the headline workload."""
+    out = {}
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=len(BETAS), seed=21)
+    for T, k in ((16, 100), (64, 10), (64, 100)):
+        lat.set_update_order(B.SPIN_ORDER_DCB, T, k)
+        lat.set_counters(0, 0)
+        B.spin_sweep(lat.h, None, BETAS, k, lat.seed)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, BETAS, k, lat.seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"ising2d_dcb_T{T}_k{k}_flips_per_ns"] = k * len(BETAS) * L * L / (a.elapsed_time(b) * 1e6)
+    lat.close()
     return out
 
 
@@ -454,6 +475,9 @@ def run_case(name):
             B.spin_batch_run(item, 4, 1, 1, stream.cuda_stream)
             b.record(stream)
             flips = 4 * 2 ** 28
+    elif name == "dcb":
+        print(json.dumps({"case": name, **dcb(torch, sp, B, stream)}), flush=True)
+        return
     elif name == "ising_pt":
         print(json.dumps({"case": name, **ising_pt(torch, sp, B, stream)}), flush=True)
         return
@@ -490,7 +514,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, uneven, ising_pt)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, uneven, ising_pt, dcb)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

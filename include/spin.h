@@ -259,6 +259,36 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * paper's "fast_math" mode, Sec. 5), within the same tolerances. */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
+/* Update order of the sweeps of a handle.
+ *  SPIN_ORDER_CHECKERBOARD  all colour-0 sites, then all colour-1 sites
+ *                           (default; every other call here assumes it).
+ *  SPIN_ORDER_DCB           double checkerboard with multi-hit updates
+ *                           (Sec. 3.2, Fig. checker; Sec. 3.4): the lattice
+ *                           is cut into tile x tile tiles coloured like a
+ *                           checkerboard; a compound move gives the tiles of
+ *                           coarse colour 0 `hits` hits (fine colour 0,
+ *                           then fine colour 1, each hit) and then the
+ *                           tiles of coarse colour 1 the same way, so every
+ *                           site takes `hits` updates.  Hit h of compound
+ *                           move m draws with sweep number m * hits + h.
+ *  SPIN_ORDER_DCB_SYMMETRIC the same with coarse colour 1 first in odd
+ *                           compound moves (counted by sweeps / hits), so
+ *                           that the moves alternate A^k B^k and B^k A^k,
+ *                           the compound order of Sec. 3.4 that satisfies
+ *                           detailed balance.
+ * The double-checkerboard orders take 2D Ising ferromagnets in the int8
+ * layout, tile in {8, 16, 32, 64, 128} dividing L with L / tile even, and
+ * hits >= 1; spin_sweep then counts sweeps as updates per site and needs
+ * n_sweeps and the handle's sweep count to be multiples of hits (so must
+ * spin_run's measure_every and pt_every).  Such handles cannot join a
+ * batched launch.  tile and hits are ignored for SPIN_ORDER_CHECKERBOARD. */
+typedef enum {
+  SPIN_ORDER_CHECKERBOARD = 0,
+  SPIN_ORDER_DCB = 1,
+  SPIN_ORDER_DCB_SYMMETRIC = 2
+} spin_update_order;
+int spin_set_update_order(spin_lattice *lat, int32_t order, int32_t tile, int32_t hits);
+
 const char *spin_strerror(int code);
 void spin_destroy(spin_lattice *lat);
 

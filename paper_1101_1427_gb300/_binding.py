@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libspin_gb300.so")
 SPIN_OK, SPIN_EINVAL, SPIN_EALIGN, SPIN_ENOMEM, SPIN_ECUDA, SPIN_ETIMEOUT = 0, -1, -2, -3, -4, -5
 SPIN_ISING, SPIN_EA, SPIN_HEISENBERG = 0, 1, 2
 SPIN_I8, SPIN_MSC1, SPIN_F32X4 = 0, 1, 2
+SPIN_ORDER_CHECKERBOARD, SPIN_ORDER_DCB, SPIN_ORDER_DCB_SYMMETRIC = 0, 1, 2
 TAG_UPDATE, TAG_INIT, TAG_COUPLING, TAG_PT, TAG_HEIS, TAG_HEIS_INIT = range(6)
 
 
@@ -66,6 +67,7 @@ def lib():
         L.spin_pt_steps_done.restype = i64
         L.spin_set_counters.argtypes = [p, i64, i64]
         L.spin_set_variant.argtypes = [p, i32]
+        L.spin_set_update_order.argtypes = [p, i32, i32, i32]
         L.spin_strerror.argtypes = [C.c_int]
         L.spin_strerror.restype = C.c_char_p
         L.spin_destroy.argtypes = [p]
@@ -73,7 +75,7 @@ def lib():
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
-                     "spin_set_batch_options", "spin_heis_measure_noalloc"):
+                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -214,6 +216,10 @@ def spin_set_counters(h, sweeps_done, pt_steps_done):
 
 def spin_set_variant(h, variant):
     return _check(lib().spin_set_variant(h, variant), "spin_set_variant")
+
+
+def spin_set_update_order(h, order, tile=0, hits=1):
+    return _check(lib().spin_set_update_order(h, order, tile, hits), "spin_set_update_order")
 
 
 def spin_destroy(h):

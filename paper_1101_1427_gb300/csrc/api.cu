@@ -245,9 +245,13 @@ int spin_sweep(spin_lattice *h, const void *couplings, const double *betas, int6
   if (ea(h) && !couplings) return SPIN_EINVAL;
   if (couplings && !aligned16(couplings)) return SPIN_EALIGN;
   if (h->sweeps_done + n_sweeps > (int64_t)0xFFFFFFFFll) return SPIN_EINVAL;
+  if (h->order != SPIN_ORDER_CHECKERBOARD &&
+      (n_sweeps % h->order_hits != 0 || h->sweeps_done % h->order_hits != 0))
+    return SPIN_EINVAL;  // whole compound moves only
   int rc = upload_thresholds(h, betas);
   if (rc) return rc;
-  cudaError_t e = do_sweeps(h, ea(h) ? couplings : nullptr, n_sweeps);
+  cudaError_t e = h->order != SPIN_ORDER_CHECKERBOARD ? launch_sweeps_dcb(h, n_sweeps)
+                                                      : do_sweeps(h, ea(h) ? couplings : nullptr, n_sweeps);
   if (e != cudaSuccess) return SPIN_ECUDA;
   h->sweeps_done += n_sweeps;
   return SPIN_OK;
@@ -380,6 +384,21 @@ int spin_set_batch_options(spin_lattice *h, uint64_t timeout_ns, int32_t ctas_pe
   h->batch_timeout_ns = timeout_ns;
   h->batch_ctas_per_sm = ctas_per_sm;
   h->batch_fault_extra = missing_arrivals;
+  return SPIN_OK;
+}
+
+int spin_set_update_order(spin_lattice *h, int32_t order, int32_t tile, int32_t hits) {
+  if (!h) return SPIN_EINVAL;
+  if (order == SPIN_ORDER_CHECKERBOARD) {
+    h->order = order;
+    return SPIN_OK;
+  }
+  if ((order != SPIN_ORDER_DCB && order != SPIN_ORDER_DCB_SYMMETRIC) || hits < 1 || hits > (1 << 20) ||
+      !spin::dcb_supported(h, tile))
+    return SPIN_EINVAL;
+  h->order = order;
+  h->order_tile = tile;
+  h->order_hits = hits;
   return SPIN_OK;
 }
 

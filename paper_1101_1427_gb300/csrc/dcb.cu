@@ -1,0 +1,112 @@
+// Double checkerboard with multi-hit updates for the 2D int8 ferromagnet
+// (Sec. 3.2 and 3.4).  The lattice is cut into T x T tiles coloured like a
+// checkerboard; one launch takes every tile of one coarse colour, loads it
+// with a one-site halo (from tiles of the other colour, which this launch
+// does not change) into shared memory, and gives it k hits there, each hit
+// updating the fine colour-0 sites and then the fine colour-1 sites, before
+// the tile goes back to global memory.  A compound move is one launch per
+// coarse colour; hit h of compound move m draws its uniforms with sweep
+// number m k + h, so every site takes k updates per compound move.
+#include "i8chunk.cuh"
+#include "internal.h"
+
+namespace spin {
+namespace {
+
+// Shared tile: T + 2 rows (tile rows -1 .. T), each of T / 8 + 2 eight-byte
+// words holding x = -8 .. T + 7 relative to the tile's first column, so
+// that the halo bytes x = -1 and x = T sit in whole words read straight
+// from the row above / below / beside.
+template <int kT>
+__global__ void __launch_bounds__(256) dcb_tile_kernel(int8_t *__restrict__ spins, int L, int coarse,
+                                                       uint32_t sweep0, int k,
+                                                       const uint32_t *__restrict__ thr, Geom g,
+                                                       RoundKeys rk) {
+  constexpr int kWords = kT / 8 + 2;  // words per shared row
+  constexpr int kCpr = kT / 8;        // chunks per tile row
+  constexpr int kChunks = kT * kCpr;  // chunks per tile
+  __shared__ __align__(16) uint64_t sw[(kT + 2) * kWords];
+  const uint8_t *sb = reinterpret_cast<const uint8_t *>(sw);
+  const int half = (L / kT) >> 1;
+  const int t = blockIdx.x;
+  const int by = t / half, bx = 2 * (t % half) + ((by + coarse) & 1);
+  const int64_t lat = blockIdx.y;
+  int8_t *base = spins + lat * (int64_t)L * L;
+  const int x0 = bx * kT, y0 = by * kT;
+  for (int q = threadIdx.x; q < (kT + 2) * kWords; q += blockDim.x) {
+    const int ry = q / kWords - 1, rw = q % kWords - 1;
+    const int gy = (y0 + ry + L) % L, gx = (x0 + 8 * rw + L) % L;  // L, x0 are multiples of 8
+    sw[q] = *reinterpret_cast<const uint64_t *>(base + (int64_t)gy * L + gx);
+  }
+  __syncthreads();
+  const int slot = slot_of(g, lat);
+  const uint32_t thr4 = __ldg(thr + 4 * slot + 1), thr8 = __ldg(thr + 4 * slot + 2);
+  const uint32_t lid = lattice_id_of(g, lat);
+  const uint32_t row_chunks = (uint32_t)L >> 3;
+  long long unused_a = 0, unused_d = 0;
+  for (int h = 0; h < k; ++h) {
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)c, 0);
+      for (int q = threadIdx.x; q < kChunks; q += blockDim.x) {
+        const int ty = q / kCpr, m = q % kCpr;
+        const int row = ty + 1, word = m + 1;
+        const uint64_t C = sw[row * kWords + word];
+        const uint64_t U = sw[(row - 1) * kWords + word], D = sw[(row + 1) * kWords + word];
+        const uint64_t lb = sb[(row * kWords + word) * 8 - 1], rb = sb[(row * kWords + word) * 8 + 8];
+        const int gy = y0 + ty;
+        const uint32_t gchunk = (uint32_t)gy * row_chunks + (uint32_t)(x0 >> 3) + (uint32_t)m;
+        const uint4 r = philox(make_uint4(gchunk, sweep0 + (uint32_t)h, lid, wctr), rk);
+        sw[row * kWords + word] = ising_chunk<0>(C, U, D, lb, rb, r, (c + gy) & 1, thr4, thr8, unused_a, unused_d);
+      }
+      __syncthreads();
+    }
+  }
+  for (int q = threadIdx.x; q < kChunks; q += blockDim.x) {
+    const int ty = q / kCpr, m = q % kCpr;
+    *reinterpret_cast<uint64_t *>(base + (int64_t)(y0 + ty) * L + x0 + 8 * m) = sw[(ty + 1) * kWords + m + 1];
+  }
+}
+
+template <int kT>
+cudaError_t launch_tiles(spin_lattice *h, int coarse, uint32_t sweep0) {
+  const int B = h->g.L / kT;
+  const int threads = kT * kT / 8 < 256 ? kT * kT / 8 : 256;
+  dim3 grid((unsigned)(B * B / 2), (unsigned)h->n_lat);
+  dcb_tile_kernel<kT><<<grid, threads, 0, h->stream>>>((int8_t *)h->spins, h->g.L, coarse, sweep0, h->order_hits,
+                                                       h->d_thr, h->g, make_round_keys(h->d.seed));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dcb_supported(const spin_lattice *h, int tile) {
+  if (h->d.model != SPIN_ISING || h->d.dim != 2 || h->d.layout != SPIN_I8 || h->n_lat > 65535) return false;
+  if (tile != 8 && tile != 16 && tile != 32 && tile != 64 && tile != 128) return false;
+  return h->g.L % tile == 0 && ((h->g.L / tile) & 1) == 0;
+}
+
+// n_sweeps / k compound moves (the caller has checked that k divides both
+// n_sweeps and the handle's sweep count).
+cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps) {
+  const int k = h->order_hits;
+  for (int64_t mv = 0; mv < n_sweeps / k; ++mv) {
+    const uint32_t M = (uint32_t)(h->sweeps_done / k + mv);
+    const int first = (h->order == SPIN_ORDER_DCB_SYMMETRIC && (M & 1u)) ? 1 : 0;
+    for (int cc = 0; cc < 2; ++cc) {
+      const int coarse = first ^ cc;
+      const uint32_t sweep0 = M * (uint32_t)k;
+      cudaError_t e;
+      switch (h->order_tile) {
+        case 8: e = launch_tiles<8>(h, coarse, sweep0); break;
+        case 16: e = launch_tiles<16>(h, coarse, sweep0); break;
+        case 32: e = launch_tiles<32>(h, coarse, sweep0); break;
+        case 64: e = launch_tiles<64>(h, coarse, sweep0); break;
+        default: e = launch_tiles<128>(h, coarse, sweep0); break;
+      }
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace spin

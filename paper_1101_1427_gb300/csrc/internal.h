@@ -18,6 +18,9 @@ struct spin_lattice {
   int64_t sweeps_done;
   int64_t pt_steps_done;
   int variant;           // 2D int8 sweep: 0 phases, 1 fused
+  int order;             // spin_update_order
+  int order_tile;        // double checkerboard: tile edge T
+  int order_hits;        // double checkerboard: hits k per compound move
 
   // handle-owned device workspaces
   uint32_t *d_thr;       // [n_temps][4] Metropolis thresholds, index dE/4
@@ -72,6 +75,10 @@ cudaError_t launch_rng_fill(uint64_t seed, uint32_t w, uint32_t lattice_id, uint
                             uint64_t count, uint32_t *out, cudaStream_t s);
 cudaError_t launch_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out,
                              cudaStream_t s);
+
+// dcb.cu
+bool dcb_supported(const spin_lattice *h, int tile);
+cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps);
 
 // batch.cu: load the batch kernel's device counters from the host counters
 int sync_device_counters(spin_lattice *h, cudaStream_t st);

@@ -302,19 +302,30 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
   if (acc && accepted) add_ll(&accepted[a * g.n_temps + t], 1);
 }
 
-// Exchange of whole lattices (int8, or coded 2D lattices), 16 bytes per thread.
+// Exchange of whole lattices (int8, or coded 2D lattices): 16 bytes per
+// thread step when the lattice size is a multiple of 16 bytes (the spins
+// buffer is 16-byte aligned, so every lattice then is), single bytes
+// otherwise (e.g. 6^3 = 216-byte int8 lattices).
 __global__ void pt_swap_bytes_kernel(uint8_t *__restrict__ s, const uint8_t *__restrict__ decision,
                                      Geom g, int parity, int64_t lat_bytes) {
   const int64_t lat0 = blockIdx.y;
   const int t = slot_of(g, lat0);
   if (((t - parity) & 1) || t + 1 >= g.n_temps || !decision[lat0]) return;
-  uint4 *p0 = reinterpret_cast<uint4 *>(s + lat0 * lat_bytes);
-  uint4 *p1 = reinterpret_cast<uint4 *>(s + (lat0 + g.n_real) * lat_bytes);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < lat_bytes / 16;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 a = p0[k], b = p1[k];
-    p0[k] = b;
-    p1[k] = a;
+  uint8_t *b0 = s + lat0 * lat_bytes, *b1 = s + (lat0 + g.n_real) * lat_bytes;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  if ((lat_bytes & 15) == 0) {
+    uint4 *p0 = reinterpret_cast<uint4 *>(b0), *p1 = reinterpret_cast<uint4 *>(b1);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < lat_bytes / 16; k += step) {
+      const uint4 a = p0[k], b = p1[k];
+      p0[k] = b;
+      p1[k] = a;
+    }
+  } else {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < lat_bytes; k += step) {
+      const uint8_t a = b0[k], b = b1[k];
+      b0[k] = b;
+      b1[k] = a;
+    }
   }
 }
 
@@ -421,7 +432,8 @@ cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted) {
     int64_t lat_bytes = g.N;  // int8
     if (h->d.layout == SPIN_MSC1) lat_bytes = g.N / 8;
     if (h->d.layout == SPIN_F32X4) lat_bytes = g.N * 16;
-    pt_swap_bytes_kernel<<<dim3(capped(lat_bytes / 16, 1024), (unsigned)h->n_lat), 256, 0, st>>>(
+    const int64_t units = (lat_bytes & 15) == 0 ? lat_bytes / 16 : lat_bytes;
+    pt_swap_bytes_kernel<<<dim3(capped(units, 1024), (unsigned)h->n_lat), 256, 0, st>>>(
         (uint8_t *)h->spins, decision, g, parity, lat_bytes);
   }
   return cudaGetLastError();

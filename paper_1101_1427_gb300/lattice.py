@@ -141,6 +141,36 @@ class Lattice:
     def set_update_order(self, order, tile=0, hits=1):
         B.spin_set_update_order(self.h, order, tile, hits)
 
+    # -------------------------------------------------------------- checkpoints
+    def state_dict(self):
+        """Everything a chain needs to continue: the generator is counter
+        based, so the state is the spins, the couplings, the seed and the
+        two counters (the betas and the update order are the caller's)."""
+        self.sync()
+        return {"desc": [self.model, self.dim, self.L, self.layout, self.n_real, self.n_temps,
+                         self.n_sets, self.seed],
+                "spins": self.spins.detach().cpu().clone(),
+                "couplings": None if self.couplings is None else self.couplings.detach().cpu().clone(),
+                "sweeps_done": self.sweeps_done, "pt_steps_done": self.pt_steps_done}
+
+    def save(self, path):
+        torch.save(self.state_dict(), path)
+
+    @classmethod
+    def from_state_dict(cls, state, stream=None, device=None):
+        model, dim, L, layout, n_real, n_temps, n_sets, seed = state["desc"]
+        lat = cls(model, dim, L, layout, n_real=n_real, n_temps=n_temps, n_sets=n_sets, seed=seed,
+                  stream=stream, device=device)
+        lat.spins.copy_(state["spins"])
+        if state["couplings"] is not None:
+            lat.couplings.copy_(state["couplings"])
+        lat.set_counters(state["sweeps_done"], state["pt_steps_done"])
+        return lat
+
+    @classmethod
+    def load(cls, path, stream=None, device=None):
+        return cls.from_state_dict(torch.load(path, weights_only=False), stream=stream, device=device)
+
     def close(self):
         if self.h is not None:
             B.spin_destroy(self.h)

@@ -165,9 +165,10 @@ def test_ea_sweeps_measure_bit_exact(layout, L):
                 assert M[a, t, r] == s[a, t].sum()
 
 
-@pytest.mark.parametrize("layout", [B.SPIN_I8, B.SPIN_MSC1])
-def test_ea_parallel_tempering_bit_exact(layout):
-    L, seed, n_real, n = 4, 21, 32, 40
+@pytest.mark.parametrize("layout,L", [(B.SPIN_I8, 4), (B.SPIN_MSC1, 4), (B.SPIN_I8, 6), (B.SPIN_MSC1, 6)])
+def test_ea_parallel_tempering_bit_exact(layout, L):
+    """L = 6: int8 lattices of 216 bytes, not a multiple of 16."""
+    seed, n_real, n = 21, 32, 40
     betas = list(1.0 / np.geomspace(0.9, 2.0, 5))
     lat = sp.Lattice(B.SPIN_EA, 3, L, layout, n_real=n_real, n_temps=5, n_sets=2, seed=seed)
     acc = torch.zeros(2 * 5, dtype=torch.int64, device="cuda")

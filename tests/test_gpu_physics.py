@@ -19,7 +19,7 @@ from paper_1101_1427_gb300 import _binding as B  # noqa: E402
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.mark.parametrize("L,pt_every", [(16, 1), (32, 3)])
+@pytest.mark.parametrize("L,pt_every", [(16, 1), (32, 3), (6, 1)])
 def test_ising2d_parallel_tempering_bit_exact(L, pt_every):
     """n = 20 replicas at equally spaced beta in [0.1, 0.15] (Sec. 7), int8
     layout: lattices, energies and exchange counts equal the oracle's."""

@@ -247,7 +247,8 @@ def ising_pt(torch, sp, B, stream):
 
 
 # Uneven batch: 3D EA lattices of five sizes (L, realisations, temperatures
-# geometric in [0.8, 2.2], two replica sets) and five 2D Ising ferromagnets.
+# geometric in [0.8, 2.2], two replica sets) and five 2D Ising ferromagnets
+# (1-bit coded layout).
 UNEVEN_EA = [(8, 512, 24), (12, 256, 30), (16, 128, 36), (24, 64, 42), (32, 32, 48)]
 UNEVEN_ISING = [256, 512, 1024, 2048, 4096]
 
@@ -265,7 +266,7 @@ def uneven_batch(torch, sp, B, stream, n=20):
             lat = sp.Lattice(B.SPIN_EA, 3, Le, B.SPIN_MSC1, n_real=R, n_temps=T, n_sets=2, seed=50 + k)
             side.append((lat, list(1.0 / np.geomspace(0.8, 2.2, T))))
         for k, Li in enumerate(UNEVEN_ISING):
-            side.append((sp.Lattice(B.SPIN_ISING, 2, Li, B.SPIN_I8, seed=60 + k), [0.4407]))
+            side.append((sp.Lattice(B.SPIN_ISING, 2, Li, B.SPIN_MSC1, seed=60 + k), [0.4407]))
         return side
 
     flips = n * (sum(2 * T * R * Le ** 3 for Le, R, T in UNEVEN_EA) + sum(Li * Li for Li in UNEVEN_ISING))

@@ -185,10 +185,12 @@ typedef struct {
 int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                    int32_t measure_every, int32_t pt_every, void *stream);
 
-/* Autotuner for spin_batch_run: times n_sweeps-sweep trial launches with 1..4
- * CTAs per SM on copies of the spins (handles and counters are left as they
- * were) and caches the fastest for this batch shape; best (optional, host)
- * receives it. */
+/* Autotuner for spin_batch_run: times n_sweeps-sweep trial launches (with
+ * the given measurement and exchange schedule, into scratch series) for
+ * 1..4 CTAs per SM and three weights of the Ising units in the split of
+ * CTAs between work units, on copies of the spins (handles and counters are
+ * left as they were), and caches the fastest pair for this batch shape;
+ * best (optional, host) receives the CTAs per SM. */
 int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                     int32_t measure_every, int32_t pt_every, void *stream, int32_t *best);
 

@@ -26,11 +26,12 @@
 #include "ea_cs.cuh"
 #include "i8chunk.cuh"
 #include "internal.h"
+#include "msc2d_block.cuh"
 
 namespace spin {
 
 struct BatchUnit {
-  int kind;        // 0 EA coded group, 1 Ising 2D int8 lattice
+  int kind;        // 0 EA coded group, 1 Ising 2D int8 lattice, 2 Ising 2D coded lattice
   int team_first;  // first CTA of the team
   int team_size;   // CTAs in the team
   int L;
@@ -44,7 +45,7 @@ struct BatchUnit {
   uint32_t pt0;         // ctr[1] when the launch starts
   unsigned *bar;        // the team's barrier counter (zeroed before the launch)
   // EA
-  uint32_t *w;          // words of set 0, this group, slot 0
+  uint32_t *w;          // EA: words of set 0, this group, slot 0; coded Ising: the lattice's words
   size_t set_stride;    // words between replica sets
   const uint32_t *J;    // couplings of this group [3][N]
   int grp, n_real;
@@ -588,6 +589,80 @@ __device__ bool ising_sweep(const BatchUnit &U, int part, const RoundKeys &rk, S
   return true;
 }
 
+// ---------------------------------------------------------------- coded Ising unit
+// One colour phase over the rows [r0, r1) of a 2D coded lattice, as the
+// per-phase kernel does it: each warp takes 32 consecutive blocks (128
+// same-colour sites each); lane l draws the Philox call 32 b + l of block b
+// and the warp's ballots of (r < thr4), (r < thr8) are the block's
+// acceptance masks; then lane b updates block b.
+template <int kCount>
+__device__ void msc2d_rows_phase(const BatchUnit &U, const RoundKeys &rk, uint32_t sweep, int colour, int r0,
+                                 int r1, uint4 (*mk)[32][2], long long &anti, long long &down) {
+  const int L = U.L, wpr = L / 64, bpr = L / 256;
+  const uint32_t thr4 = __ldg(U.thr + 4 * U.slot + 1), thr8 = __ldg(U.thr + 4 * U.slot + 2);
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t fb = (uint32_t)r0 * (uint32_t)bpr, nblk = (uint32_t)(r1 - r0) * (uint32_t)bpr;
+  for (uint32_t g0 = (uint32_t)warp * 32u; g0 < nblk; g0 += kWarps * 32u) {
+    const uint32_t cnt = nblk - g0 < 32u ? nblk - g0 : 32u;
+    uint32_t j4 = 32u * (fb + g0) + (uint32_t)lane;
+    for (uint32_t b = 0; b < cnt; ++b, j4 += 32u) {
+      const uint4 r = philox(make_uint4(j4, sweep, U.lid, wctr), rk);
+      const uint32_t a0 = __ballot_sync(0xffffffffu, r.x < thr4);
+      const uint32_t a1 = __ballot_sync(0xffffffffu, r.y < thr4);
+      const uint32_t a2 = __ballot_sync(0xffffffffu, r.z < thr4);
+      const uint32_t a3 = __ballot_sync(0xffffffffu, r.w < thr4);
+      const uint32_t e0 = __ballot_sync(0xffffffffu, r.x < thr8);
+      const uint32_t e1 = __ballot_sync(0xffffffffu, r.y < thr8);
+      const uint32_t e2 = __ballot_sync(0xffffffffu, r.z < thr8);
+      const uint32_t e3 = __ballot_sync(0xffffffffu, r.w < thr8);
+      if (lane == 0) {
+        mk[warp][b][0] = make_uint4(a0, a1, a2, a3);
+        mk[warp][b][1] = make_uint4(e0, e1, e2, e3);
+      }
+    }
+    __syncwarp();
+    if ((uint32_t)lane < cnt) {
+      const uint32_t gb = fb + g0 + (uint32_t)lane;
+      const uint32_t y = gb / (uint32_t)bpr, B = gb - y * (uint32_t)bpr;
+      msc2d_block<kCount>(U.w, L, wpr, bpr, colour, (int)y, B, mk[warp][lane][0], mk[warp][lane][1], anti,
+                          down);
+    }
+    __syncwarp();
+  }
+}
+
+// One sweep of the team's rows of a coded lattice, measurements fused as in
+// ising_sweep.
+__device__ bool msc2d_sweep(const BatchUnit &U, int part, const RoundKeys &rk, Sync &sy, uint32_t s_abs,
+                            bool measure, long long meas_row) {
+  const int P = U.team_size;
+  const int r0 = part * U.L / P, r1 = (part + 1) * U.L / P;
+  const bool count = measure && (U.E_series || U.M_series);
+  __shared__ uint4 mk[kWarps][32][2];  // acceptance masks, per warp and block
+  long long anti = 0, down = 0;
+  for (int colour = 0; colour < 2; ++colour) {
+    if (!count) msc2d_rows_phase<0>(U, rk, s_abs, colour, r0, r1, mk, anti, down);
+    else if (colour == 0) msc2d_rows_phase<1>(U, rk, s_abs, 0, r0, r1, mk, anti, down);
+    else msc2d_rows_phase<2>(U, rk, s_abs, 1, r0, r1, mk, anti, down);
+    if (colour == 1 && count) {
+      anti = warp_sum(anti);
+      down = warp_sum(down);
+      if ((threadIdx.x & 31) == 0) {
+        const long long N = (long long)U.N;
+        const long long idx = meas_row * U.n_lat + U.lat_index;
+        const bool first = part == 0 && threadIdx.x == 0;
+        if (U.E_series)
+          atomicAdd((unsigned long long *)&U.E_series[idx], (unsigned long long)(2 * anti - (first ? 2 * N : 0)));
+        if (U.M_series)
+          atomicAdd((unsigned long long *)&U.M_series[idx], (unsigned long long)(-2 * down + (first ? N : 0)));
+      }
+    }
+    if (!team_barrier(sy)) return false;
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchParams prm,
                                                          int *err) {
   __shared__ BatchUnit U;
@@ -629,8 +704,10 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     bool ok;
     if (U.kind == 0)
       ok = ea_sweep(U, Jsrc, part, rk, sy, s_abs, measure, pt, meas_row, pt_step);
-    else
+    else if (U.kind == 1)
       ok = ising_sweep(U, part, rk, sy, s_abs, measure, meas_row);
+    else
+      ok = msc2d_sweep(U, part, rk, sy, s_abs, measure, meas_row);
     if (!ok) return;
     if (measure) ++meas_row;
     if (pt) ++pt_step;
@@ -673,11 +750,20 @@ __global__ void batch_epilogue_kernel(const BatchCtl c) {
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-static std::map<std::vector<long long>, int> g_tuned_bps;  // autotuner cache: batch signature -> CTAs per SM
+struct Tuned {
+  int ctas_per_sm;
+  double ising_scale;
+};
+static std::map<std::vector<long long>, Tuned> g_tuned;  // autotuner cache, by batch signature
 
-static double unit_work(const BatchUnit &U) {
-  if (U.kind == 0) return 48.0 * U.n_sets * U.n_T * (double)U.N;  // ~48 ops per word-site
-  return 30.0 * (double)U.N;                                      // ~30 ops per int8 site
+// Relative cost of one sweep of a unit, per CTA-time, with measurement and
+// exchange every sweep (calibrated on GB300: a coded EA word-site costs ~4x
+// an int8 Ising site and ~8x a coded Ising site); the autotuner rescales
+// the Ising share.
+static double unit_work(const BatchUnit &U, double ising_scale) {
+  if (U.kind == 0) return 48.0 * U.n_sets * U.n_T * (double)U.N;
+  if (U.kind == 1) return 12.0 * ising_scale * (double)U.N;
+  return 6.0 * ising_scale * (double)U.N;
 }
 
 // Distributes `grid` CTAs over the units: every unit gets its minimum (EA:
@@ -685,7 +771,7 @@ static double unit_work(const BatchUnit &U) {
 // one to the unit with the largest work per CTA, up to each unit's maximum
 // (EA: one word-lattice per CTA; Ising: 8 rows per CTA).  Returns the CTAs
 // used.
-static int assign_teams(BatchUnit *units, int n, int grid) {
+static int assign_teams(BatchUnit *units, int n, int grid, double ising_scale) {
   std::vector<int> P(n), cap(n);
   int used = 0;
   for (int u = 0; u < n; ++u) {
@@ -695,9 +781,12 @@ static int assign_teams(BatchUnit *units, int n, int grid) {
       while (units[u].n_sets * ((units[u].n_T + p - 1) / p) > 64) ++p;
       P[u] = p;
       cap[u] = units[u].n_T * units[u].n_sets;  // one word-lattice per CTA at most
-    } else {
+    } else if (units[u].kind == 1) {
       P[u] = 1;
       cap[u] = std::max(1, units[u].L / 8);
+    } else {  // at least 256 blocks (one per thread) per CTA
+      P[u] = 1;
+      cap[u] = std::max(1, units[u].L * (units[u].L / 256) / 256);
     }
     used += P[u];
   }
@@ -705,8 +794,8 @@ static int assign_teams(BatchUnit *units, int n, int grid) {
     int best = -1;
     double bw = -1;
     for (int u = 0; u < n; ++u)
-      if (P[u] < cap[u] && unit_work(units[u]) / P[u] > bw) {
-        bw = unit_work(units[u]) / P[u];
+      if (P[u] < cap[u] && unit_work(units[u], ising_scale) / P[u] > bw) {
+        bw = unit_work(units[u], ising_scale) / P[u];
         best = u;
       }
     if (best < 0) break;
@@ -822,11 +911,13 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.Escr = h->d_escr + (size_t)grp * g.n_sets * g.n_temps * 32;
       }
     } else {
+      const bool coded = h->d.layout == SPIN_MSC1;
       for (int64_t lat = 0; lat < h->n_lat; ++lat) {
         if (prm.n_units >= kMaxUnits) return SPIN_EINVAL;
         BatchUnit &U = prm.units[prm.n_units++];
         U = BatchUnit{};
-        U.kind = 1;
+        U.kind = coded ? 2 : 1;
+        if (coded) U.w = (uint32_t *)h->spins + lat * (g.N / 32);
         U.L = g.L;
         U.N = (uint32_t)g.N;
         U.n_T = g.n_temps;
@@ -835,7 +926,7 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.key = k;
         U.ctr = (const long long *)h->d_ctr;
         U.bar = h->d_bar + lat;
-        U.s = (int8_t *)h->spins + lat * g.N;
+        if (!coded) U.s = (int8_t *)h->spins + lat * g.N;
         U.fC = make_fastdiv((uint32_t)(g.L / 8));
         U.E_series = (long long *)items[k].E_series;
         U.M_series = (long long *)items[k].M_series;
@@ -855,7 +946,8 @@ static bool batch_item_ok(const spin_batch_item &it, int32_t pt_every) {
   if (h->d.model == SPIN_EA)
     return h->d.layout == SPIN_MSC1 && it.couplings != nullptr && h->g.L <= 32 && h->d.n_sets <= 32;
   if (h->d.model == SPIN_ISING)
-    return h->d.layout == SPIN_I8 && h->g.dim == 2 && h->g.L % 16 == 0 && it.Q_series == nullptr &&
+    return h->g.dim == 2 && it.Q_series == nullptr &&
+           ((h->d.layout == SPIN_I8 && h->g.L % 16 == 0) || (h->d.layout == SPIN_MSC1 && h->g.L % 256 == 0)) &&
            h->order == SPIN_ORDER_CHECKERBOARD &&
            !(pt_every > 0 && h->d.n_temps > 1);
   return false;
@@ -970,9 +1062,13 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
     sig.push_back(prm.units[u].n_sets);
   }
   int bps = std::min(per_sm, h0->batch_ctas_per_sm > 0 ? h0->batch_ctas_per_sm : 2);
-  auto it = g_tuned_bps.find(sig);
-  if (h0->batch_ctas_per_sm <= 0 && it != g_tuned_bps.end()) bps = std::min(per_sm, it->second);
-  const int grid = assign_teams(prm.units, prm.n_units, sms * bps);
+  double scale = h0->batch_ising_scale > 0.0 ? h0->batch_ising_scale : 1.0;
+  auto it = g_tuned.find(sig);
+  if (it != g_tuned.end()) {
+    if (h0->batch_ctas_per_sm <= 0) bps = std::min(per_sm, it->second.ctas_per_sm);
+    if (h0->batch_ising_scale <= 0.0) scale = it->second.ising_scale;
+  }
+  const int grid = assign_teams(prm.units, prm.n_units, sms * bps, scale);
   if (grid > sms * per_sm) return SPIN_EINVAL;
   batch_prologue_kernel<<<1, 256, 0, st>>>(ctl);
   if (cudaGetLastError() != cudaSuccess) return SPIN_ECUDA;
@@ -1010,41 +1106,67 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
   for (int k = 0; k < n_items; ++k) {
     spin_lattice *h = items[k].lat;
     bytes[k] = h->d.layout == SPIN_I8 ? (size_t)(h->n_lat * h->g.N)
-                                      : (size_t)h->g.n_sets * (h->g.n_real / 32) * h->g.n_temps * h->g.N * 4;
+               : h->d.model == SPIN_ISING ? (size_t)(h->n_lat * h->g.N / 8)
+                                          : (size_t)h->g.n_sets * (h->g.n_real / 32) * h->g.n_temps * h->g.N * 4;
     if (cudaMalloc(&backup[k], bytes[k]) != cudaSuccess) return SPIN_ENOMEM;
     cudaMemcpyAsync(backup[k], h->spins, bytes[k], cudaMemcpyDeviceToDevice, st);
     sw[k] = h->sweeps_done;
     ps[k] = h->pt_steps_done;
     tmp[k].E_series = tmp[k].M_series = tmp[k].Q_series = tmp[k].accepted = nullptr;
   }
+  // scratch series, so that the trials measure as the real runs will
+  std::vector<void *> scratch;
+  const int64_t n_meas = measure_every > 0 ? n_sweeps / measure_every + 1 : 0;
+  for (int k = 0; k < n_items && n_meas > 0; ++k) {
+    spin_lattice *h = items[k].lat;
+    const size_t rows[3] = {(size_t)h->n_lat, (size_t)h->n_lat, (size_t)h->g.n_temps * h->g.n_real};
+    int64_t **dst[3] = {&tmp[k].E_series, &tmp[k].M_series, &tmp[k].Q_series};
+    const int64_t *src[3] = {items[k].E_series, items[k].M_series, items[k].Q_series};
+    for (int q = 0; q < 3; ++q) {
+      if (!src[q]) continue;
+      void *buf = nullptr;
+      if (cudaMalloc(&buf, 8 * rows[q] * (size_t)n_meas) != cudaSuccess) return SPIN_ENOMEM;
+      scratch.push_back(buf);
+      *dst[q] = (int64_t *)buf;
+    }
+  }
   spin_lattice *h0 = items[0].lat;
-  const int saved = h0->batch_ctas_per_sm;
+  const int saved_bps = h0->batch_ctas_per_sm;
+  const double saved_scale = h0->batch_ising_scale;
   float best_ms = 1e30f;
-  int best = 1;
+  Tuned best{1, 1.0};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   int rc = SPIN_OK;
-  for (int c = 1; c <= std::min(per_sm, 4); ++c) {
-    h0->batch_ctas_per_sm = c;
-    cudaEventRecord(a, st);
-    rc = spin_batch_run(tmp.data(), n_items, n_sweeps, 0, pt_every, stream_v);
-    cudaEventRecord(b, st);
-    if (rc) break;
-    cudaEventSynchronize(b);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+  const double scales[3] = {0.5, 1.0, 2.0};
+  for (int c = 1; c <= std::min(per_sm, 4) && !rc; ++c)
+    for (double sc : scales) {
+      h0->batch_ctas_per_sm = c;
+      h0->batch_ising_scale = sc;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && !rc; ++rep) {  // best of two
+        cudaEventRecord(a, st);
+        rc = spin_batch_run(tmp.data(), n_items, n_sweeps, measure_every, pt_every, stream_v);
+        cudaEventRecord(b, st);
+        if (rc) break;
+        cudaEventSynchronize(b);
+        float t = 0;
+        cudaEventElapsedTime(&t, a, b);
+        ms = std::min(ms, t);
+        for (int k = 0; k < n_items; ++k) {
+          items[k].lat->sweeps_done = sw[k];
+          items[k].lat->pt_steps_done = ps[k];
+        }
+      }
+      if (rc) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = Tuned{c, sc};
+      }
     }
-    for (int k = 0; k < n_items; ++k) {
-      items[k].lat->sweeps_done = sw[k];
-      items[k].lat->pt_steps_done = ps[k];
-    }
-  }
-  (void)measure_every;
-  h0->batch_ctas_per_sm = saved;
+  h0->batch_ctas_per_sm = saved_bps;
+  h0->batch_ising_scale = saved_scale;
   for (int k = 0; k < n_items; ++k) {
     cudaMemcpyAsync(items[k].lat->spins, backup[k], bytes[k], cudaMemcpyDeviceToDevice, st);
     items[k].lat->sweeps_done = sw[k];
@@ -1053,6 +1175,7 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
   }
   cudaStreamSynchronize(st);
   for (int k = 0; k < n_items; ++k) cudaFree(backup[k]);
+  for (void *p : scratch) cudaFree(p);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
@@ -1066,7 +1189,7 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
     sig.push_back(prm->units[u].n_sets);
   }
   delete prm;
-  g_tuned_bps[sig] = best;
-  if (best_out) *best_out = best;
+  g_tuned[sig] = best;
+  if (best_out) *best_out = best.ctas_per_sm;
   return SPIN_OK;
 }

@@ -11,6 +11,7 @@
 // bit l.  The comparisons with the two thresholds become masks through
 // warp ballots; the neighbour count and the flip decision are bit-sliced.
 #include "internal.h"
+#include "msc2d_block.cuh"
 
 namespace spin {
 namespace {
@@ -76,46 +77,9 @@ __global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__
   const uint32_t rem = gb - lat * per_lat;
   const uint32_t y = rem / (uint32_t)m.bpr;
   const uint32_t B = rem - y * (uint32_t)m.bpr;
-  const int yu = y == 0 ? m.L - 1 : (int)y - 1, yd = (int)y == m.L - 1 ? 0 : (int)y + 1;
-  const int oc = colour ^ 1;
-  uint32_t *S = w + row_word(m, lat, colour, (int)y) + 4 * B;
-  const uint32_t *O = w + row_word(m, lat, oc, (int)y);
-  const uint4 s = *reinterpret_cast<const uint4 *>(S);
-  const uint4 o = *reinterpret_cast<const uint4 *>(O + 4 * B);
-  const uint4 u = *reinterpret_cast<const uint4 *>(w + row_word(m, lat, oc, yu) + 4 * B);
-  const uint4 d = *reinterpret_cast<const uint4 *>(w + row_word(m, lat, oc, yd) + 4 * B);
-  const uint4 m4 = mk[2 * lane], m8 = mk[2 * lane + 1];
-  const int p = (colour + (int)y) & 1;
-  // second horizontal neighbour: k - 1 (p = 0) or k + 1 (p = 1)
-  uint32_t sh[4];
-  if (p == 0) {
-    const uint32_t Bp = B == 0 ? (uint32_t)m.bpr - 1 : B - 1;
-    sh[0] = (o.w << 1) | (O[4 * Bp + 3] >> 31);
-    sh[1] = o.x;
-    sh[2] = o.y;
-    sh[3] = o.z;
-  } else {
-    const uint32_t Bn = B == (uint32_t)m.bpr - 1 ? 0 : B + 1;
-    sh[0] = o.y;
-    sh[1] = o.z;
-    sh[2] = o.w;
-    sh[3] = (o.x >> 1) | (O[4 * Bn] << 31);
-  }
-  const uint32_t sv[4] = {s.x, s.y, s.z, s.w}, ov[4] = {o.x, o.y, o.z, o.w};
-  const uint32_t uv[4] = {u.x, u.y, u.z, u.w}, dv[4] = {d.x, d.y, d.z, d.w};
-  const uint32_t m4v[4] = {m4.x, m4.y, m4.z, m4.w}, m8v[4] = {m8.x, m8.y, m8.z, m8.w};
-  uint32_t nv[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t a0 = sv[q] ^ uv[q], a1 = sv[q] ^ dv[q], a2 = sv[q] ^ ov[q], a3 = sv[q] ^ sh[q];
-    const uint32_t s1 = a0 ^ a1, c1 = a0 & a1, s2 = a2 ^ a3, c2 = a2 & a3;
-    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
-    const uint32_t b1 = c1 ^ c2 ^ c3, b2 = (c1 & c2) | (c3 & (c1 ^ c2));
-    // n antiparallel neighbours, dE = 8 - 4n
-    const uint32_t ge2 = b2 | b1, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
-    nv[q] = sv[q] ^ (ge2 | (eq1 & m4v[q]) | (eq0 & m8v[q]));
-  }
-  *reinterpret_cast<uint4 *>(S) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
+  long long unused_a = 0, unused_d = 0;
+  msc2d_block<0>(w + (int64_t)lat * m.lat_words, m.L, m.wpr, m.bpr, colour, (int)y, B, mk[2 * lane],
+                 mk[2 * lane + 1], unused_a, unused_d);
 }
 
 // Hot start: bit 0 of the INIT word of each site, as in the int8 layout.

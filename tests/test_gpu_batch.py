@@ -26,10 +26,13 @@ def _make(kind, seed):
     elif kind == "ising96x2":
         lat = sp.Lattice(B.SPIN_ISING, 2, 96, B.SPIN_I8, n_temps=2, seed=seed)
         betas = [0.35, 0.5]
+    elif kind == "coded512x2":
+        lat = sp.Lattice(B.SPIN_ISING, 2, 512, B.SPIN_MSC1, n_temps=2, seed=seed)
+        betas = [0.4, 0.5]
     return lat, betas
 
 
-KINDS = ["ea8", "ea6", "ising64", "ising96x2"]
+KINDS = ["ea8", "ea6", "ising64", "ising96x2", "coded512x2"]
 
 
 @pytest.mark.parametrize("measure_every,pt_every", [(1, 1), (3, 2), (0, 1), (2, 0)])

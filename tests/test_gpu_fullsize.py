@@ -170,11 +170,13 @@ UNEVEN_EA = [(8, 512, 24), (12, 256, 30), (16, 128, 36), (24, 64, 42), (32, 32, 
 UNEVEN_ISING = [256, 512, 1024, 2048, 4096]
 
 
-def test_uneven_batch_full_size():
+@pytest.mark.parametrize("ising_layout", [B.SPIN_I8, B.SPIN_MSC1])
+def test_uneven_batch_full_size(ising_layout):
     """The full uneven batch (EA L = 8..32 with 512..32 realisations and
-    24..48 temperatures in [0.8, 2.2], two sets; 2D Ising L = 256..4096) in
-    one batched launch, measurement and exchange every sweep: equal to plain
-    per-handle runs, and sampled EA realisations equal to the oracle."""
+    24..48 temperatures in [0.8, 2.2], two sets; 2D Ising L = 256..4096, int8
+    or coded) in one batched launch, measurement and exchange every sweep:
+    equal to plain per-handle runs, and sampled EA realisations equal to the
+    oracle."""
     n = 3
 
     def build():
@@ -183,7 +185,7 @@ def test_uneven_batch_full_size():
             lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=R, n_temps=T, n_sets=2, seed=50 + k)
             side.append((lat, list(1.0 / np.geomspace(0.8, 2.2, T))))
         for k, L in enumerate(UNEVEN_ISING):
-            side.append((sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=60 + k), [0.4407]))
+            side.append((sp.Lattice(B.SPIN_ISING, 2, L, ising_layout, seed=60 + k), [0.4407]))
         return side
 
     batch, plain = build(), build()

@@ -48,15 +48,18 @@ WIDE_MULS_PER_FLIP = 5
 WIDE_MULS_PER_CLK_PER_SM = 32
 
 # DRAM bytes of one phase launch of the coded sweep over the three lattices
-# (ncu capture summarised in profiles/), valid while the kernel source hash
-# matches; otherwise reported as null.
-KERNEL_TRAFFIC_BYTES = 100_678_144 + 11_205_376
-KERNEL_TRAFFIC_SRC_SHA = "91d31522b50997f7"
+# (mean of two launches captured with ncu, summarised in profiles/), valid
+# while the kernel's sources hash to KERNEL_TRAFFIC_SRC_SHA; otherwise
+# reported as null.
+KERNEL_TRAFFIC_BYTES = (100_678_656 + 11_274_496 + 100_748_800 + 7_459_328) // 2
+KERNEL_TRAFFIC_SRC_SHA = "66288d0cf4178ccd"
 
 
 def kernel_sha():
-    p = os.path.join(ROOT, "paper_1101_1427_gb300", "csrc", "msc2d.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("msc2d.cu", "msc2d_block.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1101_1427_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- clocks

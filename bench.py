@@ -200,6 +200,25 @@ def side_configs(torch, sp, B, stream):
     torch.cuda.synchronize()
     ea.sync()
     out["ea_L16_pt_batched_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
+    # the same lattices with 64 realisations per shared uniform (Sec. 6, w = 64)
+    ea.set_msc_width(64)
+    for name, me in (("ea_L16_w64_sweep_flips_per_ns", 0), ("ea_L16_w64_pt_plain_flips_per_ns", 1)):
+        B.spin_run(ea.h, ea.couplings, betas, 2, me, me, ser["E"] if me else None, ser["M"] if me else None,
+                   ser["Q"] if me else None, None, None, acc if me else None)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_run(ea.h, ea.couplings, betas, n, me, me, ser["E"] if me else None, ser["M"] if me else None,
+                   ser["Q"] if me else None, None, None, acc if me else None)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = flips / (a.elapsed_time(b) * 1e6)
+    ea.set_msc_width(32)
+    a, b = _events(torch)
+    a.record(stream)
+    B.spin_run(ea.h, ea.couplings, betas, n, 0, 0, None, None, None, None, None, None)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["ea_L16_w32_sweep_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
     ea.close()
     out.update(uneven_batch(torch, sp, B, stream))
     out.update(ising_pt(torch, sp, B, stream))

@@ -261,6 +261,16 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * paper's "fast_math" mode, Sec. 5), within the same tolerances. */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
+/* Realisations that share one uniform per site in the coded EA layout
+ * (Sec. 6, footnote: the same random number serves all w spins of a word):
+ * 32 (one word, the default) or 64 (the paper's w = 64: realisation groups
+ * 2q and 2q + 1 draw the words of group q, i.e. lattice_id(a, r >> 6, t);
+ * the storage stays 32-bit, since on this GPU a 64-bit logical operation is
+ * two 32-bit ones, and one Philox call serves both words).  Needs n_real a
+ * multiple of 64; initial states, couplings and exchange draws do not
+ * change. */
+int spin_set_msc_width(spin_lattice *lat, int32_t width);
+
 /* Update order of the sweeps of a handle.
  *  SPIN_ORDER_CHECKERBOARD  all colour-0 sites, then all colour-1 sites
  *                           (default; every other call here assumes it).

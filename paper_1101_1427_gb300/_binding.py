@@ -68,6 +68,7 @@ def lib():
         L.spin_set_counters.argtypes = [p, i64, i64]
         L.spin_set_variant.argtypes = [p, i32]
         L.spin_set_update_order.argtypes = [p, i32, i32, i32]
+        L.spin_set_msc_width.argtypes = [p, i32]
         L.spin_strerror.argtypes = [C.c_int]
         L.spin_strerror.restype = C.c_char_p
         L.spin_destroy.argtypes = [p]
@@ -75,7 +76,7 @@ def lib():
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
-                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order"):
+                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -220,6 +221,10 @@ def spin_set_variant(h, variant):
 
 def spin_set_update_order(h, order, tile=0, hits=1):
     return _check(lib().spin_set_update_order(h, order, tile, hits), "spin_set_update_order")
+
+
+def spin_set_msc_width(h, width):
+    return _check(lib().spin_set_msc_width(h, width), "spin_set_msc_width")
 
 
 def spin_destroy(h):

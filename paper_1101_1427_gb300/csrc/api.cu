@@ -181,6 +181,7 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   spin_lattice *h = new (std::nothrow) spin_lattice();
   if (!h) return SPIN_ENOMEM;
   h->d = *desc;
+  h->msc_width = 32;
   h->stream = (cudaStream_t)desc->stream;
   h->spins = spins;
   h->couplings = couplings;
@@ -384,6 +385,13 @@ int spin_set_batch_options(spin_lattice *h, uint64_t timeout_ns, int32_t ctas_pe
   h->batch_timeout_ns = timeout_ns;
   h->batch_ctas_per_sm = ctas_per_sm;
   h->batch_fault_extra = missing_arrivals;
+  return SPIN_OK;
+}
+
+int spin_set_msc_width(spin_lattice *h, int32_t width) {
+  if (!h || h->d.model != SPIN_EA || h->d.layout != SPIN_MSC1) return SPIN_EINVAL;
+  if (width != 32 && !(width == 64 && h->g.n_real % 64 == 0)) return SPIN_EINVAL;
+  h->msc_width = width;
   return SPIN_OK;
 }
 

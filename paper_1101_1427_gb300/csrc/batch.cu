@@ -49,6 +49,7 @@ struct BatchUnit {
   size_t set_stride;    // words between replica sets
   const uint32_t *J;    // couplings of this group [3][N]
   int grp, n_real;
+  int rgrp;             // key of the group's uniforms: grp (w = 32) or grp / 2 (w = 64)
   const uint32_t *pt_tab;
   const int32_t *pt_off, *pt_len;
   const double *pt_dbeta;
@@ -397,7 +398,7 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
     for (int wi = warp / wpw; wi < n_w; wi += kWarps / wpw) {
       const int g = g0 + wi, a = g % U.n_sets, t = g / U.n_sets;
       uint32_t *s = words(a, t);
-      const uint32_t lid = lattice_id((uint32_t)a, (uint32_t)U.grp, (uint32_t)t);
+      const uint32_t lid = lattice_id((uint32_t)a, (uint32_t)U.rgrp, (uint32_t)t);
       const uint32_t t4 = __ldg(U.thr + 4 * t + 1), t8 = __ldg(U.thr + 4 * t + 2), t12 = __ldg(U.thr + 4 * t + 3);
       const uint32_t first = (uint32_t)((warp % wpw) * 32 + lane), stride = (uint32_t)(wpw * 32);
       uint32_t C[kPl];
@@ -898,6 +899,7 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.w = (uint32_t *)h->spins + (size_t)grp * g.n_temps * g.N;
         U.J = (const uint32_t *)items[k].couplings + (size_t)grp * 3 * g.N;
         U.grp = grp;
+        U.rgrp = h->msc_width == 64 ? grp / 2 : grp;
         U.n_real = g.n_real;
         U.pt_tab = h->d_pt_thr;
         U.pt_off = h->d_pt_off;

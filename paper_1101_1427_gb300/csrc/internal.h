@@ -18,6 +18,7 @@ struct spin_lattice {
   int64_t sweeps_done;
   int64_t pt_steps_done;
   int variant;           // 2D int8 sweep: 0 phases, 1 fused
+  int msc_width;         // EA coded: realisations sharing one uniform (32 or 64)
   int order;             // spin_update_order
   int order_tile;        // double checkerboard: tile edge T
   int order_hits;        // double checkerboard: hits k per compound move

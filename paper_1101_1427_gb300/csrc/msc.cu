@@ -81,6 +81,30 @@ __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w
   }
 }
 
+// w = 64 (Sec. 6: 64 spins per variable): realisation groups 2q and 2q + 1
+// of one (set, slot) share their uniforms, keyed by q, so one Philox call
+// serves the same quad of both word-lattices.
+__global__ void __launch_bounds__(256) msc_phase_pair_kernel(uint32_t *__restrict__ w,
+                                                             const uint32_t *__restrict__ J, Geom g,
+                                                             uint32_t total,
+                                                             const uint32_t *__restrict__ thr,
+                                                             RoundKeys rk, uint32_t sweep, int colour) {
+  const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = (N / 2 + 3) / 4;
+  const uint32_t G = (uint32_t)g.n_real / 32, G2 = G / 2, T = (uint32_t)g.n_temps;
+  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const uint32_t pl = fdiv(k, g.fquads), j4 = k - pl * quads;
+    const uint32_t t = pl % T, q = (pl / T) % G2, a = pl / (T * G2);
+    const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, q, t), wctr), rk);
+    const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
+    const size_t wl0 = ((size_t)a * G + 2 * q) * T + t;  // group 2q; group 2q + 1 is T word-lattices on
+    ea_cs_quad<false>(w + wl0 * N, J + (size_t)(2 * q) * 3 * N, j4, colour, L, N, g.fL, r, t4, t8, t12,
+                      NoAdd());
+    ea_cs_quad<false>(w + (wl0 + T) * N, J + (size_t)(2 * q + 1) * 3 * N, j4, colour, L, N, g.fL, r, t4, t8,
+                      t12, NoAdd());
+  }
+}
+
 // words -> one int8 per spin, [n_sets][n_temps][n_real][N]
 __global__ void unpack_msc_kernel(const uint32_t *__restrict__ w, int8_t *__restrict__ out, Geom g) {
   const int G = g.n_real / 32;
@@ -144,12 +168,17 @@ cudaError_t launch_sweeps_msc_ea(spin_lattice *h, const uint32_t *J, int64_t n_s
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
   const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-  const uint32_t work = (uint32_t)(n_wl * ((g.N / 2 + 3) / 4));
+  const bool pair = h->msc_width == 64;
+  const uint32_t work = (uint32_t)((pair ? n_wl / 2 : n_wl) * ((g.N / 2 + 3) / 4));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour)
-      msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
-                                                            h->d_thr, rk, sweep, colour);
+      if (pair)
+        msc_phase_pair_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
+                                                                   h->d_thr, rk, sweep, colour);
+      else
+        msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
+                                                              h->d_thr, rk, sweep, colour);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

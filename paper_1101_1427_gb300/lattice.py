@@ -138,6 +138,9 @@ class Lattice:
     def set_variant(self, variant):
         B.spin_set_variant(self.h, variant)
 
+    def set_msc_width(self, width):
+        B.spin_set_msc_width(self.h, width)
+
     def set_update_order(self, order, tile=0, hits=1):
         B.spin_set_update_order(self.h, order, tile, hits)
 

@@ -160,3 +160,21 @@ def test_batch_graph_replays_continue_the_chain():
         lg.run(betas, 3, 0, pt, series=False)
         lp.run(betas, 3, 0, pt, series=False)
         assert torch.equal(lg.spins, lp.spins)
+
+
+def test_batch_w64_equals_plain_w64():
+    """The batched launch keys the uniforms of a w = 64 handle by group pair,
+    as the per-handle pair kernel does."""
+    betas = list(1.0 / np.geomspace(0.8, 2.2, 5))
+    make = lambda: sp.Lattice(B.SPIN_EA, 3, 8, B.SPIN_MSC1, n_real=128, n_temps=5, n_sets=2, seed=71)
+    a, b = make(), make()
+    a.set_msc_width(64)
+    b.set_msc_width(64)
+    ser = a.series_buffers(6)
+    sp.batch_run([a.batch_item(betas, ser)], 6, 1, 1)
+    out = b.run(betas, 6, 1, 1)
+    a.sync()
+    assert torch.equal(a.spins, b.spins)
+    for key in ("E", "M", "Q"):
+        assert torch.equal(ser[key], out[key]), key
+

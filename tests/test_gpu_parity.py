@@ -111,8 +111,11 @@ def test_fused_equals_phases_on_large_lattice():
 
 
 # ------------------------------------------------------------------ EA
-def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None):
+def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None, width=32):
+    """Oracle runs of single realisations; `width` realisations share each
+    update uniform (key r >> 5 for 32, r >> 6 for 64)."""
     n_temps = len(betas)
+    shift = 5 if width == 32 else 6
     reals = range(n_real) if reals is None else reals
     res = {}
     for r in reals:
@@ -120,9 +123,33 @@ def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None)
         sp_ = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t),
                                                     bit=r & 31) for t in range(n_temps)])
                         for a in range(n_sets)]).copy()
-        E, Q, acc, _ = oracle.pt_run(3, L, sp_, betas, seed, r, r >> 5, 0, n_sweeps, pt_every, J=J)
+        E, Q, acc, _ = oracle.pt_run(3, L, sp_, betas, seed, r, r >> shift, 0, n_sweeps, pt_every, J=J)
         res[r] = (J, sp_, E, Q, acc)
     return res
+
+
+@pytest.mark.parametrize("L", [8, 6])
+def test_ea_w64_shared_uniforms_bit_exact(L):
+    """w = 64 (Sec. 6): realisations r and r' with r >> 6 == r' >> 6 share
+    every update uniform; plain per-handle path with exchange and
+    measurement every sweep, sampled realisations of both words of a pair."""
+    seed, n_real, n = 23, 128, 10
+    betas = list(1.0 / np.geomspace(0.9, 2.0, 4))
+    lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=4, n_sets=2, seed=seed)
+    lat.set_msc_width(64)
+    out = lat.run(betas, n, measure_every=1, pt_every=1)
+    got = host(lat.unpack())
+    E = host(out["E"]).reshape(n, 2, 4, n_real)
+    Q = host(out["Q"]).reshape(n, 4, n_real)
+    ref = _ea_oracle(L, seed, betas, n_real, 2, n, pt_every=1, reals=(0, 31, 32, 63, 64, 127), width=64)
+    for r, (J, s, Es, Qs, ac) in ref.items():
+        assert np.array_equal(got[:, :, r], s), r
+        assert np.array_equal(E[:, :, :, r], Es), r
+        assert np.array_equal(Q[:, :, r], Qs), r
+    # and w = 32 gives a different chain from the same start
+    lat32 = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=4, n_sets=2, seed=seed)
+    lat32.run(betas, n, measure_every=0, pt_every=1, series=False)
+    assert not torch.equal(lat32.spins, lat.spins)
 
 
 @pytest.mark.parametrize("layout", [B.SPIN_I8, B.SPIN_MSC1])

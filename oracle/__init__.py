@@ -61,6 +61,7 @@ def lib():
         L.or_ising_window_sweeps.argtypes = [i32, i32, p, i32, p, dbl, u64, u32, u32, i32]
         L.or_ising_init_sites.argtypes = [i64, p, p, u64, u32, i32]
         L.or_dcb_sweeps.argtypes = [i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
+        L.or_ising_slab_phase.argtypes = [i32, i32, i32, p, dbl, u64, u32, u32, i32, p]
         _lib = L
     return _lib
 
@@ -174,6 +175,14 @@ def dcb_sweeps(L, s, beta, seed, lid, first_sweep, n_sweeps, T, k, symmetric=Fal
     flips = np.zeros(1, np.int64)
     lib().or_dcb_sweeps(L, _ptr(s), _ptr(J), beta, seed, lid, first_sweep, n_sweeps, T, k,
                         int(bool(symmetric)), _ptr(flips))
+    return int(flips[0])
+
+
+def slab_phase(L, y0, rows, slab, beta, seed, lid, sweep, colour):
+    """One colour phase of the own rows of a slab ([rows + 2][L] int8, ghost
+    rows 0 and rows + 1) in place; returns the flip count."""
+    flips = np.zeros(1, np.int64)
+    lib().or_ising_slab_phase(L, y0, rows, _ptr(slab), beta, seed, lid, sweep, colour, _ptr(flips))
     return int(flips[0])
 
 

@@ -244,6 +244,42 @@ void or_ising_sweep(int dim, int L, int8_t *s, const int8_t *J, double beta,
   }
 }
 
+/* One colour phase of rows y0 .. y0 + rows - 1 (0 <= y0, y0 + rows <= L) of
+ * a 2D L x L periodic ferromagnet held as a slab of rows + 2 rows of L
+ * sites: slab row 0 holds a copy of row y0 - 1 and slab row rows + 1 a copy
+ * of row y0 + rows (both mod L), rows 1 .. rows are the slab's own rows.
+ * Every own site of the colour is updated as in or_ising_sweep: the colour
+ * and the random word are those of its global index y L + x, so slabs that
+ * exchange their boundary rows before every phase reproduce the unsplit
+ * sweep.  The copies are only read. */
+void or_ising_slab_phase(int L, int y0, int rows, int8_t *slab, double beta, uint64_t seed,
+                         uint32_t lattice_id, uint32_t sweep, int colour, int64_t *flips) {
+  uint32_t thr[3] = {0, 0, 0};
+  for (int m = 1; m <= 2; ++m) thr[m] = or_metropolis_threshold(beta, 4 * m);
+  for (int r = 1; r <= rows; ++r) {
+    const int64_t y = y0 + r - 1;
+    int8_t *row = slab + (int64_t)r * L;
+    const int8_t *up = row - L, *dn = row + L;
+    for (int x = 0; x < L; ++x) {
+      if ((int)((x + y) & 1) != colour) continue;
+      const int h = row[x == L - 1 ? 0 : x + 1] + row[x == 0 ? L - 1 : x - 1] + up[x] + dn[x];
+      const int dE = 2 * row[x] * h;
+      int flip;
+      if (dE <= 0) {
+        flip = 1;
+      } else {
+        const uint32_t rw = or_draw(seed, OR_TAG_UPDATE, (uint32_t)colour, 0, lattice_id, sweep,
+                                    (uint32_t)((y * L + x) >> 1));
+        flip = rw < thr[dE / 4];
+      }
+      if (flip) {
+        row[x] = (int8_t)(-row[x]);
+        if (flips) ++*flips;
+      }
+    }
+  }
+}
+
 /* Double checkerboard order with multi-hit updates (Sec. 3.2 and 3.4), 2D.
  * The L x L lattice is cut into T x T tiles; tile (x / T, y / T) has the
  * coarse colour (x / T + y / T) mod 2.  A compound move takes the tiles of

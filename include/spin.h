@@ -261,6 +261,31 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * paper's "fast_math" mode, Sec. 5), within the same tolerances. */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
+/* Slab decomposition of one 2D int8 ferromagnet over several GPUs (the
+ * domain decomposition of Sec. 3.2 carried one level up, to devices): a rank
+ * owns rows y0 .. y0 + rows - 1 of the L x L periodic lattice (0 <= y0,
+ * y0 + rows <= L) and holds them as a device buffer slab[rows + 2][L] of +-1
+ * bytes (8-byte aligned), slab rows 0 and rows + 1 being copies of global
+ * rows y0 - 1 and y0 + rows (mod L).  The caller refreshes those two ghost
+ * rows from the neighbouring ranks before every colour phase (one row per
+ * neighbour; see paper_1101_1427_gb300/slab.py).
+ *
+ * spin_slab_phase: one colour phase (colour 0 or 1) of the own rows, as in
+ * spin_sweep: the colour of a site is that of its global index and its
+ * uniform is the UPDATE word of (seed, lattice_id, sweep, global colour
+ * index), so the slabs of a lattice together reproduce the unsplit sweep bit
+ * for bit.  L % 8 == 0; beta >= 0; work is enqueued on `stream`; ghost rows
+ * are read only.
+ * spin_slab_measure: device int64 partial sums of the own rows, E over the
+ * bond to the right and the bond below of every own site (the last own row
+ * reads the lower ghost), M over own sites; the partials of all slabs add up
+ * to the lattice's E and M.  Errors: SPIN_EINVAL for bad sizes or pointers,
+ * SPIN_EALIGN for a misaligned slab, SPIN_ECUDA for a launch failure.
+ * The paper has no multi-GPU code; this is the design its tiling implies. */
+int spin_slab_phase(int8_t *slab, int32_t L, int32_t y0, int32_t rows, double beta, uint64_t seed,
+                    uint32_t lattice_id, uint32_t sweep, int32_t colour, void *stream);
+int spin_slab_measure(const int8_t *slab, int32_t L, int32_t rows, int64_t *E, int64_t *M, void *stream);
+
 /* Realisations that share one uniform per site in the coded EA layout
  * (Sec. 6, footnote: the same random number serves all w spins of a word):
  * 32 (one word, the default) or 64 (the paper's w = 64: realisation groups

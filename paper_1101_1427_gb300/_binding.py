@@ -69,6 +69,8 @@ def lib():
         L.spin_set_variant.argtypes = [p, i32]
         L.spin_set_update_order.argtypes = [p, i32, i32, i32]
         L.spin_set_msc_width.argtypes = [p, i32]
+        L.spin_slab_phase.argtypes = [p, i32, i32, i32, C.c_double, u64, u32, u32, i32, p]
+        L.spin_slab_measure.argtypes = [p, i32, i32, p, p, p]
         L.spin_strerror.argtypes = [C.c_int]
         L.spin_strerror.restype = C.c_char_p
         L.spin_destroy.argtypes = [p]
@@ -76,7 +78,8 @@ def lib():
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
-                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width"):
+                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width", "spin_slab_phase",
+                     "spin_slab_measure"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -225,6 +228,16 @@ def spin_set_update_order(h, order, tile=0, hits=1):
 
 def spin_set_msc_width(h, width):
     return _check(lib().spin_set_msc_width(h, width), "spin_set_msc_width")
+
+
+def spin_slab_phase(slab, L, y0, rows, beta, seed, lattice_id, sweep, colour, stream=None):
+    return _check(lib().spin_slab_phase(_ptr(slab), L, y0, rows, float(beta), seed, lattice_id, sweep,
+                                        colour, stream), "spin_slab_phase")
+
+
+def spin_slab_measure(slab, L, rows, E, M, stream=None):
+    return _check(lib().spin_slab_measure(_ptr(slab), L, rows, _ptr(E), _ptr(M), stream),
+                  "spin_slab_measure")
 
 
 def spin_destroy(h):

@@ -70,3 +70,56 @@ def test_two_gloo_ranks_equal_unsharded(tmp_path):
         E, Q, acc, _ = oracle.pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J)
         ref = np.concatenate([E.ravel(), Q.ravel(), s.ravel().astype(np.int64)])
         assert np.array_equal(got[k], ref), r
+
+
+def _slab_rank_main(rank, world, port, L, n, out_path):
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_1101_1427_gb300.slab import exchange_ghosts, split_rows
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    beta, seed = 0.44, 17
+    lid = oracle.lattice_id(0, 0, 0)
+    y0, rows = split_rows(L, world, rank)
+    full0 = oracle.ising_init(2, L, seed, lid).reshape(L, L)
+    slab = torch.zeros(rows + 2, L, dtype=torch.int8)
+    slab[1:rows + 1] = torch.from_numpy(full0[y0:y0 + rows].copy())
+    view = slab.numpy()  # shares memory with the tensor the exchange fills
+    for sweep in range(n):
+        for colour in (0, 1):
+            exchange_ghosts(slab, rank, world)
+            oracle.slab_phase(L, y0, rows, view, beta, seed, lid, sweep, colour)
+    exchange_ghosts(slab, rank, world)
+    # partial energy (bonds right and below of own sites) and magnetisation, then one all-reduce
+    own, below = view[1:rows + 1].astype(np.int64), view[2:rows + 2].astype(np.int64)
+    part = torch.tensor([-(own * np.roll(own, -1, axis=1)).sum() - (own * below).sum(), own.sum()],
+                        dtype=torch.int64)
+    dist.all_reduce(part)
+    rows_all = [None] * world
+    dist.all_gather_object(rows_all, view[1:rows + 1].copy())
+    if rank == 0:
+        np.savez(out_path, lattice=np.concatenate(rows_all), EM=part.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,L", [(2, 32), (3, 40)])
+def test_slab_decomposition_over_gloo_ranks_equals_unsplit(world, L, tmp_path):
+    """Ranks own bands of rows of one lattice and exchange one ghost row per
+    neighbour before each colour phase (send/recv over gloo); the gathered
+    lattice and the all-reduced E, M equal the unsplit oracle."""
+    import torch.multiprocessing as mp
+    import oracle
+    n = 5
+    out = tmp_path / "slab.npz"
+    mp.start_processes(_slab_rank_main, args=(world, _free_port(), L, n, str(out)), nprocs=world,
+                       join=True, start_method="spawn")
+    res = np.load(out)
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(2, L, 17, lid)
+    for sweep in range(n):
+        oracle.ising_sweep(2, L, s, 0.44, 17, lid, sweep)
+    assert np.array_equal(res["lattice"].ravel(), s)
+    assert res["EM"][0] == oracle.ising_energy(2, L, s)
+    assert res["EM"][1] == oracle.ising_magnetisation(2, L, s)

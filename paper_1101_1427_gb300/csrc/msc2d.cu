@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
   uint32_t j4 = 32u * (first - lat * per_lat) + (uint32_t)lane;
   uint4 *mk = &masks[wib][0][0];
-#pragma unroll 2
+#pragma unroll  // 32 independent generator calls: full unrolling lets them interleave
   for (uint32_t b = 0; b < 32u; ++b, j4 += 32u) {
     const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
     const uint32_t a0 = __ballot_sync(0xffffffffu, r.x < thr4);

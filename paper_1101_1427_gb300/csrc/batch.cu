@@ -607,6 +607,7 @@ __device__ void msc2d_rows_phase(const BatchUnit &U, const RoundKeys &rk, uint32
   for (uint32_t g0 = (uint32_t)warp * 32u; g0 < nblk; g0 += kWarps * 32u) {
     const uint32_t cnt = nblk - g0 < 32u ? nblk - g0 : 32u;
     uint32_t j4 = 32u * (fb + g0) + (uint32_t)lane;
+#pragma unroll 4
     for (uint32_t b = 0; b < cnt; ++b, j4 += 32u) {
       const uint4 r = philox(make_uint4(j4, sweep, U.lid, wctr), rk);
       const uint32_t a0 = __ballot_sync(0xffffffffu, r.x < thr4);

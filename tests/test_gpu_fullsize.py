@@ -215,3 +215,67 @@ def test_uneven_batch_full_size(ising_layout):
         assert np.array_equal(got, s), L
         E = sers[UNEVEN_EA.index((L, R, T))]["E"].view(n, 2, T, R)[:, :, :, r].cpu().numpy()
         assert np.array_equal(E, Es), L
+
+
+def _tab_rng_e():
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    for line in open(os.path.join(here, "golden", "tab_rng_exact.txt")):
+        if line.strip() and not line.startswith("#"):
+            return float(line.split()[2])
+
+
+@pytest.mark.parametrize("order", [B.SPIN_ORDER_DCB, B.SPIN_ORDER_DCB_SYMMETRIC])
+def test_dcb_L16384_energy_matches_exact(order):
+    """The double-checkerboard chain on the full L = 16384 lattice (tile 64,
+    10 hits) at beta = 0.4 samples the exact energy per spin (Tab. rng; at
+    this beta the L = 1024 torus value equals the infinite lattice's to far
+    below the statistical error of 2^28 spins)."""
+    L, T, k = 16384, 64, 10
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=91)
+    lat.set_update_order(order, T, k)
+    lat.sweep([0.4], 300)
+    out = lat.run([0.4], 600, measure_every=k)
+    e = -out["E"].cpu().numpy().astype(np.float64) / L ** 2
+    m, s = binned_mean(e, 20)
+    assert abs(m - _tab_rng_e()) <= 4 * s + 1e-6, (m, s)
+
+
+def test_ea_w64_full_size_batched_equals_plain():
+    """3D EA L = 16, 1024 realisations x 32 slots x 2 sets, w = 64: the
+    batched launch equals the per-handle pair kernel, series included."""
+    L, n = 16, 4
+    betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
+    a = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=5)
+    b = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=5)
+    a.set_msc_width(64)
+    b.set_msc_width(64)
+    ser = a.series_buffers(n)
+    sp.batch_run([a.batch_item(betas, ser)], n, 1, 1)
+    out = b.run(betas, n, 1, 1)
+    a.sync()
+    assert torch.equal(a.spins, b.spins)
+    for key in ("E", "M", "Q"):
+        assert torch.equal(ser[key], out[key]), key
+
+
+def test_slabs_L16384_equal_unsplit():
+    """Four slabs of the L = 16384 lattice with ghost rows exchanged on the
+    device equal the unsplit sweep."""
+    from paper_1101_1427_gb300 import slab as S
+    L, P, n, beta, seed = 16384, 4, 2, 0.4407, 93
+    full = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=seed)
+    parts = [S.split_rows(L, P, k) for k in range(P)]
+    slabs = []
+    for y0, rows in parts:
+        sl = torch.empty(rows + 2, L, dtype=torch.int8, device="cuda")
+        sl[1:rows + 1] = full.spins.view(L, L)[y0:y0 + rows]
+        slabs.append(sl)
+    full.sweep([beta], n)
+    for sweep in range(n):
+        for colour in (0, 1):
+            S.exchange_ghosts_local(slabs)
+            for (y0, rows), sl in zip(parts, slabs):
+                S.phase(sl, L, y0, rows, beta, seed, 0, sweep, colour)
+    for (y0, rows), sl in zip(parts, slabs):
+        assert torch.equal(sl[1:rows + 1], full.spins.view(L, L)[y0:y0 + rows]), y0

@@ -20,49 +20,20 @@
 //     recomputation equals what the neighbouring strip computes.
 //
 // The result is identical to the two in-place colour phases.
+#include "i8chunk.cuh"
 #include "internal.h"
 
 namespace spin {
 namespace {
 
-constexpr uint64_t kBit1 = 0x0202020202020202ull;
-
-// New value of one 8-byte chunk: the active colour sits on the bytes of
-// parity p.  Neighbours: U, D above/below; lb/rb the bytes left of byte 0
-// and right of byte 7.  Antiparallel neighbours are counted byte-wise
-// (2 per antiparallel neighbour, at most 8 per byte), dE = 8 - 4n.  The
-// active bytes are then moved to the even positions so that every later
-// step uses fixed bit positions: n >= 2 (dE <= 0) flips outright; otherwise
-// the site flips iff r < thr(dE), thr4 for n = 1 (byte bit 1 set), thr8 for
-// n = 0.  A flip is the byte XOR 0xFE (+1 <-> -1).
-template <int P>
-__device__ __forceinline__ uint64_t update_chunk_p(uint64_t C, uint64_t U, uint64_t D, uint32_t lb,
-                                                   uint32_t rb, uint4 r, uint32_t thr4,
-                                                   uint32_t thr8) {
-  const uint64_t Lw = (C << 8) | (uint64_t)lb;
-  const uint64_t Rw = (C >> 8) | ((uint64_t)rb << 56);
-  const uint64_t A = ((C ^ U) & kBit1) + ((C ^ D) & kBit1) + ((C ^ Lw) & kBit1) + ((C ^ Rw) & kBit1);
-  const uint64_t An = A >> (8 * P);
-  const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
-  // 1 in bit 0 / bit 16 of each half where n >= 2
-  const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
-  const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
-  const uint32_t t0 = (lo & 0x2u) ? thr4 : thr8, t1 = (lo & 0x20000u) ? thr4 : thr8;
-  const uint32_t t2 = (hi & 0x2u) ? thr4 : thr8, t3 = (hi & 0x20000u) ? thr4 : thr8;
-  const uint32_t f_lo = g_lo | (uint32_t)(r.x < t0) | ((uint32_t)(r.y < t1) << 16);
-  const uint32_t f_hi = g_hi | (uint32_t)(r.z < t2) | ((uint32_t)(r.w < t3) << 16);
-  const uint64_t F = ((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu);
-  return C ^ (F << (8 * P));
-}
-
-// p is the same for every thread of the CTA (it depends on the row and the
-// colour only), so the branch does not diverge and both paths use constant
-// shifts.
+// New value of one 8-byte chunk whose active colour sits on the bytes of
+// parity p (the same for every thread of the CTA: it depends on the row and
+// the colour only); lb/rb are the bytes left of byte 0 and right of byte 7.
 __device__ __forceinline__ uint64_t update_chunk(uint64_t C, uint64_t U, uint64_t D, uint32_t lb,
                                                  uint32_t rb, int p, uint4 r, uint32_t thr4,
                                                  uint32_t thr8) {
-  return p ? update_chunk_p<1>(C, U, D, lb, rb, r, thr4, thr8)
-           : update_chunk_p<0>(C, U, D, lb, rb, r, thr4, thr8);
+  long long unused_a = 0, unused_d = 0;
+  return ising_chunk<0>(C, U, D, lb, rb, r, p, thr4, thr8, unused_a, unused_d);
 }
 
 struct Row16 {

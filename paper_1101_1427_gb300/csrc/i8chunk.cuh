@@ -15,31 +15,36 @@ template <int kCount>
 __device__ __forceinline__ uint64_t ising_chunk(uint64_t C, uint64_t Uw, uint64_t Dw, uint64_t lb, uint64_t rb,
                                                 const uint4 &r, int p, uint32_t thr4, uint32_t thr8,
                                                 long long &anti, long long &down) {
-  const uint64_t MASK = 0x0202020202020202ull;  // bit 1 of each byte: 1 for -1, 0 for +1
-  const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);
-  // per byte: twice the number of antiparallel neighbours
-  const uint64_t A = ((C ^ Uw) & MASK) + ((C ^ Dw) & MASK) + ((C ^ Lw) & MASK) + ((C ^ Rw) & MASK);
-  const uint64_t An = A >> (8 * p);
-  const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
-  // dE <= 0 (at least two antiparallel neighbours): flip
-  const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
-  const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
-  // one antiparallel neighbour: dE = 4; none: dE = 8
-  const uint32_t q0 = (lo & 0x2u) ? thr4 : thr8, q1 = (lo & 0x20000u) ? thr4 : thr8;
-  const uint32_t q2 = (hi & 0x2u) ? thr4 : thr8, q3 = (hi & 0x20000u) ? thr4 : thr8;
-  const uint32_t f_lo = g_lo | (uint32_t)(r.x < q0) | ((uint32_t)(r.y < q1) << 16);
-  const uint32_t f_hi = g_hi | (uint32_t)(r.z < q2) | ((uint32_t)(r.w < q3) << 16);
+  // the four sites (bytes p, p+2, p+4, p+6) and each of their neighbours,
+  // gathered into one 32-bit word apiece
+  const uint32_t sel = p ? 0x7531u : 0x6420u;
+  const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);  // left / right neighbour of every byte
+  const uint32_t S = __byte_perm((uint32_t)C, (uint32_t)(C >> 32), sel);
+  const uint32_t Un = __byte_perm((uint32_t)Uw, (uint32_t)(Uw >> 32), sel);
+  const uint32_t Dn = __byte_perm((uint32_t)Dw, (uint32_t)(Dw >> 32), sel);
+  const uint32_t Ln = __byte_perm((uint32_t)Lw, (uint32_t)(Lw >> 32), sel);
+  const uint32_t Rn = __byte_perm((uint32_t)Rw, (uint32_t)(Rw >> 32), sel);
+  // per site: 2n, n the number of antiparallel neighbours (bit 1 of a +-1
+  // byte is set for -1, so (a ^ b) & 2 is 2 iff a != b); dE = 8 - 4n
+  const uint32_t M = 0x02020202u;
+  const uint32_t A = ((S ^ Un) & M) + ((S ^ Dn) & M) + ((S ^ Ln) & M) + ((S ^ Rn) & M);
+  // n >= 2 (dE <= 0) flips; n = 1 flips iff r < thr4, n = 0 iff r < thr8
+  uint32_t f = ((A | (A >> 1)) >> 2) & 0x01010101u;
+  const uint32_t t0 = (A & 0x2u) ? thr4 : thr8, t1 = (A & 0x200u) ? thr4 : thr8;
+  const uint32_t t2 = (A & 0x20000u) ? thr4 : thr8, t3 = (A & 0x2000000u) ? thr4 : thr8;
+  f |= (r.x < t0 ? 0x1u : 0u) | (r.y < t1 ? 0x100u : 0u) | (r.z < t2 ? 0x10000u : 0u) |
+       (r.w < t3 ? 0x1000000u : 0u);
+  if (kCount >= 1) down += __popc(((S >> 1) & 0x01010101u) ^ f);
   if (kCount == 2) {
-    const uint32_t n0 = (lo >> 1) & 7u, n1 = (lo >> 17) & 7u, n2 = (hi >> 1) & 7u, n3 = (hi >> 17) & 7u;
-    anti += (long long)((f_lo & 1u) ? 4u - n0 : n0) + ((f_lo >> 16) ? 4u - n1 : n1) +
-            ((f_hi & 1u) ? 4u - n2 : n2) + ((f_hi >> 16) ? 4u - n3 : n3);
+    const uint32_t n4 = (A >> 1) & 0x07070707u, m = f * 0xFFu;
+    const uint32_t after = (n4 & ~m) | ((0x04040404u - n4) & m);  // a flip turns n into 4 - n
+    anti += (long long)((after * 0x01010101u) >> 24);
   }
-  if (kCount >= 1) {
-    const uint64_t old_down = (C >> (8 * p)) & 0x0002000200020002ull;
-    const uint64_t flips = ((uint64_t)f_hi << 33) | ((uint64_t)f_lo << 1);
-    down += __popcll(old_down ^ flips);
-  }
-  return C ^ ((((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu)) << (8 * p));
+  // 0xFE (+1 <-> -1) in the bytes of the flipping sites, scattered back
+  const uint32_t F = f * 0xFEu;
+  const uint32_t flo = __byte_perm(F, 0u, p ? 0x1404u : 0x4140u);
+  const uint32_t fhi = __byte_perm(F, 0u, p ? 0x3424u : 0x4342u);
+  return C ^ (((uint64_t)fhi << 32) | flo);
 }
 
 }  // namespace spin

@@ -1,6 +1,7 @@
 // Ising ferromagnet and +-J EA glass with one int8 (+-1) per spin:
 // initialisation, couplings and the checkerboard Metropolis sweep
 // (Sec. 3.2, Eq. metropolis, Eq. spinglass_hamiltonian).
+#include "i8chunk.cuh"
 #include "internal.h"
 
 namespace spin {
@@ -50,11 +51,8 @@ __global__ void couplings_i8_kernel(int8_t *__restrict__ J, Geom g, RoundKeys rk
 // ---------------------------------------------------------------- 2D phase, L % 8 == 0
 // One thread owns eight consecutive bytes of a row (x = 8m .. 8m+7): the
 // four sites of the active colour among them draw their uniforms from one
-// Philox call (their colour indices j = yL/2 + 4m + q share j >> 2).  The
-// number of antiparallel neighbours of all eight bytes is formed at once
-// with byte-wise arithmetic on 64-bit words: for +-1 bytes, (a ^ b) & 2 is 2
-// iff a != b, so the sum of four such terms is 2n per byte (n <= 4, no
-// carries between bytes).  dE = 2 s h = 8 - 4n.
+// Philox call (their colour indices j = yL/2 + 4m + q share j >> 2); the
+// update itself is ising_chunk (byte-wise neighbour counts, dE = 8 - 4n).
 __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__ spins, int L,
                                                             const uint32_t *__restrict__ thr,
                                                             Geom g, RoundKeys rk, uint32_t sweep,
@@ -73,25 +71,13 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
   const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
   const uint64_t lb = (uint8_t)base[(int64_t)y * L + xl];
   const uint64_t rb = (uint8_t)base[(int64_t)y * L + xr];
-  const uint64_t MASK = 0x0202020202020202ull;
-  const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);
-  const uint64_t A = ((C ^ U) & MASK) + ((C ^ D) & MASK) + ((C ^ Lw) & MASK) + ((C ^ Rw) & MASK);
   const int t = slot_of(g, lat);
   const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
   const uint32_t j4 = (uint32_t)y * (uint32_t)chunks + (uint32_t)m;
   const uint4 r = philox(make_uint4(j4, sweep, lattice_id_of(g, lat), ctr_w(TAG_UPDATE, colour, 0)), rk);
-  const int p = (colour + y) & 1;
-  // active bytes to the even positions; n >= 2 flips outright, else r < thr(dE)
-  const uint64_t An = A >> (8 * p);
-  const uint32_t lo = (uint32_t)An, hi = (uint32_t)(An >> 32);
-  const uint32_t g_lo = ((lo | (lo >> 1)) >> 2) & 0x00010001u;
-  const uint32_t g_hi = ((hi | (hi >> 1)) >> 2) & 0x00010001u;
-  const uint32_t t0 = (lo & 0x2u) ? thr4 : thr8, t1 = (lo & 0x20000u) ? thr4 : thr8;
-  const uint32_t t2 = (hi & 0x2u) ? thr4 : thr8, t3 = (hi & 0x20000u) ? thr4 : thr8;
-  const uint32_t f_lo = g_lo | (uint32_t)(r.x < t0) | ((uint32_t)(r.y < t1) << 16);
-  const uint32_t f_hi = g_hi | (uint32_t)(r.z < t2) | ((uint32_t)(r.w < t3) << 16);
-  const uint64_t F = (((uint64_t)(f_hi * 0xFEu) << 32) | (uint64_t)(f_lo * 0xFEu)) << (8 * p);
-  reinterpret_cast<uint64_t *>(base + (int64_t)y * L)[m] = C ^ F;
+  long long unused_a = 0, unused_d = 0;
+  reinterpret_cast<uint64_t *>(base + (int64_t)y * L)[m] =
+      ising_chunk<0>(C, U, D, lb, rb, r, (colour + y) & 1, thr4, thr8, unused_a, unused_d);
 }
 
 // ---------------------------------------------------------------- generic phase

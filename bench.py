@@ -51,8 +51,8 @@ WIDE_MULS_PER_CLK_PER_SM = 32
 # (mean of two launches captured with ncu, summarised in profiles/), valid
 # while the kernel's sources hash to KERNEL_TRAFFIC_SRC_SHA; otherwise
 # reported as null.
-KERNEL_TRAFFIC_BYTES = (100_678_656 + 11_274_496 + 100_748_800 + 7_459_328) // 2
-KERNEL_TRAFFIC_SRC_SHA = "66288d0cf4178ccd"
+KERNEL_TRAFFIC_BYTES = (100_707_072 + 10_955_776 + 100_703_744 + 7_540_736) // 2
+KERNEL_TRAFFIC_SRC_SHA = "eda6cf8063fe9d0e"
 
 
 def kernel_sha():

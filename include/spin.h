@@ -161,7 +161,8 @@ typedef struct {
  * spin_run, in ONE cooperative kernel launch on `stream`.  Results
  * (lattices, series, exchange decisions) are identical to calling spin_run
  * on each handle.  Supported handles: EA in the coded layout (L <= 32) and
- * 2D int8 ferromagnets with L % 16 == 0 (no exchange for those); at most 16
+ * 2D ferromagnets, int8 with L % 16 == 0 or coded with L % 256 == 0, in the
+ * checkerboard order and without exchange between their slots; at most 16
  * handles and 96 work units (one unit per EA realisation group or Ising
  * lattice).  Work units are spread over teams of co-resident CTAs in
  * proportion to their work; a team synchronises through global-memory

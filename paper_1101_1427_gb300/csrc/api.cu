@@ -266,17 +266,26 @@ int spin_measure(spin_lattice *h, const void *couplings, int64_t *E, int64_t *M,
   return cuda_status(launch_measure(h, ea(h) ? couplings : nullptr, E, M, Q, Ef, Mf));
 }
 
-int spin_pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_t seed,
-                 int64_t *accepted) {
+namespace {
+// One exchange step; `energies` (device, [n_lat]) are the lattices' current
+// energies when the caller has just measured them, else NULL.
+int pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_t seed,
+            int64_t *accepted, const int64_t *energies) {
   if (!h || seed != h->d.seed || !betas) return SPIN_EINVAL;
   if (h->d.model == SPIN_HEISENBERG) return SPIN_EINVAL;
   if (ea(h) && !couplings) return SPIN_EINVAL;
   int rc = upload_pt_tables(h, betas);
   if (rc) return rc;
-  cudaError_t e = launch_pt_swap(h, ea(h) ? couplings : nullptr, accepted);
+  cudaError_t e = launch_pt_swap(h, ea(h) ? couplings : nullptr, accepted, energies);
   if (e != cudaSuccess) return SPIN_ECUDA;
   h->pt_steps_done += 1;
   return SPIN_OK;
+}
+}  // namespace
+
+int spin_pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_t seed,
+                 int64_t *accepted) {
+  return pt_swap(h, couplings, betas, seed, accepted, nullptr);
 }
 
 int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_t n_sweeps,
@@ -302,6 +311,7 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
     if (rc) return rc;
     done += next;
     const int64_t now = h->sweeps_done;
+    const int64_t *energies = nullptr;  // energies measured at this sweep, if any
     if (measuring && now % measure_every == 0) {
       const int64_t nl = h->n_lat;
       const int64_t nq = (int64_t)h->g.n_temps * h->g.n_real;
@@ -311,10 +321,11 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
                         Ef_series ? Ef_series + k_meas * nl : nullptr,
                         Mf_series ? Mf_series + 3 * k_meas * nl : nullptr);
       if (rc) return rc;
+      if (E_series) energies = E_series + k_meas * nl;
       ++k_meas;
     }
     if (pt_every > 0 && now % pt_every == 0) {
-      rc = spin_pt_swap(h, couplings, betas, h->d.seed, accepted);
+      rc = pt_swap(h, couplings, betas, h->d.seed, accepted, energies);
       if (rc) return rc;
     }
   }

@@ -70,7 +70,9 @@ cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps);
 // measure.cu
 cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *M, int64_t *Q,
                            double *Ef, double *Mf);
-cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted);
+// energies: the lattices' current energies if the caller has them (device,
+// [n_lat]), else NULL to compute them
+cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, const int64_t *energies);
 
 // rng.cu
 cudaError_t launch_rng_fill(uint64_t seed, uint32_t w, uint32_t lattice_id, uint32_t sweep,

@@ -186,24 +186,20 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   }
   const uint32_t lane = threadIdx.x & 31;
   const int64_t lat = ((int64_t)a * T + t) * g.n_real + 32 * grp + lane;
+  // E = 2 unsat - 3N, M = N - 2 down, Q = N - 2 diff: block 0 adds the constants
+  const long long n0 = blockIdx.x == 0 ? (long long)N : 0;
   const long long unsat = vc_block_total(CE, sm);
-  if (threadIdx.x < 32 && E) add_ll(&E[lat], 2 * unsat);
+  if (threadIdx.x < 32 && E) add_ll(&E[lat], 2 * unsat - 3 * n0);
   if (M) {
     const long long down = vc_block_total(CM, sm);
-    if (threadIdx.x < 32) add_ll(&M[lat], -2 * down);
+    if (threadIdx.x < 32) add_ll(&M[lat], n0 - 2 * down);
   }
   if (do_q) {
     const long long diff = vc_block_total(CQ, sm);
-    if (threadIdx.x < 32) add_ll(&Q[(int64_t)t * g.n_real + 32 * grp + lane], -2 * diff);
+    if (threadIdx.x < 32) add_ll(&Q[(int64_t)t * g.n_real + 32 * grp + lane], n0 - 2 * diff);
   }
 }
 
-// constant parts: E = 2 unsat - 3N, M = N - 2 down, Q = N - 2 diff
-__global__ void add_const_kernel(long long *__restrict__ v, int64_t n, long long c) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    v[k] += c;
-}
 
 // ---------------------------------------------------------------- Heisenberg
 // Per-block partial sums in double, then a fixed-order second pass, so the
@@ -330,7 +326,9 @@ __global__ void pt_swap_bytes_kernel(uint8_t *__restrict__ s, const uint8_t *__r
 }
 
 // Bitwise exchange of coded EA words: per (a, g, pair) the accepted
-// realisations form a mask A; x = (w_t ^ w_{t+1}) & A exchanges those bits.
+// realisations form a mask A (one warp ballot over their decisions);
+// x = (w_t ^ w_{t+1}) & A exchanges those bits, 16 bytes at a time (N is a
+// multiple of 8 and every word-lattice starts 32-byte aligned).
 __global__ void pt_swap_msc_kernel(uint32_t *__restrict__ w, const uint8_t *__restrict__ decision,
                                    Geom g, int parity) {
   const int G = g.n_real / 32;
@@ -339,17 +337,17 @@ __global__ void pt_swap_msc_kernel(uint32_t *__restrict__ w, const uint8_t *__re
   if (((t - parity) & 1) || t + 1 >= g.n_temps) return;
   const int grp = (int)((wl / g.n_temps) % G);
   const int a = (int)(wl / ((int64_t)g.n_temps * G));
-  uint32_t mask = 0;
   const int64_t lat0 = ((int64_t)a * g.n_temps + t) * g.n_real + 32 * grp;
-  for (int b = 0; b < 32; ++b) mask |= (uint32_t)decision[lat0 + b] << b;
+  const uint32_t mask = __ballot_sync(0xffffffffu, decision[lat0 + (threadIdx.x & 31)] != 0);
   if (!mask) return;
-  uint32_t *w0 = w + wl * g.N, *w1 = w0 + g.N;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+  uint4 *w0 = reinterpret_cast<uint4 *>(w + wl * g.N), *w1 = reinterpret_cast<uint4 *>(w + (wl + 1) * g.N);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N / 4;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t a0 = w0[i], a1 = w1[i];
-    const uint32_t x = (a0 ^ a1) & mask;
-    w0[i] = a0 ^ x;
-    w1[i] = a1 ^ x;
+    const uint4 a0 = w0[i], a1 = w1[i];
+    const uint4 x = make_uint4((a0.x ^ a1.x) & mask, (a0.y ^ a1.y) & mask, (a0.z ^ a1.z) & mask,
+                               (a0.w ^ a1.w) & mask);
+    w0[i] = make_uint4(a0.x ^ x.x, a0.y ^ x.y, a0.z ^ x.z, a0.w ^ x.w);
+    w1[i] = make_uint4(a1.x ^ x.x, a1.y ^ x.y, a1.z ^ x.z, a1.w ^ x.w);
   }
 }
 
@@ -402,19 +400,17 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
   measure_msc_kernel<<<dim3(gx, (unsigned)n_wl), 256, 0, st>>>(
       (const uint32_t *)h->spins, (const uint32_t *)J, g, (long long *)E, (long long *)M,
       (g.n_sets >= 2) ? (long long *)Q : nullptr);
-  if (E) add_const_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)E, nl, -3 * (long long)g.N);
-  if (M) add_const_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)M, nl, (long long)g.N);
-  if (Q && g.n_sets >= 2)
-    add_const_kernel<<<capped((int64_t)g.n_temps * g.n_real, 4096), 256, 0, st>>>(
-        (long long *)Q, (int64_t)g.n_temps * g.n_real, (long long)g.N);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted) {
+cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, const int64_t *energies) {
   const Geom &g = h->g;
   cudaStream_t st = h->stream;
-  cudaError_t e = launch_measure(h, J, h->d_energy, nullptr, nullptr, nullptr, nullptr);
-  if (e != cudaSuccess) return e;
+  if (!energies) {
+    cudaError_t e = launch_measure(h, J, h->d_energy, nullptr, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    energies = h->d_energy;
+  }
   const uint32_t step = (uint32_t)h->pt_steps_done;
   const int parity = (int)(step & 1u);
   const int n_pairs = (g.n_temps - parity) / 2;
@@ -422,11 +418,11 @@ cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted) {
   if (n_pairs <= 0) return cudaSuccess;
   const int64_t total = (int64_t)g.n_sets * n_pairs * g.n_real;
   pt_decide_kernel<<<grid_for(total, 256), 256, 0, st>>>(
-      (const long long *)h->d_energy, g, h->d_pt_dbeta, h->d_pt_thr, h->d_pt_off, h->d_pt_len,
+      (const long long *)energies, g, h->d_pt_dbeta, h->d_pt_thr, h->d_pt_off, h->d_pt_len,
       make_round_keys(h->d.seed), step, decision, (long long *)accepted);
   if (h->d.layout == SPIN_MSC1 && h->d.model == SPIN_EA) {
     const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-    pt_swap_msc_kernel<<<dim3(capped(g.N, 64), (unsigned)n_wl), 256, 0, st>>>(
+    pt_swap_msc_kernel<<<dim3(capped(g.N / 4, 64), (unsigned)n_wl), 256, 0, st>>>(
         (uint32_t *)h->spins, decision, g, parity);
   } else {
     int64_t lat_bytes = g.N;  // int8

@@ -168,8 +168,39 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   const uint32_t *s1 = s + (size_t)G * T * N;  // set 1, same (g, t)
   uint32_t CE[kThr] = {}, CM[kThr] = {}, CQ[kThr] = {};
   const uint32_t half = N / 2;
-  // storage index k: colour c = k / half, colour index j = k % half; the
-  // bonds (i, i + e_d) of every site count each bond once
+  // the bonds (i, i + e_d) of every site count each bond once
+  if ((L & 7u) == 0) {
+    // four consecutive colour indices of one row per step, 16-byte loads
+    const uint32_t quads = half / 4, LH = L / 2;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * quads; q += gridDim.x * blockDim.x) {
+      const int c = q >= quads ? 1 : 0;
+      const uint32_t j0 = 4 * (q - (uint32_t)c * quads);
+      const uint32_t co = (uint32_t)c * half, oc = (uint32_t)(c ^ 1) * half;
+      const CsSite st = cs_site(j0, c, L, g.fL);
+      const uint32_t p = st.i & 1u, jr = st.rb >> 1;
+      const uint4 S = ldv4(s + co + j0), O = ldv4(s + oc + j0);
+      // x + 1: the other colour at the same index (p = 0) or the next (p = 1)
+      const uint32_t jx = j0 + 4 == jr + LH ? jr : j0 + 4;
+      const uint32_t Ox = p ? s[oc + jx] : 0u;
+      const uint4 YP = ldv4(s + oc + (st.yp >> 1)), ZP = ldv4(s + oc + (st.zp >> 1));
+      const uint4 JX = ldv4(Jg + co + j0), JY = ldv4(Jg + N + co + j0), JZ = ldv4(Jg + 2 * N + co + j0);
+      const uint4 S1 = do_q ? ldv4(s1 + co + j0) : make_uint4(0, 0, 0, 0);
+      const uint32_t sv[4] = {S.x, S.y, S.z, S.w}, ov[4] = {O.x, O.y, O.z, O.w};
+      const uint32_t yv[4] = {YP.x, YP.y, YP.z, YP.w}, zv[4] = {ZP.x, ZP.y, ZP.z, ZP.w};
+      const uint32_t jxv[4] = {JX.x, JX.y, JX.z, JX.w}, jyv[4] = {JY.x, JY.y, JY.z, JY.w};
+      const uint32_t jzv[4] = {JZ.x, JZ.y, JZ.z, JZ.w}, s1v[4] = {S1.x, S1.y, S1.z, S1.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t xp = p ? (k < 3 ? ov[k + 1] : Ox) : ov[k];
+        const uint32_t u0 = sv[k] ^ xp ^ jxv[k], u1 = sv[k] ^ yv[k] ^ jyv[k], u2 = sv[k] ^ zv[k] ^ jzv[k];
+        vc_add(CE, u0 ^ u1 ^ u2, 0);
+        vc_add(CE, (u0 & u1) | (u2 & (u0 ^ u1)), 1);
+        if (M) vc_add(CM, sv[k], 0);
+        if (do_q) vc_add(CQ, sv[k] ^ s1v[k], 0);
+      }
+    }
+  } else
+  // storage index k: colour c = k / half, colour index j = k % half
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     const int c = k >= half ? 1 : 0;
     const uint32_t j = k - (uint32_t)c * half;

@@ -326,7 +326,14 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
     acc = word_of(w, (uint32_t)r & 3u) < thr;
   }
   decision[lat0] = acc ? 1 : 0;
-  if (acc && accepted) add_ll(&accepted[a * g.n_temps + t], 1);
+  if (!accepted) return;
+  if ((g.n_real & 31) == 0) {
+    // the 32 lanes of a warp share (a, t): one atomic per warp
+    const uint32_t votes = __ballot_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && votes) add_ll(&accepted[a * g.n_temps + t], __popc(votes));
+  } else if (acc) {
+    add_ll(&accepted[a * g.n_temps + t], 1);
+  }
 }
 
 // Exchange of whole lattices (int8, or coded 2D lattices): 16 bytes per

@@ -461,7 +461,8 @@ def run_gpu(args, rank, world, local_rank):
     i8_value = world * k8 * flips_per_step / (max_over_ranks(timed(step8, k8)) * 1e6)
     lat8.close()
 
-    side = side_configs(torch, sp, B, stream) if rank == 0 and not args.no_side else {}
+    # the side configurations and the CPU baseline are single-GPU context: rank 0 at N = 1 only
+    side = side_configs(torch, sp, B, stream) if rank == 0 and world == 1 and not args.no_side else {}
     if rank != 0:
         return
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -469,7 +470,11 @@ def run_gpu(args, rank, world, local_rank):
     achieved = WIDE_MULS_PER_FLIP * flips_per_launch / (launch_ms * 1e-3) / 1e9  # Gmul/s
     peak = sms * WIDE_MULS_PER_CLK_PER_SM * mhz * 1e6 / 1e9
     traffic = KERNEL_TRAFFIC_BYTES if KERNEL_TRAFFIC_SRC_SHA == kernel_sha() else None
-    cpu_value, cpu_flips, cpu_s = oracle_rate(args.cpu_seconds)
+    cpu_baseline = None
+    if world == 1:
+        cpu_value, cpu_flips, cpu_s = oracle_rate(args.cpu_seconds)
+        cpu_baseline = {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                        "sample": f"{cpu_flips} flips on 1024^2 lattices at beta=0.4407 ({cpu_s:.1f} s)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -487,9 +492,7 @@ def run_gpu(args, rank, world, local_rank):
                      "flips_per_launch": flips_per_launch,
                      "peak_basis": f"{sms} SMs x {WIDE_MULS_PER_CLK_PER_SM} wide multiplies/clk x "
                                    f"{mhz:.0f} MHz (sampled median); {WIDE_MULS_PER_FLIP} per flip"},
-        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{cpu_flips} flips on 1024^2 lattices at beta=0.4407 "
-                                   f"({cpu_s:.1f} s)"},
+        "cpu_baseline": cpu_baseline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spin_bytes,
                 "d2h_bytes_per_step": spin_bytes + 8 * 2 * n_lat},
         "gpu_launches": args.steps * (2 * S + 1),

@@ -232,7 +232,7 @@ def dcb(torch, sp, B, stream):
     lattices of the headline workload."""
     out = {}
     lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=len(BETAS), seed=21)
-    for T, k in ((16, 100), (64, 10), (64, 100)):
+    for T, k in ((16, 100), (32, 100), (64, 10), (64, 100)):
         lat.set_update_order(B.SPIN_ORDER_DCB, T, k)
         lat.set_counters(0, 0)
         B.spin_sweep(lat.h, None, BETAS, k, lat.seed)

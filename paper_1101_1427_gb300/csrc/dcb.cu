@@ -25,19 +25,27 @@ __global__ void __launch_bounds__(256) dcb_tile_kernel(int8_t *__restrict__ spin
   constexpr int kWords = kT / 8 + 2;  // words per shared row
   constexpr int kCpr = kT / 8;        // chunks per tile row
   constexpr int kChunks = kT * kCpr;  // chunks per tile
-  __shared__ __align__(16) uint64_t sw[(kT + 2) * kWords];
+  // small tiles share a CTA of 256 threads (kTPT threads per tile)
+  constexpr int kTPT = kChunks < 256 ? kChunks : 256;
+  constexpr int kTiles = 256 / kTPT;
+  constexpr int kTileWords = (kT + 2) * kWords;
+  __shared__ __align__(16) uint64_t smem[kTiles * kTileWords];
+  const int tsub = threadIdx.x / kTPT, tid = threadIdx.x - tsub * kTPT;
+  uint64_t *sw = smem + tsub * kTileWords;
   const uint8_t *sb = reinterpret_cast<const uint8_t *>(sw);
   const int half = (L / kT) >> 1;
-  const int t = blockIdx.x;
+  const int t = blockIdx.x * kTiles + tsub;
+  const bool active = t < (L / kT) * half;  // the last CTA may hold fewer tiles
   const int by = t / half, bx = 2 * (t % half) + ((by + coarse) & 1);
   const int64_t lat = blockIdx.y;
   int8_t *base = spins + lat * (int64_t)L * L;
   const int x0 = bx * kT, y0 = by * kT;
-  for (int q = threadIdx.x; q < (kT + 2) * kWords; q += blockDim.x) {
-    const int ry = q / kWords - 1, rw = q % kWords - 1;
-    const int gy = (y0 + ry + L) % L, gx = (x0 + 8 * rw + L) % L;  // L, x0 are multiples of 8
-    sw[q] = *reinterpret_cast<const uint64_t *>(base + (int64_t)gy * L + gx);
-  }
+  if (active)
+    for (int q = tid; q < kTileWords; q += kTPT) {
+      const int ry = q / kWords - 1, rw = q % kWords - 1;
+      const int gy = (y0 + ry + L) % L, gx = (x0 + 8 * rw + L) % L;  // L, x0 are multiples of 8
+      sw[q] = *reinterpret_cast<const uint64_t *>(base + (int64_t)gy * L + gx);
+    }
   __syncthreads();
   const int slot = slot_of(g, lat);
   const uint32_t thr4 = __ldg(thr + 4 * slot + 1), thr8 = __ldg(thr + 4 * slot + 2);
@@ -47,33 +55,38 @@ __global__ void __launch_bounds__(256) dcb_tile_kernel(int8_t *__restrict__ spin
   for (int h = 0; h < k; ++h) {
     for (int c = 0; c < 2; ++c) {
       const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)c, 0);
-      for (int q = threadIdx.x; q < kChunks; q += blockDim.x) {
-        const int ty = q / kCpr, m = q % kCpr;
-        const int row = ty + 1, word = m + 1;
-        const uint64_t C = sw[row * kWords + word];
-        const uint64_t U = sw[(row - 1) * kWords + word], D = sw[(row + 1) * kWords + word];
-        const uint64_t lb = sb[(row * kWords + word) * 8 - 1], rb = sb[(row * kWords + word) * 8 + 8];
-        const int gy = y0 + ty;
-        const uint32_t gchunk = (uint32_t)gy * row_chunks + (uint32_t)(x0 >> 3) + (uint32_t)m;
-        const uint4 r = philox(make_uint4(gchunk, sweep0 + (uint32_t)h, lid, wctr), rk);
-        sw[row * kWords + word] = ising_chunk<0>(C, U, D, lb, rb, r, (c + gy) & 1, thr4, thr8, unused_a, unused_d);
-      }
+      if (active)
+        for (int q = tid; q < kChunks; q += kTPT) {
+          const int ty = q / kCpr, m = q % kCpr;
+          const int row = ty + 1, word = m + 1;
+          const uint64_t C = sw[row * kWords + word];
+          const uint64_t U = sw[(row - 1) * kWords + word], D = sw[(row + 1) * kWords + word];
+          const uint64_t lb = sb[(row * kWords + word) * 8 - 1], rb = sb[(row * kWords + word) * 8 + 8];
+          const int gy = y0 + ty;
+          const uint32_t gchunk = (uint32_t)gy * row_chunks + (uint32_t)(x0 >> 3) + (uint32_t)m;
+          const uint4 r = philox(make_uint4(gchunk, sweep0 + (uint32_t)h, lid, wctr), rk);
+          sw[row * kWords + word] =
+              ising_chunk<0>(C, U, D, lb, rb, r, (c + gy) & 1, thr4, thr8, unused_a, unused_d);
+        }
       __syncthreads();
     }
   }
-  for (int q = threadIdx.x; q < kChunks; q += blockDim.x) {
-    const int ty = q / kCpr, m = q % kCpr;
-    *reinterpret_cast<uint64_t *>(base + (int64_t)(y0 + ty) * L + x0 + 8 * m) = sw[(ty + 1) * kWords + m + 1];
-  }
+  if (active)
+    for (int q = tid; q < kChunks; q += kTPT) {
+      const int ty = q / kCpr, m = q % kCpr;
+      *reinterpret_cast<uint64_t *>(base + (int64_t)(y0 + ty) * L + x0 + 8 * m) = sw[(ty + 1) * kWords + m + 1];
+    }
 }
 
 template <int kT>
 cudaError_t launch_tiles(spin_lattice *h, int coarse, uint32_t sweep0) {
+  constexpr int kChunks = kT * (kT / 8);
+  constexpr int kTiles = kChunks < 256 ? 256 / kChunks : 1;
   const int B = h->g.L / kT;
-  const int threads = kT * kT / 8 < 256 ? kT * kT / 8 : 256;
-  dim3 grid((unsigned)(B * B / 2), (unsigned)h->n_lat);
-  dcb_tile_kernel<kT><<<grid, threads, 0, h->stream>>>((int8_t *)h->spins, h->g.L, coarse, sweep0, h->order_hits,
-                                                       h->d_thr, h->g, make_round_keys(h->d.seed));
+  const int n_tiles = B * B / 2;
+  dim3 grid((unsigned)((n_tiles + kTiles - 1) / kTiles), (unsigned)h->n_lat);
+  dcb_tile_kernel<kT><<<grid, 256, 0, h->stream>>>((int8_t *)h->spins, h->g.L, coarse, sweep0, h->order_hits,
+                                                    h->d_thr, h->g, make_round_keys(h->d.seed));
   return cudaGetLastError();
 }
 

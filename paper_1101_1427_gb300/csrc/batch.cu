@@ -21,6 +21,7 @@
 // The kernel is launched cooperatively so that all CTAs are co-resident.
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "ea_cs.cuh"
@@ -970,10 +971,15 @@ static cudaError_t batch_launch(BatchParams &prm, int grid, cudaStream_t st, int
   return cudaLaunchKernelEx(&cfg, batch_kernel, prm, err);
 }
 
+// The launch parameters are built in function-static buffers and the tuning
+// cache is shared: calls from several host threads are serialised.
+static std::recursive_mutex g_batch_mutex;
+
 extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                               int32_t measure_every, int32_t pt_every, void *stream_v) {
   if (!items || n_items <= 0 || n_items > kMaxHandles || n_sweeps < 0 || measure_every < 0 || pt_every < 0)
     return SPIN_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock(g_batch_mutex);
   cudaStream_t st = (cudaStream_t)stream_v;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return SPIN_ECUDA;
@@ -1096,6 +1102,7 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
 extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                                int32_t measure_every, int32_t pt_every, void *stream_v,
                                int32_t *best_out) {
+  std::lock_guard<std::recursive_mutex> lock(g_batch_mutex);
   if (!items || n_items <= 0 || n_items > kMaxHandles) return SPIN_EINVAL;
   cudaStream_t st = (cudaStream_t)stream_v;
   int per_sm = 0;

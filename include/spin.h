@@ -106,7 +106,11 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
  * as in spin_init.  seed must equal the handle's seed (else SPIN_EINVAL).
  * Sweep k of this call uses sweep counter value (sweeps done so far) + k, so
  * consecutive calls continue one Markov chain.  Heisenberg spins are
- * renormalised after every sweep whose 1-based count is a multiple of 100. */
+ * renormalised after every sweep whose 1-based count is a multiple of 100.
+ * The per-handle calls take their sweep numbers from the host counter when
+ * they are enqueued, so a CUDA graph captured around them would repeat the
+ * same random numbers on every replay; the batched launch (spin_batch_run)
+ * reads its counters on the device and is the form meant for capture. */
 int spin_sweep(spin_lattice *lat, const void *couplings, const double *betas,
                int64_t n_sweeps, uint64_t seed);
 

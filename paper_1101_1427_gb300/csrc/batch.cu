@@ -1096,9 +1096,9 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
   return SPIN_OK;
 }
 
-// Autotuner: times one short batch per CTAs-per-SM candidate on copies of
-// the spins (the handles' own state is untouched) and caches the fastest
-// for this batch signature.
+// Autotuner: times one short batch per (CTAs per SM, Ising weight) candidate
+// on copies of the spins (the handles' own state is untouched) and caches
+// the fastest for this batch signature.
 extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                                int32_t measure_every, int32_t pt_every, void *stream_v,
                                int32_t *best_out) {

@@ -206,26 +206,32 @@ cudaError_t launch_pack_msc2d(spin_lattice *h, const int8_t *in) {
 __global__ void msc2d_measure_kernel(const uint32_t *__restrict__ w, Msc2d m, int64_t n_lat,
                                      long long *__restrict__ E, long long *__restrict__ M) {
   const int64_t lat = blockIdx.y;
-  const int64_t words = (int64_t)m.L * m.wpr;  // colour-0 words of one lattice
+  const uint32_t blocks = (uint32_t)m.L * (uint32_t)m.bpr;  // blocks of 4 colour-0 words per lattice
+  const uint32_t *wl = w + lat * m.lat_words;
   long long anti = 0, down = 0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < words;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(k / m.wpr), wi = (int)(k % m.wpr);
-    const int B = wi >> 2, q = wi & 3;
-    const int yu = y == 0 ? m.L - 1 : y - 1, yd = y == m.L - 1 ? 0 : y + 1;
-    const uint32_t S = w[row_word(m, lat, 0, y) + wi];
-    const uint32_t *O = w + row_word(m, lat, 1, y);
-    const uint32_t up = w[row_word(m, lat, 1, yu) + wi], dn = w[row_word(m, lat, 1, yd) + wi];
-    uint32_t sh;
-    if (((0 + y) & 1) == 0) {
-      const int Bp = B == 0 ? m.bpr - 1 : B - 1;
-      sh = q == 0 ? (O[4 * B + 3] << 1) | (O[4 * Bp + 3] >> 31) : O[4 * B + q - 1];
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < blocks; k += gridDim.x * blockDim.x) {
+    const uint32_t y = k / (uint32_t)m.bpr, B = k - y * (uint32_t)m.bpr;
+    const uint32_t yu = y == 0 ? (uint32_t)m.L - 1 : y - 1, yd = y == (uint32_t)m.L - 1 ? 0 : y + 1;
+    const uint32_t *O = wl + ((int64_t)m.L + y) * m.wpr;  // colour 1, row y
+    const uint4 s = *reinterpret_cast<const uint4 *>(wl + (int64_t)y * m.wpr + 4 * B);
+    const uint4 o = *reinterpret_cast<const uint4 *>(O + 4 * B);
+    const uint4 u = *reinterpret_cast<const uint4 *>(wl + ((int64_t)m.L + yu) * m.wpr + 4 * B);
+    const uint4 d = *reinterpret_cast<const uint4 *>(wl + ((int64_t)m.L + yd) * m.wpr + 4 * B);
+    // second horizontal neighbour of the colour-0 sites: k - 1 (y even) or k + 1 (y odd)
+    uint4 sh;
+    if ((y & 1u) == 0) {
+      const uint32_t Bp = B == 0 ? (uint32_t)m.bpr - 1 : B - 1;
+      sh = make_uint4((o.w << 1) | (O[4 * Bp + 3] >> 31), o.x, o.y, o.z);
     } else {
-      const int Bn = B == m.bpr - 1 ? 0 : B + 1;
-      sh = q == 3 ? (O[4 * B] >> 1) | (O[4 * Bn] << 31) : O[4 * B + q + 1];
+      const uint32_t Bn = B == (uint32_t)m.bpr - 1 ? 0 : B + 1;
+      sh = make_uint4(o.y, o.z, o.w, (o.x >> 1) | (O[4 * Bn] << 31));
     }
-    anti += __popc(S ^ up) + __popc(S ^ dn) + __popc(S ^ O[wi]) + __popc(S ^ sh);
-    down += __popc(S) + __popc(w[row_word(m, lat, 1, y) + wi]);
+    anti += __popc(s.x ^ u.x) + __popc(s.x ^ d.x) + __popc(s.x ^ o.x) + __popc(s.x ^ sh.x) +
+            __popc(s.y ^ u.y) + __popc(s.y ^ d.y) + __popc(s.y ^ o.y) + __popc(s.y ^ sh.y) +
+            __popc(s.z ^ u.z) + __popc(s.z ^ d.z) + __popc(s.z ^ o.z) + __popc(s.z ^ sh.z) +
+            __popc(s.w ^ u.w) + __popc(s.w ^ d.w) + __popc(s.w ^ o.w) + __popc(s.w ^ sh.w);
+    down += __popc(s.x) + __popc(s.y) + __popc(s.z) + __popc(s.w) + __popc(o.x) + __popc(o.y) + __popc(o.z) +
+            __popc(o.w);
   }
   anti = warp_sum(anti);
   down = warp_sum(down);
@@ -248,8 +254,8 @@ cudaError_t launch_measure_msc2d(spin_lattice *h, int64_t *E, int64_t *M) {
   if (!mm) mm = (long long *)h->d_energy + h->n_lat;
   cudaMemsetAsync(e, 0, sizeof(long long) * h->n_lat, h->stream);
   cudaMemsetAsync(mm, 0, sizeof(long long) * h->n_lat, h->stream);
-  const int64_t words = (int64_t)m.L * m.wpr;
-  unsigned gx = grid_for(words, 256);
+  const int64_t blocks = (int64_t)m.L * m.bpr;  // one thread per block of 4 colour-0 words
+  unsigned gx = grid_for(blocks, 256);
   if (gx > 4096u) gx = 4096u;
   msc2d_measure_kernel<<<dim3(gx, (unsigned)h->n_lat), 256, 0, h->stream>>>(
       (const uint32_t *)h->spins, m, h->n_lat, e, mm);

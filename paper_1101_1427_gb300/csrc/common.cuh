@@ -56,6 +56,49 @@ __device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys &rk) {
   return c;
 }
 
+// Philox4x32-10 for counters (x0, x1, x2, x3) of which only x1 changes from
+// call to call (a thread re-drawing for the same sites at successive sweep
+// numbers): the products and XORs of rounds 0 to 2 that do not involve x1
+// are computed once, leaving 16 of the 20 multiplies per call.  Equal to
+// philox() word for word.
+struct PhiloxX1 {
+  uint32_t a;    // hi(M1 x2) ^ k0[0]:             round-1 word 0 is a ^ x1
+  uint32_t b;    // lo(M0 x0) ^ k1[1]:             round-2 word 2 is hi(M0 c1.x) ^ b
+  uint32_t c2y;  // round-2 word 1
+  uint32_t hz;   // hi(M0 c2.x) ^ k1[2]:           round-3 word 2 is hz ^ c2.w
+  uint32_t c3w;  // round-3 word 3
+};
+
+__device__ __forceinline__ PhiloxX1 philox_x1_setup(uint32_t x0, uint32_t x2, uint32_t x3, const RoundKeys &rk) {
+  const uint64_t p0 = mul_wide(0xD2511F53u, x0), p1 = mul_wide(0xCD9E8D57u, x2);
+  PhiloxX1 q;
+  q.a = (uint32_t)(p1 >> 32) ^ rk.k0[0];
+  const uint32_t c1y = (uint32_t)p1, c1z = (uint32_t)(p0 >> 32) ^ x3 ^ rk.k1[0];
+  q.b = (uint32_t)p0 ^ rk.k1[1];
+  const uint64_t r1 = mul_wide(0xCD9E8D57u, c1z);
+  const uint32_t c2x = (uint32_t)(r1 >> 32) ^ c1y ^ rk.k0[1];
+  q.c2y = (uint32_t)r1;
+  const uint64_t r2 = mul_wide(0xD2511F53u, c2x);
+  q.hz = (uint32_t)(r2 >> 32) ^ rk.k1[2];
+  q.c3w = (uint32_t)r2;
+  return q;
+}
+
+__device__ __forceinline__ uint4 philox_x1(const PhiloxX1 &q, uint32_t x1, const RoundKeys &rk) {
+  const uint64_t p0 = mul_wide(0xD2511F53u, q.a ^ x1);             // round 1, word 0 product
+  const uint32_t c2z = (uint32_t)(p0 >> 32) ^ q.b, c2w = (uint32_t)p0;
+  const uint64_t p1 = mul_wide(0xCD9E8D57u, c2z);                  // round 2, word 2 product
+  uint4 c = make_uint4((uint32_t)(p1 >> 32) ^ q.c2y ^ rk.k0[2], (uint32_t)p1, q.hz ^ c2w, q.c3w);
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    const uint64_t m0 = mul_wide(0xD2511F53u, c.x);
+    const uint64_t m1 = mul_wide(0xCD9E8D57u, c.z);
+    c = make_uint4((uint32_t)(m1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)m1, (uint32_t)(m0 >> 32) ^ c.w ^ rk.k1[r],
+                   (uint32_t)m0);
+  }
+  return c;
+}
+
 __host__ __device__ __forceinline__ uint32_t ctr_w(uint32_t tag, uint32_t colour, uint32_t extra) {
   return (tag << 28) | (colour << 27) | extra;
 }

@@ -52,11 +52,28 @@ __global__ void __launch_bounds__(256) dcb_tile_kernel(int8_t *__restrict__ spin
   const uint32_t lid = lattice_id_of(g, lat);
   const uint32_t row_chunks = (uint32_t)L >> 3;
   long long unused_a = 0, unused_d = 0;
+  // a thread keeps the same kPer chunks for all hits, and only the sweep
+  // word of their Philox counters changes: the rest of the first rounds is
+  // computed once (PhiloxX1) where that fits in registers
+  constexpr int kPer = kChunks / kTPT;
+  constexpr bool kHoist = kPer <= 2;
+  PhiloxX1 pre[kHoist ? kPer : 1][2];
+  if (kHoist && active)
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int q = tid + i * kTPT;
+      const uint32_t gchunk = (uint32_t)(y0 + q / kCpr) * row_chunks + (uint32_t)(x0 >> 3) + (uint32_t)(q % kCpr);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) pre[kHoist ? i : 0][c] = philox_x1_setup(gchunk, lid, ctr_w(TAG_UPDATE, (uint32_t)c, 0), rk);
+    }
   for (int h = 0; h < k; ++h) {
+#pragma unroll
     for (int c = 0; c < 2; ++c) {
       const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)c, 0);
       if (active)
-        for (int q = tid; q < kChunks; q += kTPT) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          const int q = tid + i * kTPT;
           const int ty = q / kCpr, m = q % kCpr;
           const int row = ty + 1, word = m + 1;
           const uint64_t C = sw[row * kWords + word];
@@ -64,7 +81,8 @@ __global__ void __launch_bounds__(256) dcb_tile_kernel(int8_t *__restrict__ spin
           const uint64_t lb = sb[(row * kWords + word) * 8 - 1], rb = sb[(row * kWords + word) * 8 + 8];
           const int gy = y0 + ty;
           const uint32_t gchunk = (uint32_t)gy * row_chunks + (uint32_t)(x0 >> 3) + (uint32_t)m;
-          const uint4 r = philox(make_uint4(gchunk, sweep0 + (uint32_t)h, lid, wctr), rk);
+          const uint4 r = kHoist ? philox_x1(pre[kHoist ? i : 0][c], sweep0 + (uint32_t)h, rk)
+                                 : philox(make_uint4(gchunk, sweep0 + (uint32_t)h, lid, wctr), rk);
           sw[row * kWords + word] =
               ising_chunk<0>(C, U, D, lb, rb, r, (c + gy) & 1, thr4, thr8, unused_a, unused_d);
         }

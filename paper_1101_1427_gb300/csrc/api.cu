@@ -3,6 +3,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "internal.h"
@@ -198,6 +199,8 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   h->g.fquads = make_fastdiv((uint32_t)((h->g.N / 2 + 3) / 4));
   h->g.freal = make_fastdiv((uint32_t)desc->n_real);
   h->g.ftemps = make_fastdiv((uint32_t)desc->n_temps);
+  h->g.fgrp = make_fastdiv((uint32_t)std::max(1, desc->n_real / 32));
+  h->g.fgrp2 = make_fastdiv((uint32_t)std::max(1, desc->n_real / 64));
   h->n_lat = (int64_t)desc->n_sets * desc->n_temps * desc->n_real;
   h->variant = (desc->model == SPIN_ISING && desc->dim == 2 && desc->layout == SPIN_I8 &&
                 fused2d_supported(desc->L))

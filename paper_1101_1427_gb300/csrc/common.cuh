@@ -154,6 +154,8 @@ struct Geom {
   FastDiv fquads;  // division by (N / 2 + 3) / 4
   FastDiv freal;   // division by n_real
   FastDiv ftemps;  // division by n_temps
+  FastDiv fgrp;    // division by the number of 32-realisation groups (at least 1)
+  FastDiv fgrp2;   // division by the number of 64-realisation group pairs (at least 1)
 };
 
 // Colour (x + y + z) mod 2 of site i.

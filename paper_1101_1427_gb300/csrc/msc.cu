@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     const uint32_t wl = fdiv(k, g.fquads), j4 = k - wl * quads;
-    const uint32_t t = wl % T, grp = (wl / T) % G, a = wl / (T * G);
+    const uint32_t st = fdiv(wl, g.ftemps), t = wl - st * T;  // wl = (a G + grp) T + t
+    const uint32_t a = fdiv(st, g.fgrp), grp = st - a * G;
     const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, grp, t), wctr), rk);
     const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
     ea_cs_quad<false>(w + (size_t)wl * N, J + (size_t)grp * 3 * N, j4, colour, L, N, g.fL, r, t4, t8,
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(256) msc_phase_pair_kernel(uint32_t *__restric
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     const uint32_t pl = fdiv(k, g.fquads), j4 = k - pl * quads;
-    const uint32_t t = pl % T, q = (pl / T) % G2, a = pl / (T * G2);
+    const uint32_t st = fdiv(pl, g.ftemps), t = pl - st * T;  // pl = (a G2 + q) T + t
+    const uint32_t a = fdiv(st, g.fgrp2), q = st - a * G2;
     const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, q, t), wctr), rk);
     const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
     const size_t wl0 = ((size_t)a * G + 2 * q) * T + t;  // group 2q; group 2q + 1 is T word-lattices on

@@ -501,6 +501,31 @@ def run_gpu(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def pipe_rates(torch, B, stream, bpsm=8, iters=4096):
+    """Operations per clock per SM of the instructions Philox and the updates
+    are built from (spin_pipe_probe: 8 CTAs of 256 threads per SM, eight
+    independent chains per thread): per SM, all its CTAs' operations over the
+    span from the earliest start to the latest end of its CTAs in SM clocks;
+    median over SMs."""
+    import numpy as np
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clocks = torch.zeros(3 * sms * bpsm, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(sms * bpsm * 256, dtype=torch.int32, device="cuda")
+    out = {}
+    names = ("mul_wide", "mad_hi", "lop3", "iadd3", "ffma", "mufu_rsq")
+    for op, nm in enumerate(names):
+        B.spin_pipe_probe(op, bpsm, iters // 8, clocks, sink, stream.cuda_stream)  # warm-up
+        B.spin_pipe_probe(op, bpsm, iters, clocks, sink, stream.cuda_stream)
+        torch.cuda.synchronize()
+        c = clocks.view(-1, 3).cpu().numpy()
+        rates = []
+        for m in np.unique(c[:, 2]):
+            mine = c[c[:, 2] == m]
+            rates.append(256 * 8 * iters * len(mine) / float(mine[:, 1].max() - mine[:, 0].min()))
+        out[f"{nm}_per_clk_per_sm"] = round(float(np.median(rates)), 2)
+    return out
+
+
 def run_case(name):
     """One kernel family on a small case with few launches (for profilers):
     prints its throughput; not the benchmark line."""
@@ -552,6 +577,9 @@ def run_case(name):
         B.spin_sweep(lat.h, None, [0.693], 2, lat.seed)
         b.record(stream)
         flips = 2 * 128 ** 3
+    elif name == "pipes":
+        print(json.dumps({"case": name, **pipe_rates(torch, B, stream)}), flush=True)
+        return
     elif name == "rng":
         threads, calls = 152 * 2048, 256
         out = torch.empty(threads, dtype=torch.int32, device="cuda")
@@ -575,7 +603,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, uneven, ising_pt, dcb)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, pipes, uneven, ising_pt, dcb)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -226,6 +226,40 @@ int spin_rng_fill(uint64_t seed, uint32_t tag, uint32_t colour, uint32_t extra,
  * threads * calls must stay below 2^32. */
 int spin_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out, void *stream);
 
+/* Instruction-throughput probe for the roofline of the sweeps (the
+ * operations of Philox4x32-10 and of the updates; no counterpart in the
+ * paper).  Launches blocks_per_sm CTAs of 256 threads on every SM; every
+ * thread g (global index) keeps eight chains x[c], c < 8, and runs `iters`
+ * iterations of one operation on all eight:
+ *   SPIN_PIPE_MUL_WIDE  64-bit x[c] = lo32(x[c]) * 0xD2511F53 + x[c] (mad.wide.u32), x[c] = 8 g + c + 1
+ *   SPIN_PIPE_MAD_HI    x[c] = hi32(x[c] * 0xCD9E8D57) + 0x9E3779B9 (mad.hi.u32), x[c] = 8 g + c + 1
+ *   SPIN_PIPE_LOP3      x'[c] = x[c] ^ x[c+1] ^ x[c+2] (indices mod 8, all from the old x; lop3.b32), x[c] = 8 g + c + 1
+ *   SPIN_PIPE_IADD3     x'[c] = x[c] + x[c+1] + x[c+2] mod 2^32 (as LOP3), x[c] = 8 g + c + 1
+ *   SPIN_PIPE_FFMA      x[c] = fma(x[c], 0.999f, 0.001f), x[c] = 1 + (8 g + c) 2^-20 (FP32)
+ *   SPIN_PIPE_MUFU_RSQ  x[c] = rsqrt.approx.ftz(x[c]), same start (FP32)
+ * (8 operations per iteration), then writes sink[g] = XOR over c of x[c]
+ * (MUL_WIDE: of lo32 ^ hi32; FFMA, MUFU_RSQ: the bits of the FP32 sum
+ * x[0] + ... + x[7], added in that order), and for every CTA b
+ * clocks[3b] and clocks[3b + 1], the SM clock (clock64) after the barriers
+ * before and after the loop, and clocks[3b + 2], the index of its SM.  The
+ * CTAs of one SM do not progress evenly, so the rate of SM m is
+ * 256 * 8 * iters * (its CTAs) / (latest end - earliest start over its CTAs)
+ * operations per clock.  clocks (int64, 3 per CTA, SMs * blocks_per_sm CTAs)
+ * and sink (uint32, 256 entries per CTA) are caller-owned device buffers;
+ * `sms` returns the SM count (host pointer, may be NULL).  SPIN_EINVAL if op
+ * is unknown, blocks_per_sm is outside 1..8 or that many CTAs of this kernel
+ * cannot be resident on one SM together. */
+typedef enum {
+  SPIN_PIPE_MUL_WIDE = 0,
+  SPIN_PIPE_MAD_HI = 1,
+  SPIN_PIPE_LOP3 = 2,
+  SPIN_PIPE_IADD3 = 3,
+  SPIN_PIPE_FFMA = 4,
+  SPIN_PIPE_MUFU_RSQ = 5
+} spin_pipe_op;
+int spin_pipe_probe(int op, int32_t blocks_per_sm, uint32_t iters, int64_t *clocks, uint32_t *sink,
+                    int32_t *sms, void *stream);
+
 /* Heisenberg energy and magnetisation (as Ef and Mf of spin_measure) for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this entry point exists for library users: code inside a framework that

@@ -14,6 +14,8 @@ SPIN_OK, SPIN_EINVAL, SPIN_EALIGN, SPIN_ENOMEM, SPIN_ECUDA, SPIN_ETIMEOUT = 0, -
 SPIN_ISING, SPIN_EA, SPIN_HEISENBERG = 0, 1, 2
 SPIN_I8, SPIN_MSC1, SPIN_F32X4 = 0, 1, 2
 SPIN_ORDER_CHECKERBOARD, SPIN_ORDER_DCB, SPIN_ORDER_DCB_SYMMETRIC = 0, 1, 2
+(SPIN_PIPE_MUL_WIDE, SPIN_PIPE_MAD_HI, SPIN_PIPE_LOP3, SPIN_PIPE_IADD3, SPIN_PIPE_FFMA,
+ SPIN_PIPE_MUFU_RSQ) = range(6)
 TAG_UPDATE, TAG_INIT, TAG_COUPLING, TAG_PT, TAG_HEIS, TAG_HEIS_INIT = range(6)
 
 
@@ -56,6 +58,7 @@ def lib():
         L.spin_pack_i8.argtypes = [p, p]
         L.spin_rng_fill.argtypes = [u64, u32, u32, u32, u32, u32, u64, p, p]
         L.spin_rng_probe.argtypes = [u64, u32, u32, p, p]
+        L.spin_pipe_probe.argtypes = [C.c_int, i32, u32, p, p, p, p]
         L.spin_sync.argtypes = [p]
         L.spin_heis_measure_noalloc.argtypes = [p, i32, i32, p, p, p]
         L.spin_batch_run.argtypes = [p, C.c_int, i64, i32, i32, p]
@@ -76,7 +79,7 @@ def lib():
         L.spin_destroy.argtypes = [p]
         L.spin_destroy.restype = None
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
-                     "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_sync",
+                     "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_pipe_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
                      "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width", "spin_slab_phase",
                      "spin_slab_measure"):
@@ -158,6 +161,14 @@ def spin_rng_fill(seed, tag, colour, extra, lattice_id, sweep, count, out, strea
 
 def spin_rng_probe(seed, threads, calls, out, stream=None):
     return _check(lib().spin_rng_probe(seed, threads, calls, _ptr(out), stream), "spin_rng_probe")
+
+
+def spin_pipe_probe(op, blocks_per_sm, iters, cycles, sink, stream=None):
+    """Launches the instruction-throughput probe; returns the SM count."""
+    sms = C.c_int32(0)
+    _check(lib().spin_pipe_probe(op, blocks_per_sm, iters, _ptr(cycles), _ptr(sink), C.byref(sms), stream),
+           "spin_pipe_probe")
+    return sms.value
 
 
 def _batch_items(items):

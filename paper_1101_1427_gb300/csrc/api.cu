@@ -369,6 +369,15 @@ int spin_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *ou
   return cuda_status(launch_rng_probe(seed, threads, calls, out, (cudaStream_t)stream));
 }
 
+int spin_pipe_probe(int op, int32_t blocks_per_sm, uint32_t iters, int64_t *clocks, uint32_t *sink,
+                    int32_t *sms, void *stream) {
+  if (op < SPIN_PIPE_MUL_WIDE || op > SPIN_PIPE_MUFU_RSQ || blocks_per_sm < 1 || blocks_per_sm > 8 || !clocks ||
+      !sink)
+    return SPIN_EINVAL;
+  return launch_pipe_probe(op, blocks_per_sm, iters, reinterpret_cast<long long *>(clocks), sink, sms,
+                           (cudaStream_t)stream);
+}
+
 int spin_sync(spin_lattice *h) {
   if (!h) return SPIN_EINVAL;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SPIN_ECUDA;

@@ -80,6 +80,10 @@ cudaError_t launch_rng_fill(uint64_t seed, uint32_t w, uint32_t lattice_id, uint
 cudaError_t launch_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, uint32_t *out,
                              cudaStream_t s);
 
+// probe.cu (returns a SPIN_* status)
+int launch_pipe_probe(int op, int blocks_per_sm, uint32_t iters, long long *clocks, uint32_t *sink,
+                      int *sms, cudaStream_t s);
+
 // dcb.cu
 bool dcb_supported(const spin_lattice *h, int tile);
 cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps);

@@ -82,6 +82,39 @@ def test_ea_L16_full_size_batched_sampled_realisations():
         assert np.array_equal(Q[:, :, r].cpu().numpy(), Qs), r
 
 
+def test_ea_L16_full_size_long_run_first_and_last_group():
+    """3D EA L=16, 1024 realisations x 32 slots x 2 sets, exchange and
+    measurement every sweep for 2000 sweeps in one batched launch: one
+    realisation of the first and one of the last group of 32 equal their
+    oracle runs (lattices, energy and overlap series every sweep)."""
+    from concurrent.futures import ThreadPoolExecutor
+    L, seed, n = 16, 9, 2000
+    betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
+
+    def oracle_run(r):
+        J = oracle.ea_couplings(3, L, r, seed)
+        s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t), bit=r & 31)
+                                for t in range(32)]) for a in range(2)]).copy()
+        Es, Qs, _, _ = oracle.pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J)
+        return s, Es, Qs
+
+    reals = (5, 31 * 32 + 26)
+    with ThreadPoolExecutor(len(reals)) as ex:  # the oracle's C calls run while the GPU works
+        futs = [ex.submit(oracle_run, r) for r in reals]
+        lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=seed)
+        ser = lat.series_buffers(n)
+        sp.batch_run([lat.batch_item(betas, ser)], n, 1, 1)
+        lat.sync()
+        got = lat.unpack()
+        E = ser["E"].view(n, 2, 32, 1024)
+        Q = ser["Q"].view(n, 32, 1024)
+        for r, f in zip(reals, futs):
+            s, Es, Qs = f.result()
+            assert np.array_equal(got[:, :, r].cpu().numpy(), s), r
+            assert np.array_equal(E[:, :, :, r].cpu().numpy(), Es), r
+            assert np.array_equal(Q[:, :, r].cpu().numpy(), Qs), r
+
+
 @pytest.mark.parametrize("variant", [0, 2])
 def test_heis_L128_one_sweep_full_lattice(variant):
     """3D Heisenberg L=128 (2M sites): one sweep from a common FP32 start,

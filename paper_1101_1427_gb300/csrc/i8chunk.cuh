@@ -16,18 +16,22 @@ __device__ __forceinline__ uint64_t ising_chunk(uint64_t C, uint64_t Uw, uint64_
                                                 const uint4 &r, int p, uint32_t thr4, uint32_t thr8,
                                                 long long &anti, long long &down) {
   // the four sites (bytes p, p+2, p+4, p+6) and each of their neighbours,
-  // gathered into one 32-bit word apiece
+  // gathered into one 32-bit word apiece.  The horizontal neighbours of the
+  // sites are the chunk's other-colour bytes O (right neighbours for p = 0,
+  // left ones for p = 1) and the same bytes shifted by one site with the
+  // byte beyond the chunk moved in (lb for p = 0, rb for p = 1); the count
+  // below does not depend on which of the two is left and which is right.
+  const uint32_t lo = (uint32_t)C, hi = (uint32_t)(C >> 32);
   const uint32_t sel = p ? 0x7531u : 0x6420u;
-  const uint64_t Lw = (C << 8) | lb, Rw = (C >> 8) | (rb << 56);  // left / right neighbour of every byte
-  const uint32_t S = __byte_perm((uint32_t)C, (uint32_t)(C >> 32), sel);
+  const uint32_t S = __byte_perm(lo, hi, sel);
+  const uint32_t O = __byte_perm(lo, hi, p ? 0x6420u : 0x7531u);
+  const uint32_t E = __byte_perm(O, (uint32_t)(p ? rb : lb), p ? 0x4321u : 0x2104u);
   const uint32_t Un = __byte_perm((uint32_t)Uw, (uint32_t)(Uw >> 32), sel);
   const uint32_t Dn = __byte_perm((uint32_t)Dw, (uint32_t)(Dw >> 32), sel);
-  const uint32_t Ln = __byte_perm((uint32_t)Lw, (uint32_t)(Lw >> 32), sel);
-  const uint32_t Rn = __byte_perm((uint32_t)Rw, (uint32_t)(Rw >> 32), sel);
   // per site: 2n, n the number of antiparallel neighbours (bit 1 of a +-1
   // byte is set for -1, so (a ^ b) & 2 is 2 iff a != b); dE = 8 - 4n
   const uint32_t M = 0x02020202u;
-  const uint32_t A = ((S ^ Un) & M) + ((S ^ Dn) & M) + ((S ^ Ln) & M) + ((S ^ Rn) & M);
+  const uint32_t A = ((S ^ Un) & M) + ((S ^ Dn) & M) + ((S ^ O) & M) + ((S ^ E) & M);
   // n >= 2 (dE <= 0) flips; n = 1 flips iff r < thr4, n = 0 iff r < thr8
   uint32_t f = ((A | (A >> 1)) >> 2) & 0x01010101u;
   const uint32_t t0 = (A & 0x2u) ? thr4 : thr8, t1 = (A & 0x200u) ? thr4 : thr8;

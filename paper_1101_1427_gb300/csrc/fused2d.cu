@@ -141,12 +141,16 @@ __global__ void __launch_bounds__(1024, 1)
 bool fused2d_supported(int L) { return L % 16 == 0 && L >= 32 && L <= 16384; }
 
 int fused2d_strip_height(int L, int n_lat) {
-  int dev = 0, sms = 148;
+  int dev = 0, sms = 148, occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // one resident CTA per SM and a single wave: at most sms CTAs in total,
-  // rows split evenly over a lattice's CTAs
-  int64_t ctas_per_lat = sms / n_lat;
+  // a single wave of resident CTAs (one per SM for L = 16384, several of
+  // the smaller CTAs of smaller lattices), rows split evenly over a
+  // lattice's CTAs
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused2d_kernel, L / 16, 3 * (size_t)L) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  int64_t ctas_per_lat = (int64_t)sms * occ / n_lat;
   if (ctas_per_lat < 1) ctas_per_lat = 1;
   int H = (int)((L + ctas_per_lat - 1) / ctas_per_lat);
   if (H < 8) H = 8;

@@ -110,6 +110,23 @@ def test_fused_equals_phases_on_large_lattice():
     assert torch.equal(a.spins, b.spins)
 
 
+def test_fused_many_lattices_short_strips():
+    """20 int8 lattices of L = 2048 (the tempering benchmark's shape): the
+    fused sweep splits each lattice into many short strips (a ragged last
+    one included); sampled lattices equal the oracle."""
+    L, seed, n = 2048, 71, 3
+    betas = list(np.linspace(0.1, 0.15, 20))
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=20, seed=seed)
+    lat.set_variant(1)
+    lat.sweep(betas, n)
+    got = host(lat.spins).reshape(20, -1)
+    for t in (0, 19):
+        lid = oracle.lattice_id(0, 0, t)
+        s = oracle.ising_init(2, L, seed, lid)
+        oracle.ising_run(2, L, s, betas[t], seed, lid, 0, n, series=False)
+        assert np.array_equal(got[t], s), t
+
+
 # ------------------------------------------------------------------ EA
 def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None, width=32):
     """Oracle runs of single realisations; `width` realisations share each

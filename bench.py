@@ -164,7 +164,8 @@ def side_configs(torch, sp, B, stream):
     the headline): 3D Heisenberg L=128 (FP32), and 3D EA L=16 with 1024
     realisations x 32 slots x 2 sets, exchange and measurement every sweep,
     in the per-handle multi-launch form and in the batched persistent form;
-    then the uneven batch in both forms."""
+    then the uneven batch in both forms, the 2D tempering benchmark, the
+    double checkerboard and the 3D ferromagnet."""
     import numpy as np
     out = {}
     lat = sp.Lattice(B.SPIN_HEISENBERG, 3, 128, B.SPIN_F32X4, seed=11)
@@ -223,6 +224,24 @@ def side_configs(torch, sp, B, stream):
     out.update(uneven_batch(torch, sp, B, stream))
     out.update(ising_pt(torch, sp, B, stream))
     out.update(dcb(torch, sp, B, stream))
+    out.update(ising3d(torch, sp, B, stream))
+    return out
+
+
+def ising3d(torch, sp, B, stream):
+    """3D Ising ferromagnet (Sec. 4): one int8 lattice of L = 512 (2^27 sites,
+    larger than L2) at the critical coupling, plain red-black sweeps."""
+    out = {}
+    L, n = 512, 10
+    lat = sp.Lattice(B.SPIN_ISING, 3, L, B.SPIN_I8, seed=31)
+    B.spin_sweep(lat.h, None, [0.2216544], 2, lat.seed)
+    a, b = _events(torch)
+    a.record(stream)
+    B.spin_sweep(lat.h, None, [0.2216544], n, lat.seed)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["ising3d_L512_i8_flips_per_ns"] = n * L ** 3 / (a.elapsed_time(b) * 1e6)
+    lat.close()
     return out
 
 
@@ -561,6 +580,9 @@ def run_case(name):
             B.spin_batch_run(item, 4, 1, 1, stream.cuda_stream)
             b.record(stream)
             flips = 4 * 2 ** 28
+    elif name == "ising3d":
+        print(json.dumps({"case": name, **ising3d(torch, sp, B, stream)}), flush=True)
+        return
     elif name == "dcb":
         print(json.dumps({"case": name, **dcb(torch, sp, B, stream)}), flush=True)
         return
@@ -603,7 +625,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, pipes, uneven, ising_pt, dcb)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, pipes, uneven, ising_pt, dcb, ising3d)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(256) dcb_tile_kernel(int8_t *__restrict__ spin
       sw[q] = *reinterpret_cast<const uint64_t *>(base + (int64_t)gy * L + gx);
     }
   __syncthreads();
-  const int slot = slot_of(g, lat);
+  const uint32_t slot = slot_of32(g, (uint32_t)lat);
   const uint32_t thr4 = __ldg(thr + 4 * slot + 1), thr8 = __ldg(thr + 4 * slot + 2);
-  const uint32_t lid = lattice_id_of(g, lat);
+  const uint32_t lid = lattice_id32(g, (uint32_t)lat);
   const uint32_t row_chunks = (uint32_t)L >> 3;
   long long unused_a = 0, unused_d = 0;
   // a thread keeps the same kPer chunks for all hits, and only the sweep

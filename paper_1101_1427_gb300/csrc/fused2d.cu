@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(1024, 1)
   const int64_t LL = (int64_t)L * L;
   const int8_t *a = A + lat * LL;
   int8_t *b = B + lat * LL;
-  const int t = slot_of(g, lat);
+  const uint32_t t = slot_of32(g, (uint32_t)lat);
   const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
-  const uint32_t lid = lattice_id_of(g, lat);
+  const uint32_t lid = lattice_id32(g, (uint32_t)lat);
   const uint32_t cpr = (uint32_t)(L >> 3);  // chunks per row
   const int x0 = 16 * tid;
   const int xl = x0 == 0 ? L - 1 : x0 - 1;

@@ -51,4 +51,41 @@ __device__ __forceinline__ uint64_t ising_chunk(uint64_t C, uint64_t Uw, uint64_
   return C ^ (((uint64_t)fhi << 32) | flo);
 }
 
+// One chunk of 8 sites of a row of a 3D int8 (+-1) ferromagnet, as
+// ising_chunk with two further neighbour words in z (Fw: plane z - 1, Bw:
+// plane z + 1) and the one byte beyond the chunk the phase needs (the byte
+// left of byte 0 for p = 0, right of byte 7 for p = 1).  n antiparallel
+// neighbours of six, dE = 12 - 4n: n >= 3 flips; n = 2, 1, 0 flip iff
+// r < thr4, thr8, thr12.
+__device__ __forceinline__ uint64_t ising3d_chunk(uint64_t C, uint64_t Uw, uint64_t Dw, uint64_t Fw,
+                                                  uint64_t Bw, uint32_t edge, const uint4 &r, int p,
+                                                  uint32_t thr4, uint32_t thr8, uint32_t thr12) {
+  const uint32_t lo = (uint32_t)C, hi = (uint32_t)(C >> 32);
+  const uint32_t sel = p ? 0x7531u : 0x6420u;
+  const uint32_t S = __byte_perm(lo, hi, sel);
+  const uint32_t O = __byte_perm(lo, hi, p ? 0x6420u : 0x7531u);
+  const uint32_t E = __byte_perm(O, edge, p ? 0x4321u : 0x2104u);
+  const uint32_t Un = __byte_perm((uint32_t)Uw, (uint32_t)(Uw >> 32), sel);
+  const uint32_t Dn = __byte_perm((uint32_t)Dw, (uint32_t)(Dw >> 32), sel);
+  const uint32_t Fn = __byte_perm((uint32_t)Fw, (uint32_t)(Fw >> 32), sel);
+  const uint32_t Bn = __byte_perm((uint32_t)Bw, (uint32_t)(Bw >> 32), sel);
+  // per site 2n in 0..12 (six terms of 0 or 2 per byte, no carries)
+  const uint32_t M = 0x02020202u;
+  const uint32_t A = ((S ^ Un) & M) + ((S ^ Dn) & M) + ((S ^ Fn) & M) + ((S ^ Bn) & M) + ((S ^ O) & M) +
+                     ((S ^ E) & M);
+  // n >= 3 <=> 2n >= 6 <=> bit 3 set, or bits 2 and 1 both set
+  uint32_t f = ((A >> 3) | ((A >> 2) & (A >> 1))) & 0x01010101u;
+  // below that, 2n = 4 (bit 2) takes thr4, 2n = 2 (bit 1) thr8, 2n = 0 thr12
+  const uint32_t t0 = (A & 0x4u) ? thr4 : ((A & 0x2u) ? thr8 : thr12);
+  const uint32_t t1 = (A & 0x400u) ? thr4 : ((A & 0x200u) ? thr8 : thr12);
+  const uint32_t t2 = (A & 0x40000u) ? thr4 : ((A & 0x20000u) ? thr8 : thr12);
+  const uint32_t t3 = (A & 0x4000000u) ? thr4 : ((A & 0x2000000u) ? thr8 : thr12);
+  f |= (r.x < t0 ? 0x1u : 0u) | (r.y < t1 ? 0x100u : 0u) | (r.z < t2 ? 0x10000u : 0u) |
+       (r.w < t3 ? 0x1000000u : 0u);
+  const uint32_t F = f * 0xFEu;
+  const uint32_t flo = __byte_perm(F, 0u, p ? 0x1404u : 0x4140u);
+  const uint32_t fhi = __byte_perm(F, 0u, p ? 0x3424u : 0x4342u);
+  return C ^ (((uint64_t)fhi << 32) | flo);
+}
+
 }  // namespace spin

@@ -68,16 +68,65 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
   const uint64_t C = row[m];
   const uint64_t U = reinterpret_cast<const uint64_t *>(base + (int64_t)yu * L)[m];
   const uint64_t D = reinterpret_cast<const uint64_t *>(base + (int64_t)yd * L)[m];
-  const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
-  const uint64_t lb = (uint8_t)base[(int64_t)y * L + xl];
-  const uint64_t rb = (uint8_t)base[(int64_t)y * L + xr];
-  const int t = slot_of(g, lat);
+  // only the byte beyond the chunk on the side the phase needs is read
+  const int p = (colour + y) & 1;
+  const int xe = p ? (m == chunks - 1 ? 0 : 8 * m + 8) : (m == 0 ? L - 1 : 8 * m - 1);
+  const uint64_t lb = (uint8_t)base[(int64_t)y * L + xe], rb = lb;
+  const uint32_t t = slot_of32(g, (uint32_t)lat);
   const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
   const uint32_t j4 = (uint32_t)y * (uint32_t)chunks + (uint32_t)m;
-  const uint4 r = philox(make_uint4(j4, sweep, lattice_id_of(g, lat), ctr_w(TAG_UPDATE, colour, 0)), rk);
+  const uint4 r = philox(make_uint4(j4, sweep, lattice_id32(g, (uint32_t)lat), ctr_w(TAG_UPDATE, colour, 0)), rk);
   long long unused_a = 0, unused_d = 0;
   reinterpret_cast<uint64_t *>(base + (int64_t)y * L)[m] =
-      ising_chunk<0>(C, U, D, lb, rb, r, (colour + y) & 1, thr4, thr8, unused_a, unused_d);
+      ising_chunk<0>(C, U, D, lb, rb, r, p, thr4, thr8, unused_a, unused_d);
+}
+
+// ---------------------------------------------------------------- 3D phase, L % 8 == 0
+// The 3D form of the 2D phase kernel: a thread owns the eight bytes
+// x = 8m .. 8m+7 of row y in the planes z0 .. z0+zlen-1 and marches down z.
+// The four active sites of a chunk have colour indices
+// (z L^2 + y L + 8m) / 2 + q, q < 4, and share one Philox call
+// (j4 = (z L^2 + y L) / 8 + m); the update is ising3d_chunk.  A site's
+// neighbours are of the other colour, which the phase does not change, so
+// the word of plane z - 1 kept from the previous step (before its update)
+// serves as the lower neighbour and the word of plane z + 1 is loaded once
+// for two steps.  A CTA takes blockDim.x chunks of blockDim.y rows; grid =
+// (tiles of a plane, plane segments, lattices).
+__global__ void __launch_bounds__(256) ising3d_phase_kernel(int8_t *__restrict__ spins, int L, int tiles_x,
+                                                            int zlen, const uint32_t *__restrict__ thr, Geom g,
+                                                            RoundKeys rk, uint32_t sweep, int colour) {
+  const int chunks = L >> 3;
+  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
+  const int m = tile_x * blockDim.x + threadIdx.x;
+  const int y = tile_y * blockDim.y + threadIdx.y;
+  const int z0 = blockIdx.y * zlen;
+  const uint32_t lat = blockIdx.z;
+  if (m >= chunks || y >= L || z0 >= L) return;
+  const int z1 = min(z0 + zlen, L);
+  const int64_t LL = (int64_t)L * L;
+  int8_t *base = spins + (int64_t)lat * LL * L;
+  uint64_t *col = reinterpret_cast<uint64_t *>(base + (int64_t)y * L) + m;  // word (z = 0, y, m)
+  const int64_t zs = LL >> 3;                                               // words per plane
+  const int64_t du = (int64_t)((y == 0 ? L - 1 : y - 1) - y) * (L >> 3);     // to row y - 1
+  const int64_t dd = (int64_t)((y == L - 1 ? 0 : y + 1) - y) * (L >> 3);     // to row y + 1
+  const uint32_t t = slot_of32(g, lat);
+  const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2), thr12 = __ldg(thr + 4 * t + 3);
+  const uint32_t lid = lattice_id32(g, lat), wctr = ctr_w(TAG_UPDATE, colour, 0);
+  const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
+  uint64_t F = col[(int64_t)(z0 == 0 ? L - 1 : z0 - 1) * zs];
+  uint64_t C = col[(int64_t)z0 * zs];
+  for (int z = z0; z < z1; ++z) {
+    uint64_t *cz = col + (int64_t)z * zs;
+    const uint64_t Bk = col[(int64_t)(z == L - 1 ? 0 : z + 1) * zs];
+    const uint64_t U = cz[du], D = cz[dd];
+    const int p = (colour + y + z) & 1;
+    const uint32_t edge = (uint8_t)base[(int64_t)z * LL + (int64_t)y * L + (p ? xr : xl)];
+    const uint32_t j4 = (uint32_t)(((int64_t)z * LL + (int64_t)y * L) >> 3) + (uint32_t)m;
+    const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
+    *cz = ising3d_chunk(C, U, D, F, Bk, edge, r, p, thr4, thr8, thr12);
+    F = C;
+    C = Bk;
+  }
 }
 
 // ---------------------------------------------------------------- generic phase
@@ -158,6 +207,7 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
   const bool fast2d = g.dim == 2 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
+  const bool fast3d = g.dim == 3 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   if (fast2d && h->variant == 1 && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
@@ -168,6 +218,16 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
         const int by = 256 / bx;
         dim3 block(bx, by), grid((chunks + bx - 1) / bx, (g.L + by - 1) / by, (unsigned)h->n_lat);
         ising2d_phase_kernel<<<grid, block, 0, h->stream>>>((int8_t *)h->spins, g.L, h->d_thr, g,
+                                                             rk, sweep, colour);
+      } else if (fast3d) {
+        const int chunks = g.L / 8;
+        const int bx = chunks < 64 ? chunks : 64;
+        const int by = 256 / bx;
+        const int tiles_x = (chunks + bx - 1) / bx, tiles_y = (g.L + by - 1) / by;
+        const int zlen = g.L < 16 ? g.L : 16;
+        dim3 block(bx, by), grid((unsigned)(tiles_x * tiles_y), (unsigned)((g.L + zlen - 1) / zlen),
+                                 (unsigned)h->n_lat);
+        ising3d_phase_kernel<<<grid, block, 0, h->stream>>>((int8_t *)h->spins, g.L, tiles_x, zlen, h->d_thr, g,
                                                              rk, sweep, colour);
       } else {
         const uint32_t total = (uint32_t)(h->n_lat * ((g.N / 2 + 3) / 4));

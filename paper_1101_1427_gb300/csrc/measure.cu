@@ -343,7 +343,7 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
 __global__ void pt_swap_bytes_kernel(uint8_t *__restrict__ s, const uint8_t *__restrict__ decision,
                                      Geom g, int parity, int64_t lat_bytes) {
   const int64_t lat0 = blockIdx.y;
-  const int t = slot_of(g, lat0);
+  const int t = (int)slot_of32(g, (uint32_t)lat0);
   if (((t - parity) & 1) || t + 1 >= g.n_temps || !decision[lat0]) return;
   uint8_t *b0 = s + lat0 * lat_bytes, *b1 = s + (lat0 + g.n_real) * lat_bytes;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;

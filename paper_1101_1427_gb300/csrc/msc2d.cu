@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__
   // 32 b + l (rows are consecutive in the colour index)
   const uint32_t per_lat = (uint32_t)m.L * (uint32_t)m.bpr;
   const uint32_t lat = first / per_lat;
-  const uint32_t lid = lattice_id_of(g, lat);
-  const int t = slot_of(g, lat);
+  const uint32_t lid = lattice_id32(g, lat);
+  const uint32_t t = slot_of32(g, lat);
   const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
   uint32_t j4 = 32u * (first - lat * per_lat) + (uint32_t)lane;

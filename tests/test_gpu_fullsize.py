@@ -58,6 +58,23 @@ def test_ising2d_L16384_energy_consistent_with_state():
     assert torch.equal(E, E2.to(torch.int64)) and torch.equal(M, s.sum((1, 2)).to(torch.int64))
 
 
+def test_ising3d_L128_full_lattice():
+    """3D Ising ferromagnet L = 128 (2^21 int8 sites) at the critical
+    coupling, three sweeps by the 3D chunk kernel: the whole lattice equals
+    the oracle, and E, M agree with the state."""
+    L, seed, beta, n = 128, 17, 0.2216, 3
+    lat = sp.Lattice(B.SPIN_ISING, 3, L, B.SPIN_I8, seed=seed)
+    lat.sweep([beta], n)
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(3, L, seed, lid)
+    oracle.ising_run(3, L, s, beta, seed, lid, 0, n, series=False)
+    assert np.array_equal(lat.spins.cpu().numpy(), s)
+    E, M, _ = lat.measure()
+    v = lat.spins.view(L, L, L).to(torch.int32)
+    E2 = -sum((v * torch.roll(v, -1, d)).sum() for d in range(3))
+    assert int(E[0]) == int(E2) and int(M[0]) == int(v.sum())
+
+
 def test_ea_L16_full_size_batched_sampled_realisations():
     """3D EA L=16, 1024 realisations x 32 slots x 2 sets, exchange and
     measurement every sweep, in the batched persistent launch: sampled

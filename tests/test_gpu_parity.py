@@ -83,8 +83,10 @@ def test_ising2d_L64_1000_sweeps_bit_exact(variant):
     (2, 24, [0.5], 1, 0),             # 2D kernel, L % 16 != 0
     (2, 48, [0.4, 0.45, 0.9], 2, 1),  # fused kernel, several lattices, ragged strips
     (2, 32, [0.0, 5.0], 1, 1),        # infinite and (near) zero temperature
-    (3, 8, [0.22, 0.3], 1, 0),
-    (3, 12, [0.25], 2, 0)])
+    (3, 8, [0.22, 0.3], 1, 0),        # 3D chunk kernel, one chunk per row
+    (3, 16, [0.0, 0.2216, 50.0], 2, 0),  # 3D chunk kernel, degenerate temperatures
+    (3, 24, [0.25], 1, 0),            # 3D chunk kernel, odd number of chunks per row
+    (3, 12, [0.25], 2, 0)])           # generic kernel (L % 8 != 0)
 def test_ising_sweeps_bit_exact(dim, L, betas, n_real, variant):
     seed, n = 5, 13
     lat = sp.Lattice(B.SPIN_ISING, dim, L, B.SPIN_I8, n_real=n_real, n_temps=len(betas), seed=seed)

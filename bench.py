@@ -51,8 +51,8 @@ WIDE_MULS_PER_CLK_PER_SM = 32
 # (mean of two launches captured with ncu, summarised in profiles/), valid
 # while the kernel's sources hash to KERNEL_TRAFFIC_SRC_SHA; otherwise
 # reported as null.
-KERNEL_TRAFFIC_BYTES = (100_707_072 + 11_609_600 + 100_768_000 + 7_934_720) // 2
-KERNEL_TRAFFIC_SRC_SHA = "2823b2d568303345"
+KERNEL_TRAFFIC_BYTES = (100_703_488 + 10_839_040 + 100_700_928 + 7_587_840) // 2
+KERNEL_TRAFFIC_SRC_SHA = "aaa05b638e656a0b"
 
 
 def kernel_sha():

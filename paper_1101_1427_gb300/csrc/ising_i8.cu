@@ -114,18 +114,26 @@ __global__ void __launch_bounds__(256) ising3d_phase_kernel(int8_t *__restrict__
   const uint32_t lid = lattice_id32(g, lat), wctr = ctr_w(TAG_UPDATE, colour, 0);
   const int xl = m == 0 ? L - 1 : 8 * m - 1, xr = m == chunks - 1 ? 0 : 8 * m + 8;
   uint64_t F = col[(int64_t)(z0 == 0 ? L - 1 : z0 - 1) * zs];
-  uint64_t C = col[(int64_t)z0 * zs];
+  uint64_t *cz = col + (int64_t)z0 * zs;
+  uint64_t C = *cz;
+  // per step: the chunk moves one plane (zs words, L^2 bytes), its Philox
+  // counter by L^2 / 8 and the active parity flips
+  const uint8_t *row = reinterpret_cast<const uint8_t *>(base) + (int64_t)z0 * LL + (int64_t)y * L;
+  uint32_t j4 = ((uint32_t)z0 * (uint32_t)L + (uint32_t)y) * (uint32_t)chunks + (uint32_t)m;
+  const uint32_t dj = (uint32_t)L * (uint32_t)chunks;
+  int p = (colour + y + z0) & 1;
   for (int z = z0; z < z1; ++z) {
-    uint64_t *cz = col + (int64_t)z * zs;
-    const uint64_t Bk = col[(int64_t)(z == L - 1 ? 0 : z + 1) * zs];
+    const uint64_t Bk = z == L - 1 ? col[0] : cz[zs];
     const uint64_t U = cz[du], D = cz[dd];
-    const int p = (colour + y + z) & 1;
-    const uint32_t edge = (uint8_t)base[(int64_t)z * LL + (int64_t)y * L + (p ? xr : xl)];
-    const uint32_t j4 = (uint32_t)(((int64_t)z * LL + (int64_t)y * L) >> 3) + (uint32_t)m;
+    const uint32_t edge = row[p ? xr : xl];
     const uint4 r = philox(make_uint4(j4, sweep, lid, wctr), rk);
     *cz = ising3d_chunk(C, U, D, F, Bk, edge, r, p, thr4, thr8, thr12);
     F = C;
     C = Bk;
+    cz += zs;
+    row += LL;
+    j4 += dj;
+    p ^= 1;
   }
 }
 

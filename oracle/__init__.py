@@ -61,6 +61,7 @@ def lib():
         L.or_ising_window_sweeps.argtypes = [i32, i32, p, i32, p, dbl, u64, u32, u32, i32]
         L.or_ising_init_sites.argtypes = [i64, p, p, u64, u32, i32]
         L.or_dcb_sweeps.argtypes = [i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
+        L.or_dcb_sweeps_dim.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
         L.or_ising_slab_phase.argtypes = [i32, i32, i32, p, dbl, u64, u32, u32, i32, p]
         _lib = L
     return _lib
@@ -169,12 +170,17 @@ def pt_run(dim, L, spins, betas, seed, r, rkey, first_sweep, n_sweeps, pt_every,
     return E, Q, acc, int(step[0])
 
 
-def dcb_sweeps(L, s, beta, seed, lid, first_sweep, n_sweeps, T, k, symmetric=False, J=None):
-    """Double checkerboard multi-hit sweeps of a 2D int8 lattice in place
-    (n_sweeps updates per site, a multiple of k); returns the flip count."""
+def dcb_sweeps(L, s, beta, seed, lid, first_sweep, n_sweeps, T, k, symmetric=False, J=None, dim=2):
+    """Double checkerboard multi-hit sweeps of a 2D or 3D int8 lattice in
+    place (n_sweeps updates per site, a multiple of k); returns the flip
+    count."""
     flips = np.zeros(1, np.int64)
-    lib().or_dcb_sweeps(L, _ptr(s), _ptr(J), beta, seed, lid, first_sweep, n_sweeps, T, k,
-                        int(bool(symmetric)), _ptr(flips))
+    if dim == 2:
+        lib().or_dcb_sweeps(L, _ptr(s), _ptr(J), beta, seed, lid, first_sweep, n_sweeps, T, k,
+                            int(bool(symmetric)), _ptr(flips))
+    else:
+        lib().or_dcb_sweeps_dim(dim, L, _ptr(s), _ptr(J), beta, seed, lid, first_sweep, n_sweeps, T, k,
+                                int(bool(symmetric)), _ptr(flips))
     return int(flips[0])
 
 

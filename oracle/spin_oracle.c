@@ -280,25 +280,27 @@ void or_ising_slab_phase(int L, int y0, int rows, int8_t *slab, double beta, uin
   }
 }
 
-/* Double checkerboard order with multi-hit updates (Sec. 3.2 and 3.4), 2D.
- * The L x L lattice is cut into T x T tiles; tile (x / T, y / T) has the
- * coarse colour (x / T + y / T) mod 2.  A compound move takes the tiles of
- * one coarse colour through k hits, each hit updating the fine colour-0
- * sites of those tiles and then their fine colour-1 sites, and then treats
- * the tiles of the other coarse colour the same way.  Coarse colour 0 goes
- * first; with `symmetric`, odd compound moves (counted from the start of
- * the chain) take coarse colour 1 first, so the moves alternate A^k B^k and
- * B^k A^k.  Hit h of compound move m draws its words with sweep number
- * m k + h, so every site is updated k times per compound move and n_sweeps
- * (a multiple of k) counts those updates; first_sweep is a multiple of k.
- * T must divide L with L / T even; any order within one fine-colour step is
- * equivalent, since its sites are not neighbours. */
-void or_dcb_sweeps(int L, int8_t *s, const int8_t *J, double beta, uint64_t seed,
-                   uint32_t lattice_id, uint32_t first_sweep, int64_t n_sweeps, int T, int k,
-                   int symmetric, int64_t *flips) {
-  const int64_t n = (int64_t)L * L;
-  uint32_t thr[3] = {0, 0, 0};
-  for (int m = 1; m <= 2; ++m) thr[m] = or_metropolis_threshold(beta, 4 * m);
+/* Double checkerboard order with multi-hit updates (Sec. 3.2 and 3.4; in
+ * three dimensions, Sec. 4, the tiles are T x T x T cubes).  The lattice is
+ * cut into tiles of edge T; tile (x / T, y / T[, z / T]) has the coarse
+ * colour (x / T + y / T [+ z / T]) mod 2.  A compound move takes the tiles
+ * of one coarse colour through k hits, each hit updating the fine colour-0
+ * sites of those tiles (fine colour = the site's colour (x + y [+ z]) mod 2)
+ * and then their fine colour-1 sites, and then treats the tiles of the other
+ * coarse colour the same way.  Coarse colour 0 goes first; with `symmetric`,
+ * odd compound moves (counted from the start of the chain) take coarse
+ * colour 1 first, so the moves alternate A^k B^k and B^k A^k.  Hit h of
+ * compound move m draws its words with sweep number m k + h, so every site
+ * is updated k times per compound move and n_sweeps (a multiple of k) counts
+ * those updates; first_sweep is a multiple of k.  T must divide L with L / T
+ * even; any order within one fine-colour step is equivalent, since its
+ * sites are not neighbours. */
+void or_dcb_sweeps_dim(int dim, int L, int8_t *s, const int8_t *J, double beta, uint64_t seed,
+                       uint32_t lattice_id, uint32_t first_sweep, int64_t n_sweeps, int T, int k,
+                       int symmetric, int64_t *flips) {
+  const int64_t n = or_nsites(dim, L);
+  uint32_t thr[4] = {0, 0, 0, 0};
+  for (int m = 1; m <= dim; ++m) thr[m] = or_metropolis_threshold(beta, 4 * m);
   for (int64_t mv = 0; mv < n_sweeps / k; ++mv) {
     const uint32_t M = first_sweep / (uint32_t)k + (uint32_t)mv;
     const int first = (symmetric && (M & 1u)) ? 1 : 0;
@@ -308,10 +310,10 @@ void or_dcb_sweeps(int L, int8_t *s, const int8_t *J, double beta, uint64_t seed
         const uint32_t sweep = M * (uint32_t)k + (uint32_t)h;
         for (int colour = 0; colour < 2; ++colour) {
           for (int64_t i = 0; i < n; ++i) {
-            const int x = (int)(i % L), y = (int)(i / L);
-            if (((x / T + y / T) & 1) != coarse) continue;
-            if (or_colour(2, L, i) != colour) continue;
-            const int hf = or_local_field(2, L, s, J, i);
+            const int x = (int)(i % L), y = (int)((i / L) % L), z = dim == 3 ? (int)(i / ((int64_t)L * L)) : 0;
+            if (((x / T + y / T + z / T) & 1) != coarse) continue;
+            if (or_colour(dim, L, i) != colour) continue;
+            const int hf = or_local_field(dim, L, s, J, i);
             const int dE = 2 * s[i] * hf;
             int flip;
             if (dE <= 0) {
@@ -330,6 +332,13 @@ void or_dcb_sweeps(int L, int8_t *s, const int8_t *J, double beta, uint64_t seed
       }
     }
   }
+}
+
+/* The 2D form (kept for its callers). */
+void or_dcb_sweeps(int L, int8_t *s, const int8_t *J, double beta, uint64_t seed,
+                   uint32_t lattice_id, uint32_t first_sweep, int64_t n_sweeps, int T, int k,
+                   int symmetric, int64_t *flips) {
+  or_dcb_sweeps_dim(2, L, s, J, beta, seed, lattice_id, first_sweep, n_sweeps, T, k, symmetric, flips);
 }
 
 /* Energy E = -sum_<ij> J_ij s_i s_j (Eq. ising_hamiltonian with J = 1,

@@ -116,3 +116,141 @@ def test_long_run_matches_enumeration(k, symmetric):
     bf = exact.brute_force(2, L4, beta)
     e_mc, e_err = binned_mean(E[200:])
     assert_within(e_mc, e_err, bf["E"], what="<E>")
+
+
+# ------------------------------------------------------------------ 3D (Sec. 4: T x T x T tiles)
+def _nb3(L):
+    n = L ** 3
+    out = []
+    for i in range(n):
+        x, y, z = i % L, (i // L) % L, i // (L * L)
+        out.append([((x + 1) % L) + L * y + L * L * z, ((x - 1) % L) + L * y + L * L * z,
+                    x + L * ((y + 1) % L) + L * L * z, x + L * ((y - 1) % L) + L * L * z,
+                    x + L * y + L * L * ((z + 1) % L), x + L * y + L * L * ((z - 1) % L)])
+    return out
+
+
+def _sites3(L, T, coarse, colour):
+    out = []
+    for i in range(L ** 3):
+        x, y, z = i % L, (i // L) % L, i // (L * L)
+        if ((x // T + y // T + z // T) & 1) == coarse and ((x + y + z) & 1) == colour:
+            out.append(i)
+    return out
+
+
+@pytest.mark.parametrize("k,symmetric,compound,start", [(2, False, 0, "up"), (2, True, 1, "mixed"),
+                                                         (3, True, 2, "up")])
+def test_3d_one_compound_matches_exact_distribution(k, symmetric, compound, start):
+    """3D L = 2 (8 sites, 256 states; the periodic neighbours in each
+    direction coincide, so every site has each neighbour twice) with T = 1:
+    one compound move from a fixed start, sampled over 30000 seeds, against
+    the exact distribution propagated one single-site Metropolis kernel at a
+    time in the order of the compound move.  From the all-up start every
+    first update has dE = 12, so all three thresholds matter."""
+    L, T, beta = 2, 1, 0.15
+    n = L ** 3
+    s0 = np.ones(n, np.int8) if start == "up" else np.array([1, -1, -1, 1, 1, 1, -1, 1], np.int8)
+    states = np.arange(1 << n, dtype=np.int64)
+    spins = 1 - 2 * ((states[:, None] >> np.arange(n)) & 1)
+    nb = _nb3(L)
+    dist = np.zeros(1 << n)
+    dist[int(sum(1 << i for i in range(n) if s0[i] < 0))] = 1.0
+    first = 1 if (symmetric and compound % 2 == 1) else 0
+    for cc in range(2):
+        for _ in range(k):
+            for colour in range(2):
+                for i in _sites3(L, T, first ^ cc, colour):
+                    dE = 2 * spins[:, i] * spins[:, nb[i]].sum(axis=1)
+                    p = np.where(dE <= 0, 1.0, np.exp(-beta * dE.astype(np.float64)))
+                    moved = dist * p
+                    dist = dist * (1.0 - p) + moved[states ^ (1 << i)]
+    n_samp = 30000
+    hist = np.zeros(1 << n)
+    for seed in range(1, n_samp + 1):
+        s = s0.copy()
+        oracle.dcb_sweeps(L, s, beta, seed, 0, compound * k, k, T, k, symmetric, dim=3)
+        hist[int(sum(1 << i for i in range(n) if s[i] < 0))] += 1
+    chi2, dof = 0.0, 0
+    for st in range(1 << n):
+        e = dist[st] * n_samp
+        if e >= 20:
+            chi2 += (hist[st] - e) ** 2 / e
+            dof += 1
+    assert dof >= 10
+    assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
+    assert hist[dist * n_samp < 1e-9].sum() == 0  # no state the exact kernel cannot reach
+
+
+@pytest.mark.parametrize("T,k", [(2, 1), (4, 2), (2, 3)])
+def test_3d_infinite_temperature_flips_every_site_k_times(T, k):
+    L = 8
+    lid = oracle.lattice_id(0, 0, 0)
+    s0 = oracle.ising_init(3, L, 5, lid)
+    s = s0.copy()
+    flips = oracle.dcb_sweeps(L, s, 0.0, 5, lid, 0, 2 * k, T, k, True, dim=3)
+    assert flips == 2 * k * L ** 3 and np.array_equal(s, s0)
+    s = s0.copy()
+    oracle.dcb_sweeps(L, s, 0.0, 5, lid, 0, k, T, k, False, dim=3)
+    assert np.array_equal(s, s0 * (-1) ** k)
+
+
+@pytest.mark.parametrize("T,k,symmetric", [(2, 2, False), (4, 2, True), (2, 3, True)])
+def test_3d_zero_temperature_order_matches_numpy(T, k, symmetric):
+    """At beta = 50 every threshold is 0, so only dE <= 0 flips and the chain
+    is deterministic: it must equal a numpy implementation of the compound
+    move (tiles of one coarse colour, k hits of fine colour 0 then 1, then
+    the other coarse colour; whole fine-colour steps at once, as their sites
+    are not neighbours)."""
+    L = 8
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(3, L, 9, lid)
+    ref = s.reshape(L, L, L).astype(np.int64)  # [z][y][x]
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    coarse_of = ((x // T + y // T + z // T) & 1)
+    colour_of = (x + y + z) & 1
+    n_moves = 3
+    for m in range(n_moves):
+        first = 1 if (symmetric and m % 2 == 1) else 0
+        for cc in range(2):
+            for _ in range(k):
+                for colour in range(2):
+                    mask = (coarse_of == (first ^ cc)) & (colour_of == colour)
+                    h = sum(np.roll(ref, sh, ax) for ax in range(3) for sh in (1, -1))
+                    flip = mask & (2 * ref * h <= 0)
+                    ref = np.where(flip, -ref, ref)
+    oracle.dcb_sweeps(L, s, 50.0, 9, lid, 0, n_moves * k, T, k, symmetric, dim=3)
+    assert np.array_equal(s.reshape(L, L, L), ref)
+
+
+def test_3d_long_run_matches_enumeration():
+    """L = 2, T = 1: <E> over a long chain equals exact enumeration."""
+    beta, k = 0.3, 2
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(3, 2, 23, lid)
+    n = 40000
+    E = np.empty(n)
+    for m in range(n):
+        oracle.dcb_sweeps(2, s, beta, 23, lid, m * k, k, 1, k, True, dim=3)
+        E[m] = oracle.ising_energy(3, 2, s)
+    e_mc, e_err = binned_mean(E[200:])
+    assert_within(e_mc, e_err, exact.brute_force(3, 2, beta)["E"], what="<E>")
+
+
+def test_3d_long_run_matches_plain_sweeps():
+    """L = 4, T = 2 (eight 2^3 tiles): the double-checkerboard chain and the
+    plain red-black chain sample the same <E> (both stationary for the
+    Boltzmann distribution)."""
+    beta, k, L = 0.2, 2, 4
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.ising_init(3, L, 29, lid)
+    n = 30000
+    E = np.empty(n)
+    for m in range(n):
+        oracle.dcb_sweeps(L, s, beta, 29, lid, m * k, k, 2, k, False, dim=3)
+        E[m] = oracle.ising_energy(3, L, s)
+    s2 = oracle.ising_init(3, L, 31, lid)
+    E2, _, _ = oracle.ising_run(3, L, s2, beta, 31, lid, 0, 2 * n)
+    a, ea = binned_mean(E[200:])
+    b, eb = binned_mean(E2[400:])
+    assert abs(a - b) <= 4.5 * np.hypot(ea, eb), (a, ea, b, eb)

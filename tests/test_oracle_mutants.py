@@ -35,9 +35,15 @@ MUTANTS = {
     "dcb_fine_colour_order": ("for (int colour = 0; colour < 2; ++colour) {\n          for (int64_t i = 0; i < n; ++i) {\n            const int x",
                               "for (int colour = 1; colour >= 0; --colour) {\n          for (int64_t i = 0; i < n; ++i) {\n            const int x",
                               "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
-    "dcb_tile_colour": ("if (((x / T + y / T) & 1) != coarse) continue;",
-                        "if (((x % T + y / T) & 1) != coarse) continue;",
+    "dcb_tile_colour": ("if (((x / T + y / T + z / T) & 1) != coarse) continue;",
+                        "if (((x % T + y / T + z / T) & 1) != coarse) continue;",
                         "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
+    "dcb3_tile_colour_without_z": ("if (((x / T + y / T + z / T) & 1) != coarse) continue;",
+                                   "if (((x / T + y / T) & 1) != coarse) continue;",
+                                   "tests/test_oracle_dcb.py::test_3d_zero_temperature_order_matches_numpy"),
+    "dcb3_missing_threshold": ("const int64_t n = or_nsites(dim, L);\n  uint32_t thr[4] = {0, 0, 0, 0};\n  for (int m = 1; m <= dim; ++m)",
+                               "const int64_t n = or_nsites(dim, L);\n  uint32_t thr[4] = {0, 0, 0, 0};\n  for (int m = 1; m < dim; ++m)",
+                               "tests/test_oracle_dcb.py::test_3d_one_compound_matches_exact_distribution"),
     "dcb_hit_words": ("const uint32_t sweep = M * (uint32_t)k + (uint32_t)h;",
                       "const uint32_t sweep = M * (uint32_t)k;",
                       "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),

@@ -230,7 +230,8 @@ def side_configs(torch, sp, B, stream):
 
 def ising3d(torch, sp, B, stream):
     """3D Ising ferromagnet (Sec. 4): one int8 lattice of L = 512 (2^27 sites,
-    larger than L2) at the critical coupling, plain red-black sweeps."""
+    larger than L2) at the critical coupling, plain red-black sweeps and the
+    double checkerboard with cubic tiles (T = 8, 16) and k = 100 hits."""
     out = {}
     L, n = 512, 10
     lat = sp.Lattice(B.SPIN_ISING, 3, L, B.SPIN_I8, seed=31)
@@ -241,6 +242,17 @@ def ising3d(torch, sp, B, stream):
     b.record(stream)
     torch.cuda.synchronize()
     out["ising3d_L512_i8_flips_per_ns"] = n * L ** 3 / (a.elapsed_time(b) * 1e6)
+    # the paper's 3D GPU order: double checkerboard with 8^3 tiles, k = 100
+    for T, k in ((8, 100), (16, 100)):
+        lat.set_update_order(B.SPIN_ORDER_DCB, T, k)
+        lat.set_counters(0, 0)
+        B.spin_sweep(lat.h, None, [0.2216544], k, lat.seed)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, [0.2216544], k, lat.seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"ising3d_dcb_T{T}_k{k}_flips_per_ns"] = k * L ** 3 / (a.elapsed_time(b) * 1e6)
     lat.close()
     return out
 

@@ -352,9 +352,10 @@ int spin_set_msc_width(spin_lattice *lat, int32_t width);
  *                           that the moves alternate A^k B^k and B^k A^k,
  *                           the compound order of Sec. 3.4 that satisfies
  *                           detailed balance.
- * The double-checkerboard orders take 2D Ising ferromagnets in the int8
- * layout, tile in {8, 16, 32, 64, 128} dividing L with L / tile even, and
- * hits >= 1; spin_sweep then counts sweeps as updates per site and needs
+ * The double-checkerboard orders take Ising ferromagnets in the int8
+ * layout: 2D with tile in {8, 16, 32, 64, 128}, or 3D (Sec. 4: tile^3
+ * cubes, coarse colour (x / tile + y / tile + z / tile) mod 2) with tile in
+ * {8, 16}; tile divides L with L / tile even, and hits >= 1; spin_sweep then counts sweeps as updates per site and needs
  * n_sweeps and the handle's sweep count to be multiples of hits (so must
  * spin_run's measure_every and pt_every).  Such handles cannot join a
  * batched launch.  tile and hits are ignored for SPIN_ORDER_CHECKERBOARD. */

@@ -1,5 +1,5 @@
-// Double checkerboard with multi-hit updates for the 2D int8 ferromagnet
-// (Sec. 3.2 and 3.4).  The lattice is cut into T x T tiles coloured like a
+// Double checkerboard with multi-hit updates for the 2D and 3D int8
+// ferromagnet (Sec. 3.2 and 3.4; Sec. 4 for three dimensions).  The lattice is cut into T x T tiles coloured like a
 // checkerboard; one launch takes every tile of one coarse colour, loads it
 // with a one-site halo (from tiles of the other colour, which this launch
 // does not change) into shared memory, and gives it k hits there, each hit
@@ -108,11 +108,119 @@ cudaError_t launch_tiles(spin_lattice *h, int coarse, uint32_t sweep0) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- 3D
+// The same order in three dimensions (Sec. 4: cubic tiles of edge T, coarse
+// colour (x / T + y / T + z / T) mod 2).  Shared tile: (T + 2)^2 rows (z and
+// y from -1 to T, z slowest), each of T / 8 + 2 eight-byte words holding
+// x = -8 .. T + 7; only face neighbours are read, so the halo rows on the
+// tile's edges (loaded along with the rest) are never used.  A chunk's
+// active sites read only bytes of the other fine colour, which the current
+// fine-colour step does not change, so chunks are updated in place.
+template <int kT>
+__global__ void __launch_bounds__(256) dcb3_tile_kernel(int8_t *__restrict__ spins, int L, int coarse,
+                                                        uint32_t sweep0, int k,
+                                                        const uint32_t *__restrict__ thr, Geom g,
+                                                        RoundKeys rk) {
+  constexpr int kWords = kT / 8 + 2;          // words per shared row
+  constexpr int kSide = kT + 2;               // rows per shared plane
+  constexpr int kTileWords = kSide * kSide * kWords;
+  constexpr int kCpr = kT / 8;                // chunks per tile row
+  constexpr int kChunks = kT * kT * kCpr;     // chunks per tile
+  constexpr int kTPT = kChunks < 256 ? kChunks : 256;
+  constexpr int kTiles = 256 / kTPT;
+  constexpr int kPer = kChunks / kTPT;
+  __shared__ __align__(16) uint64_t smem[kTiles * kTileWords];
+  const int tsub = threadIdx.x / kTPT, tid = threadIdx.x - tsub * kTPT;
+  uint64_t *sw = smem + tsub * kTileWords;
+  const uint8_t *sb = reinterpret_cast<const uint8_t *>(sw);
+  const int B = L / kT, half = B >> 1;
+  const int64_t t = (int64_t)blockIdx.x * kTiles + tsub;
+  const bool active = t < (int64_t)B * B * half;  // the last CTA may hold fewer tiles
+  const int bxh = (int)(t % half);
+  const int64_t rest = t / half;
+  const int by = (int)(rest % B), bz = (int)(rest / B);
+  const int bx = 2 * bxh + ((by + bz + coarse) & 1);
+  const int64_t lat = blockIdx.y;
+  int8_t *base = spins + lat * (int64_t)L * L * L;
+  const int x0 = bx * kT, y0 = by * kT, z0 = bz * kT;
+  if (active)
+    for (int q = tid; q < kTileWords; q += kTPT) {
+      const int row = q / kWords, rw = q % kWords - 1;
+      const int ry = row % kSide - 1, rz = row / kSide - 1;
+      const int gy = (y0 + ry + L) % L, gz = (z0 + rz + L) % L, gx = (x0 + 8 * rw + L) % L;
+      sw[q] = *reinterpret_cast<const uint64_t *>(base + ((int64_t)gz * L + gy) * L + gx);
+    }
+  __syncthreads();
+  const uint32_t slot = slot_of32(g, (uint32_t)lat);
+  const uint32_t thr4 = __ldg(thr + 4 * slot + 1), thr8 = __ldg(thr + 4 * slot + 2),
+                 thr12 = __ldg(thr + 4 * slot + 3);
+  const uint32_t lid = lattice_id32(g, (uint32_t)lat);
+  const uint32_t row_chunks = (uint32_t)L >> 3;
+  // a thread keeps the same kPer chunks for all hits: the sweep-independent
+  // part of the first Philox rounds is computed once (PhiloxX1)
+  PhiloxX1 pre[kPer][2];
+  if (active)
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int q = tid + i * kTPT;
+      const int m = q % kCpr, ty = (q / kCpr) % kT, tz = q / (kCpr * kT);
+      const uint32_t gchunk =
+          ((uint32_t)(z0 + tz) * (uint32_t)L + (uint32_t)(y0 + ty)) * row_chunks + (uint32_t)(x0 >> 3) + (uint32_t)m;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) pre[i][c] = philox_x1_setup(gchunk, lid, ctr_w(TAG_UPDATE, (uint32_t)c, 0), rk);
+    }
+  for (int h = 0; h < k; ++h) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (active)
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          const int q = tid + i * kTPT;
+          const int m = q % kCpr, ty = (q / kCpr) % kT, tz = q / (kCpr * kT);
+          const int row = (tz + 1) * kSide + ty + 1, word = m + 1;
+          const int at = row * kWords + word;
+          const uint64_t C = sw[at];
+          const uint64_t U = sw[at - kWords], D = sw[at + kWords];
+          const uint64_t F = sw[at - kSide * kWords], Bk = sw[at + kSide * kWords];
+          const int p = (c + y0 + ty + z0 + tz) & 1;
+          const uint32_t edge = p ? sb[at * 8 + 8] : sb[at * 8 - 1];
+          const uint4 r = philox_x1(pre[i][c], sweep0 + (uint32_t)h, rk);
+          sw[at] = ising3d_chunk(C, U, D, F, Bk, edge, r, p, thr4, thr8, thr12);
+        }
+      __syncthreads();
+    }
+  }
+  if (active)
+    for (int q = tid; q < kChunks; q += kTPT) {
+      const int m = q % kCpr, ty = (q / kCpr) % kT, tz = q / (kCpr * kT);
+      *reinterpret_cast<uint64_t *>(base + ((int64_t)(z0 + tz) * L + (y0 + ty)) * L + x0 + 8 * m) =
+          sw[((tz + 1) * kSide + ty + 1) * kWords + m + 1];
+    }
+}
+
+template <int kT>
+cudaError_t launch_tiles3(spin_lattice *h, int coarse, uint32_t sweep0) {
+  constexpr int kChunks = kT * kT * (kT / 8);
+  constexpr int kTiles = kChunks < 256 ? 256 / kChunks : 1;
+  const int64_t B = h->g.L / kT;
+  const int64_t n_tiles = B * B * B / 2;
+  dim3 grid((unsigned)((n_tiles + kTiles - 1) / kTiles), (unsigned)h->n_lat);
+  dcb3_tile_kernel<kT><<<grid, 256, 0, h->stream>>>((int8_t *)h->spins, h->g.L, coarse, sweep0, h->order_hits,
+                                                     h->d_thr, h->g, make_round_keys(h->d.seed));
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool dcb_supported(const spin_lattice *h, int tile) {
-  if (h->d.model != SPIN_ISING || h->d.dim != 2 || h->d.layout != SPIN_I8 || h->n_lat > 65535) return false;
-  if (tile != 8 && tile != 16 && tile != 32 && tile != 64 && tile != 128) return false;
+  if (h->d.model != SPIN_ISING || h->d.layout != SPIN_I8 || h->n_lat > 65535) return false;
+  if (h->d.dim == 2) {
+    if (tile != 8 && tile != 16 && tile != 32 && tile != 64 && tile != 128) return false;
+  } else if (h->d.dim == 3) {
+    if (tile != 8 && tile != 16) return false;
+  } else {
+    return false;
+  }
   return h->g.L % tile == 0 && ((h->g.L / tile) & 1) == 0;
 }
 
@@ -127,12 +235,16 @@ cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps) {
       const int coarse = first ^ cc;
       const uint32_t sweep0 = M * (uint32_t)k;
       cudaError_t e;
-      switch (h->order_tile) {
-        case 8: e = launch_tiles<8>(h, coarse, sweep0); break;
-        case 16: e = launch_tiles<16>(h, coarse, sweep0); break;
-        case 32: e = launch_tiles<32>(h, coarse, sweep0); break;
-        case 64: e = launch_tiles<64>(h, coarse, sweep0); break;
-        default: e = launch_tiles<128>(h, coarse, sweep0); break;
+      if (h->g.dim == 3) {
+        e = h->order_tile == 8 ? launch_tiles3<8>(h, coarse, sweep0) : launch_tiles3<16>(h, coarse, sweep0);
+      } else {
+        switch (h->order_tile) {
+          case 8: e = launch_tiles<8>(h, coarse, sweep0); break;
+          case 16: e = launch_tiles<16>(h, coarse, sweep0); break;
+          case 32: e = launch_tiles<32>(h, coarse, sweep0); break;
+          case 64: e = launch_tiles<64>(h, coarse, sweep0); break;
+          default: e = launch_tiles<128>(h, coarse, sweep0); break;
+        }
       }
       if (e != cudaSuccess) return e;
     }

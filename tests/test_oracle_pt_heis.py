@@ -101,14 +101,16 @@ def test_heis_chain_correlation_matches_langevin():
     assert_within(m, err, exact.heis_chain_nn(beta, L), what="chain nn")
 
 
-def test_heis_3d_high_temperature_energy():
-    """3D lattice at small beta: the bond correlation is the two-spin value
-    coth(beta) - 1/beta up to plaquette corrections of order 4 u^3 ~ 2e-5."""
-    dim, L, beta = 3, 8, 0.05
+@pytest.mark.parametrize("dim,L", [(3, 8), (2, 24)])
+def test_heis_3d_high_temperature_energy(dim, L):
+    """Square and cubic lattices at small beta: the bond correlation is the
+    two-spin value coth(beta) - 1/beta up to plaquette corrections of order
+    4 u^3 ~ 2e-5."""
+    beta = 0.05
     s = oracle.heis_init(dim, L, 2, 0)
     E, _ = oracle.heis_run(dim, L, s, beta, 2, 0, 0, 4000)
-    m, err = binned_mean(-E[200:] / (3 * L ** 3))
-    assert_within(m, err, exact.langevin(beta), floor=3e-5, what="3D bond")
+    m, err = binned_mean(-E[200:] / (dim * L ** dim))
+    assert_within(m, err, exact.langevin(beta), floor=3e-5, what=f"{dim}D bond")
 
 
 def test_heis_renormalisation_and_energy_definition():

@@ -161,7 +161,7 @@ def _events(torch):
 
 def side_configs(torch, sp, B, stream):
     """Short measurements of the other hot-path configurations (context for
-    the headline): 3D Heisenberg L=128 (FP32), and 3D EA L=16 with 1024
+    the headline): 3D Heisenberg L=128 and 2D L=4096 (FP32), and 3D EA L=16 with 1024
     realisations x 32 slots x 2 sets, exchange and measurement every sweep,
     in the per-handle multi-launch form and in the batched persistent form;
     then the uneven batch in both forms, the 2D tempering benchmark, the
@@ -178,6 +178,18 @@ def side_configs(torch, sp, B, stream):
         b.record(stream)
         torch.cuda.synchronize()
         out[name + "_flips_per_ns"] = 40 * 128 ** 3 / (a.elapsed_time(b) * 1e6)
+    lat.close()
+    # the paper's own Heisenberg study is 2D, L = 4096 (Sec. 5)
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 2, 4096, B.SPIN_F32X4, seed=13)
+    for variant, name in ((0, "heisenberg2d_L4096_fp32"), (2, "heisenberg2d_L4096_fp32_fast")):
+        lat.set_variant(variant)
+        B.spin_sweep(lat.h, None, [1.1], 2, lat.seed)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, [1.1], 20, lat.seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_flips_per_ns"] = 20 * 4096 ** 2 / (a.elapsed_time(b) * 1e6)
     lat.close()
     betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
     ea = sp.Lattice(B.SPIN_EA, 3, 16, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=12)

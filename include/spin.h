@@ -67,7 +67,8 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *              [2 colours][L rows][L/64 words]; in row y the colour-c sites
  *              x = 2k + ((c + y) & 1) are grouped in blocks of 128 k's, and
  *              k = 128 B + 4 l + q is bit l of word 4 B + q.  Needs L % 256 == 0.
- *  SPIN_F32X4  float4 (x, y, z, 0) unit vectors, [n_sets][n_temps][n_real][L^3].
+ *  SPIN_F32X4  float4 (x, y, z, 0) unit vectors, [n_sets][n_temps][n_real][L^dim]
+ *              (Heisenberg, 2D as in Sec. 5 or 3D).
  * Couplings (EA only; NULL for the ferromagnet, J = 1):
  *  SPIN_I8     int8 +-1, [n_real][dim][L^dim]: bond (i, i + e_d).
  *  SPIN_MSC1   uint32 [n_real/32][dim][2 colours][L^3/2] (bond (i, i + e_d)
@@ -78,7 +79,7 @@ typedef enum { SPIN_I8 = 0, SPIN_MSC1 = 1, SPIN_F32X4 = 2 } spin_layout;
 
 typedef struct {
   int32_t model;     /* spin_model                                             */
-  int32_t dim;       /* 2 or 3 (EA and Heisenberg: 3)                          */
+  int32_t dim;       /* 2 or 3 (coded EA: 3)                                   */
   int32_t L;         /* edge length: even, >= 4                                */
   int32_t layout;    /* spin_layout                                            */
   int32_t n_real;    /* lattices per (set, slot): EA disorder realisations     */

@@ -123,7 +123,8 @@ int validate_desc(const spin_desc *d) {
         return (d->dim == 3 && d->n_real % 32 == 0 && d->n_real / 32 < 4096) ? SPIN_OK : SPIN_EINVAL;
       return SPIN_EINVAL;
     case SPIN_HEISENBERG:
-      return (d->dim == 3 && d->layout == SPIN_F32X4 && d->n_real <= 4096) ? SPIN_OK : SPIN_EINVAL;
+      return ((d->dim == 2 || d->dim == 3) && d->layout == SPIN_F32X4 && d->n_real <= 4096) ? SPIN_OK
+                                                                                              : SPIN_EINVAL;
     default:
       return SPIN_EINVAL;
   }

@@ -1,6 +1,7 @@
-// 3D Heisenberg model (Eq. On_hamiltonian, n = 3) with FP32 unit vectors
-// stored as float4 (x, y, z, 0): hot start, checkerboard Metropolis sweep
-// with a uniformly drawn new direction (Sec. 5), renormalisation.
+// Heisenberg model (Eq. On_hamiltonian, n = 3) on the cubic lattice and, as
+// in the paper's own study (Sec. 5), the square lattice, with FP32 unit
+// vectors stored as float4 (x, y, z, 0): hot start, checkerboard Metropolis
+// sweep with a uniformly drawn new direction (Sec. 5), renormalisation.
 #include "internal.h"
 
 namespace spin {
@@ -41,10 +42,10 @@ __global__ void heis_cold_kernel(float4 *__restrict__ s, int64_t total) {
 
 // One colour phase.  Thread per colour site j (site i = 2j + parity); one
 // Philox call per site: words 0, 1 give the proposal, word 2 the acceptance
-// uniform.  dE = -(n - s) . h with h the sum of the six neighbour spins;
+// uniform.  dE = -(n - s) . h with h the sum of the 2 kDim neighbour spins;
 // accept iff dE <= 0 or u3 < exp(-beta dE).  beta (float) is read from
 // word 0 of the slot's row of the threshold table.
-template <bool kFast>
+template <bool kFast, int kDim>
 __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s, Geom g,
                                                          uint32_t total,
                                                          const uint32_t *__restrict__ thr,
@@ -70,14 +71,22 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
     const uint32_t ixm = st.rowbase + (st.x == 0 ? L - 1 : st.x - 1);
     const uint32_t iyp = st.y == L - 1 ? i - (L - 1) * L : i + L;
     const uint32_t iym = st.y == 0 ? i + (L - 1) * L : i - L;
-    const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
-    const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
-    const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym], e = sl[izp], f = sl[izm];
+    const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym];
+    float hx, hy, hz;
+    if constexpr (kDim == 3) {
+      const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
+      const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
+      const float4 e = sl[izp], f = sl[izm];
+      hx = a.x + b.x + c.x + d.x + e.x + f.x;
+      hy = a.y + b.y + c.y + d.y + e.y + f.y;
+      hz = a.z + b.z + c.z + d.z + e.z + f.z;
+    } else {
+      hx = a.x + b.x + c.x + d.x;
+      hy = a.y + b.y + c.y + d.y;
+      hz = a.z + b.z + c.z + d.z;
+    }
     const float4 si = sl[i];
     const uint4 w = philox(make_uint4(j, sweep, lid, wctr), rk);
-    const float hx = a.x + b.x + c.x + d.x + e.x + f.x;
-    const float hy = a.y + b.y + c.y + d.y + e.y + f.y;
-    const float hz = a.z + b.z + c.z + d.z + e.z + f.z;
     const float4 n = unit_vector<kFast>(w.x, w.y);
     const float u3 = uniform24(w.z);
     const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
@@ -122,12 +131,18 @@ cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {
-      if (h->variant == 2)
-        heis_phase_kernel<true><<<capped_grid(half), 256, 0, h->stream>>>(
-            (float4 *)h->spins, h->g, half, h->d_thr, rk, sweep, colour);
-      else
-        heis_phase_kernel<false><<<capped_grid(half), 256, 0, h->stream>>>(
-            (float4 *)h->spins, h->g, half, h->d_thr, rk, sweep, colour);
+      float4 *sp = (float4 *)h->spins;
+      if (h->g.dim == 3) {
+        if (h->variant == 2)
+          heis_phase_kernel<true, 3><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
+        else
+          heis_phase_kernel<false, 3><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
+      } else {
+        if (h->variant == 2)
+          heis_phase_kernel<true, 2><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
+        else
+          heis_phase_kernel<false, 2><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
+      }
     }
     if ((sweep + 1u) % 100u == 0u)
       heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>(

@@ -250,11 +250,16 @@ __global__ void measure_heis_kernel(const float4 *__restrict__ s, Geom g,
     const float4 a = sl[i];
     const float4 bx = sl[i - x + (x == L - 1 ? 0 : x + 1)];
     const float4 by = sl[y == L - 1 ? i - (int64_t)(L - 1) * L : i + L];
-    const float4 bz = sl[z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL];
     const double ax = a.x, ay = a.y, az = a.z;
-    e -= ax * ((double)bx.x + (double)by.x + (double)bz.x) +
-         ay * ((double)bx.y + (double)by.y + (double)bz.y) +
-         az * ((double)bx.z + (double)by.z + (double)bz.z);
+    if (g.dim == 3) {
+      const float4 bz = sl[z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL];
+      e -= ax * ((double)bx.x + (double)by.x + (double)bz.x) +
+           ay * ((double)bx.y + (double)by.y + (double)bz.y) +
+           az * ((double)bx.z + (double)by.z + (double)bz.z);
+    } else {
+      e -= ax * ((double)bx.x + (double)by.x) + ay * ((double)bx.y + (double)by.y) +
+           az * ((double)bx.z + (double)by.z);
+    }
     mx += ax;
     my += ay;
     mz += az;

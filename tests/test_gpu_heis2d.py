@@ -1,0 +1,95 @@
+"""The Heisenberg model on the square lattice, the paper's own study
+(Sec. 5): FP32 GPU kernels against the FP64 oracle with the tolerances of
+the 3D tests (one sweep from a common start within 1e-5 away from near-ties,
+|s| - 1 <= 1e-6 after renormalisation, reductions on a given state, and the
+long-run energy within 3 combined standard errors)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.stats import binned_mean
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1101_1427_gb300 as sp  # noqa: E402
+from paper_1101_1427_gb300 import _binding as B  # noqa: E402
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_heis2d_one_sweep_within_tolerance(variant):
+    L, seed, beta = 64, 8, 1.1
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 2, L, B.SPIN_F32X4, seed=seed)
+    lat.set_variant(variant)
+    s0 = oracle.heis_init(2, L, seed, 0).astype(np.float32)
+    dev = np.zeros((L * L, 4), np.float32)
+    dev[:, :3] = s0
+    lat.spins.copy_(torch.from_numpy(dev.ravel()))
+    lat.sweep([beta], 1)
+    got = host(lat.spins).reshape(-1, 4)[:, :3]
+    ref = s0.astype(np.float64)
+    margin = oracle.heis_sweep(2, L, ref, beta, seed, 0, 0, want_margin=True)
+    err = np.max(np.abs(got - ref), axis=1)
+    flagged = margin < 1e-5
+    idx = np.arange(L * L)
+    x, y = idx % L, idx // L
+    near = flagged.copy()
+    for d in (1, -1):
+        for sh in ((x + d) % L + L * y, x + L * ((y + d) % L)):
+            near |= flagged[sh]
+    bad = (err > 1e-5) & ~near
+    assert not bad.any(), (np.nonzero(bad)[0][:10], err[bad][:10])
+    assert (err > 1e-5).sum() <= 20
+    assert np.all(host(lat.spins).reshape(-1, 4)[:, 3] == 0)
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_heis2d_renormalisation_bound(variant):
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 2, 32, B.SPIN_F32X4, n_temps=2, seed=4)
+    lat.set_variant(variant)
+    lat.sweep([0.7, 1.4], 100)
+    v = host(lat.spins).reshape(-1, 4)[:, :3].astype(np.float64)
+    assert np.max(np.abs(np.linalg.norm(v, axis=1) - 1)) <= 1e-6
+
+
+def test_heis2d_measure_matches_oracle_on_oracle_state():
+    L = 20
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 2, L, B.SPIN_F32X4, n_temps=2, seed=5)
+    states = [oracle.heis_init(2, L, 5 + k, 0).astype(np.float32).astype(np.float64) for k in range(2)]
+    dev = np.zeros((2, L * L, 4), np.float32)
+    for k in range(2):
+        dev[k, :, :3] = states[k]
+    lat.spins.copy_(torch.from_numpy(dev.ravel()))
+    Ef, Mf = lat.measure()
+    Ef, Mf = host(Ef), host(Mf)
+    for k in range(2):
+        assert abs(Ef[k] - oracle.heis_energy(2, L, states[k])) < 1e-9 * L * L
+        assert np.allclose(Mf[k], oracle.heis_magnetisation(2, L, states[k]), atol=1e-9 * L * L)
+
+
+def test_heis2d_long_run_energy_matches_fp64_oracle():
+    L, beta, n, seed = 24, 1.1, 3000, 12
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 2, L, B.SPIN_F32X4, seed=seed)
+    out = lat.run([beta], n, measure_every=1)
+    eg = out["Ef"].cpu().numpy() / L ** 2
+    s = oracle.heis_init(2, L, seed, 0)
+    eo, _ = oracle.heis_run(2, L, s, beta, seed, 0, 0, n)
+    eo = eo / L ** 2
+    mg, sg = binned_mean(eg[300:], 30)
+    mo, so = binned_mean(eo[300:], 30)
+    assert abs(mg - mo) <= 3 * math.sqrt(sg ** 2 + so ** 2) + 1e-12, (mg, sg, mo, so)
+
+
+def test_heis2d_init_equals_oracle():
+    L, seed = 32, 3
+    lat = sp.Lattice(B.SPIN_HEISENBERG, 2, L, B.SPIN_F32X4, seed=seed)
+    got = host(lat.spins).reshape(-1, 4)[:, :3]
+    ref = oracle.heis_init(2, L, seed, 0)
+    assert np.max(np.abs(got - ref)) < 1e-6

@@ -138,12 +138,14 @@ int spin_measure(spin_lattice *lat, const void *couplings, int64_t *E, int64_t *
 int spin_pt_swap(spin_lattice *lat, const void *couplings, const double *betas,
                  uint64_t seed, int64_t *accepted);
 
-/* A whole simulation on one handle: n_sweeps sweeps; after every sweep whose
- * 1-based count is a multiple of measure_every (> 0) the measurements of
- * spin_measure are appended to the series (device buffers, NULL to skip,
- * row k holds measurement k); after every sweep whose count is a multiple
- * of pt_every (> 0) one exchange step as in spin_pt_swap follows the
- * measurement. */
+/* A whole simulation on one handle: n_sweeps sweeps; after every sweep that
+ * brings the handle's sweep count (spin_sweeps_done) to a multiple of
+ * measure_every (> 0) the measurements of spin_measure are appended to the
+ * series (device buffers, NULL to skip, row k holds the call's measurement
+ * k, so a call writes (s + n_sweeps) / measure_every - s / measure_every
+ * rows for a count s before it); after every sweep that brings the count to
+ * a multiple of pt_every (> 0) one exchange step as in spin_pt_swap follows
+ * the measurement. */
 int spin_run(spin_lattice *lat, const void *couplings, const double *betas, int64_t n_sweeps,
              int32_t measure_every, int32_t pt_every, int64_t *E_series, int64_t *M_series,
              int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted);
@@ -291,6 +293,11 @@ int spin_sync(spin_lattice *lat);
  * handle's stream a write of the same values to the device copy that
  * batched launches read. */
 int64_t spin_sweeps_done(const spin_lattice *lat);
+/* Copies the handle's descriptor (as given to spin_init) to *out (host), so
+ * that a binding can size and check the arrays it passes: betas holds
+ * n_temps doubles, E and M n_lat int64 per measurement, and so on.
+ * SPIN_EINVAL for a NULL argument. */
+int spin_describe(const spin_lattice *lat, spin_desc *out);
 int64_t spin_pt_steps_done(const spin_lattice *lat);
 int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_done);
 

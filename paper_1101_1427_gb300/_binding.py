@@ -59,6 +59,7 @@ def lib():
         L.spin_rng_fill.argtypes = [u64, u32, u32, u32, u32, u32, u64, p, p]
         L.spin_rng_probe.argtypes = [u64, u32, u32, p, p]
         L.spin_pipe_probe.argtypes = [C.c_int, i32, u32, p, p, p, p]
+        L.spin_describe.argtypes = [p, C.POINTER(spin_desc)]
         L.spin_sync.argtypes = [p]
         L.spin_heis_measure_noalloc.argtypes = [p, i32, i32, p, p, p]
         L.spin_batch_run.argtypes = [p, C.c_int, i64, i32, i32, p]
@@ -82,7 +83,7 @@ def lib():
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_pipe_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
                      "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width", "spin_slab_phase",
-                     "spin_slab_measure"):
+                     "spin_slab_measure", "spin_describe"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -117,6 +118,70 @@ def _host_doubles(values):
     return arr
 
 
+# ------------------------------------------------------------------ argument checks
+# The C ABI takes host beta arrays and device buffers without their lengths
+# (they follow from the handle's descriptor), so the binding checks every
+# array it passes against the descriptor before the call.
+def spin_describe(h):
+    d = spin_desc()
+    _check(lib().spin_describe(h, C.byref(d)), "spin_describe")
+    return d
+
+
+def _shape(h):
+    d = spin_describe(h)
+    return d, d.L ** d.dim, d.n_sets * d.n_temps * d.n_real
+
+
+def _bad(what, msg):
+    raise SpinError(SPIN_EINVAL, f"{what}: {msg}")
+
+
+def _need_betas(d, betas, what):
+    if len(betas) != d.n_temps:
+        _bad(what, f"{len(betas)} betas for {d.n_temps} temperature slots")
+
+
+def _need(t, n, dtype, what, name):
+    """t (if given) must be a contiguous CUDA tensor of dtype with >= n elements."""
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() < n:
+        _bad(what, f"{name} must be a contiguous CUDA {dtype} tensor of at least {n} elements "
+                   f"(got {t.dtype}, {t.numel()}, cuda={t.is_cuda})")
+
+
+def _need_couplings(d, N, couplings, what):
+    import torch
+    if d.model != SPIN_EA:
+        return
+    if couplings is None:
+        _bad(what, "EA handles need their couplings")
+    if d.layout == SPIN_I8:
+        _need(couplings, d.n_real * d.dim * N, torch.int8, what, "couplings")
+    else:
+        _need(couplings, (d.n_real // 32) * d.dim * N, torch.int32, what, "couplings")
+
+
+def _n_meas(h, n_sweeps, measure_every):
+    """Measurement rows a call writes: sweep counts reaching a multiple of
+    measure_every between the handle's count now and after the call."""
+    if measure_every <= 0:
+        return 0
+    cur = spin_sweeps_done(h)
+    return (cur + n_sweeps) // measure_every - cur // measure_every
+
+
+def _need_series(h, d, n_lat, rows, E, M, Q, Ef, Mf, accepted, what):
+    import torch
+    _need(E, rows * n_lat, torch.int64, what, "E")
+    _need(M, rows * n_lat, torch.int64, what, "M")
+    _need(Q, rows * d.n_temps * d.n_real, torch.int64, what, "Q")
+    _need(Ef, rows * n_lat, torch.float64, what, "Ef")
+    _need(Mf, 3 * rows * n_lat, torch.float64, what, "Mf")
+    _need(accepted, d.n_sets * d.n_temps, torch.int64, what, "accepted")
+
+
 # ------------------------------------------------------------------ ABI names
 def spin_init(desc, spins, couplings=None):
     h = C.c_void_p()
@@ -125,32 +190,53 @@ def spin_init(desc, spins, couplings=None):
 
 
 def spin_sweep(h, couplings, betas, n_sweeps, seed):
+    d, N, _ = _shape(h)
+    _need_betas(d, betas, "spin_sweep")
+    _need_couplings(d, N, couplings, "spin_sweep")
     return _check(lib().spin_sweep(h, _ptr(couplings), _host_doubles(betas), n_sweeps, seed),
                   "spin_sweep")
 
 
 def spin_measure(h, couplings=None, E=None, M=None, Q=None, Ef=None, Mf=None):
+    d, N, n_lat = _shape(h)
+    _need_couplings(d, N, couplings, "spin_measure")
+    _need_series(h, d, n_lat, 1, E, M, Q, Ef, Mf, None, "spin_measure")
     return _check(lib().spin_measure(h, _ptr(couplings), _ptr(E), _ptr(M), _ptr(Q), _ptr(Ef),
                                      _ptr(Mf)), "spin_measure")
 
 
 def spin_pt_swap(h, couplings, betas, seed, accepted=None):
+    d, N, n_lat = _shape(h)
+    _need_betas(d, betas, "spin_pt_swap")
+    _need_couplings(d, N, couplings, "spin_pt_swap")
+    _need_series(h, d, n_lat, 0, None, None, None, None, None, accepted, "spin_pt_swap")
     return _check(lib().spin_pt_swap(h, _ptr(couplings), _host_doubles(betas), seed,
                                      _ptr(accepted)), "spin_pt_swap")
 
 
 def spin_run(h, couplings, betas, n_sweeps, measure_every=0, pt_every=0, E=None, M=None,
              Q=None, Ef=None, Mf=None, accepted=None):
+    d, N, n_lat = _shape(h)
+    _need_betas(d, betas, "spin_run")
+    _need_couplings(d, N, couplings, "spin_run")
+    rows = _n_meas(h, n_sweeps, measure_every) if n_sweeps > 0 else 0
+    _need_series(h, d, n_lat, rows, E, M, Q, Ef, Mf, accepted, "spin_run")
     return _check(lib().spin_run(h, _ptr(couplings), _host_doubles(betas), n_sweeps,
                                  measure_every, pt_every, _ptr(E), _ptr(M), _ptr(Q), _ptr(Ef),
                                  _ptr(Mf), _ptr(accepted)), "spin_run")
 
 
 def spin_unpack_i8(h, out):
+    import torch
+    _, N, n_lat = _shape(h)
+    _need(out, n_lat * N, torch.int8, "spin_unpack_i8", "out")
     return _check(lib().spin_unpack_i8(h, _ptr(out)), "spin_unpack_i8")
 
 
 def spin_pack_i8(h, inp):
+    import torch
+    _, N, n_lat = _shape(h)
+    _need(inp, n_lat * N, torch.int8, "spin_pack_i8", "in")
     return _check(lib().spin_pack_i8(h, _ptr(inp)), "spin_pack_i8")
 
 
@@ -171,24 +257,31 @@ def spin_pipe_probe(op, blocks_per_sm, iters, cycles, sink, stream=None):
     return sms.value
 
 
-def _batch_items(items):
+def _batch_items(items, n_sweeps=0, measure_every=0):
     """items: list of dicts with keys lat (handle), couplings, betas and the
-    optional device tensors E, M, Q, accepted.  Returns the ctypes array and
-    the host beta arrays that must stay alive during the call."""
+    optional device tensors E, M, Q, accepted (checked against each handle's
+    descriptor).  Returns the ctypes array and the host beta arrays that must
+    stay alive during the call."""
     arr = (spin_batch_item * len(items))()
     keep = []
     for k, it in enumerate(items):
+        lat = it["lat"].value if hasattr(it["lat"], "value") else it["lat"]
+        d, N, n_lat = _shape(lat)
+        _need_betas(d, it["betas"], "spin_batch_run")
+        _need_couplings(d, N, it.get("couplings"), "spin_batch_run")
+        rows = _n_meas(lat, n_sweeps, measure_every) if n_sweeps > 0 else 0
+        _need_series(lat, d, n_lat, rows, it.get("E"), it.get("M"), it.get("Q"), None, None,
+                     it.get("accepted"), "spin_batch_run")
         b = _host_doubles(it["betas"])
         keep.append(b)
         dp = lambda key: it[key].data_ptr() if it.get(key) is not None else None
-        lat = it["lat"].value if hasattr(it["lat"], "value") else it["lat"]
         arr[k] = spin_batch_item(lat, dp("couplings"), C.cast(b, C.c_void_p), dp("E"), dp("M"),
                                  dp("Q"), dp("accepted"))
     return arr, keep
 
 
 def spin_batch_run(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
-    arr, keep = _batch_items(items)
+    arr, keep = _batch_items(items, n_sweeps, measure_every)
     return _check(lib().spin_batch_run(arr, len(items), n_sweeps, measure_every, pt_every, stream),
                   "spin_batch_run")
 
@@ -209,6 +302,10 @@ def spin_set_batch_options(h, timeout_ns=0, ctas_per_sm=0, missing_arrivals=0):
 def spin_heis_measure_noalloc(spins, L, n_lat, Ef=None, Mf=None, stream=None):
     """Heisenberg E and M into caller-owned tensors without any device
     allocation (the partial sums use a fixed array inside the library)."""
+    import torch
+    _need(spins, 4 * n_lat * L ** 3, torch.float32, "spin_heis_measure_noalloc", "spins")
+    _need(Ef, n_lat, torch.float64, "spin_heis_measure_noalloc", "Ef")
+    _need(Mf, 3 * n_lat, torch.float64, "spin_heis_measure_noalloc", "Mf")
     return _check(lib().spin_heis_measure_noalloc(_ptr(spins), L, n_lat, _ptr(Ef), _ptr(Mf), stream),
                   "spin_heis_measure_noalloc")
 

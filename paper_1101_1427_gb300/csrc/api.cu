@@ -393,6 +393,11 @@ int spin_sync(spin_lattice *h) {
 }
 
 int64_t spin_sweeps_done(const spin_lattice *h) { return h ? h->sweeps_done : -1; }
+int spin_describe(const spin_lattice *h, spin_desc *out) {
+  if (!h || !out) return SPIN_EINVAL;
+  *out = h->d;
+  return SPIN_OK;
+}
 int64_t spin_pt_steps_done(const spin_lattice *h) { return h ? h->pt_steps_done : -1; }
 
 int spin_set_counters(spin_lattice *h, int64_t sweeps_done, int64_t pt_steps_done) {

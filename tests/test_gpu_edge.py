@@ -149,3 +149,30 @@ def test_double_checkerboard_hundred_hits():
         s = oracle.ising_init(2, L, seed, lid)
         oracle.dcb_sweeps(L, s, 0.4407, seed, lid, 0, 2 * k, T, k, order == B.SPIN_ORDER_DCB_SYMMETRIC)
         assert np.array_equal(host(lat.spins), s), order
+
+
+def test_binding_checks_arrays_against_the_handle():
+    """The ABI takes host betas and device buffers without lengths; the
+    binding checks them against the handle's descriptor and refuses short,
+    mistyped or host arrays before the call, leaving the handle unchanged."""
+    lat = sp.Lattice(B.SPIN_ISING, 2, 32, B.SPIN_I8, n_temps=3, seed=41)
+    before = lat.spins.clone()
+    with pytest.raises(B.SpinError):
+        lat.sweep([0.4, 0.5], 1)  # three slots
+    short = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(B.SpinError):
+        B.spin_measure(lat.h, None, E=short)
+    with pytest.raises(B.SpinError):
+        B.spin_measure(lat.h, None, E=torch.zeros(3, dtype=torch.int32, device="cuda"))
+    with pytest.raises(B.SpinError):
+        B.spin_measure(lat.h, None, M=torch.zeros(3, dtype=torch.int64))  # host tensor
+    with pytest.raises(B.SpinError):  # 4 measurement rows need 12 entries
+        B.spin_run(lat.h, None, [0.4, 0.5, 0.6], 8, 2, 0, torch.zeros(11, dtype=torch.int64, device="cuda"))
+    with pytest.raises(B.SpinError):
+        lat.pack(torch.ones(32 * 32, dtype=torch.int8, device="cuda"))  # one lattice of three
+    assert torch.equal(lat.spins, before) and lat.sweeps_done == 0
+    d = B.spin_describe(lat.h)
+    assert (d.model, d.dim, d.L, d.layout, d.n_temps) == (B.SPIN_ISING, 2, 32, B.SPIN_I8, 3)
+    ok = torch.zeros(12, dtype=torch.int64, device="cuda")
+    B.spin_run(lat.h, None, [0.4, 0.5, 0.6], 8, 2, 0, ok)
+    assert lat.sweeps_done == 8

@@ -71,22 +71,17 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
     const uint32_t ixm = st.rowbase + (st.x == 0 ? L - 1 : st.x - 1);
     const uint32_t iyp = st.y == L - 1 ? i - (L - 1) * L : i + L;
     const uint32_t iym = st.y == 0 ? i + (L - 1) * L : i - L;
-    const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym];
-    float hx, hy, hz;
-    if constexpr (kDim == 3) {
-      const uint32_t izp = st.z == L - 1 ? i - (L - 1) * LL : i + LL;
-      const uint32_t izm = st.z == 0 ? i + (L - 1) * LL : i - LL;
-      const float4 e = sl[izp], f = sl[izm];
-      hx = a.x + b.x + c.x + d.x + e.x + f.x;
-      hy = a.y + b.y + c.y + d.y + e.y + f.y;
-      hz = a.z + b.z + c.z + d.z + e.z + f.z;
-    } else {
-      hx = a.x + b.x + c.x + d.x;
-      hy = a.y + b.y + c.y + d.y;
-      hz = a.z + b.z + c.z + d.z;
-    }
+    // (kDim is a compile-time constant: the 2D form drops the z terms)
+    const uint32_t izp = kDim == 3 ? (st.z == L - 1 ? i - (L - 1) * LL : i + LL) : i;
+    const uint32_t izm = kDim == 3 ? (st.z == 0 ? i + (L - 1) * LL : i - LL) : i;
+    const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 a = sl[ixp], b = sl[ixm], c = sl[iyp], d = sl[iym], e = kDim == 3 ? sl[izp] : zero,
+                 f = kDim == 3 ? sl[izm] : zero;
     const float4 si = sl[i];
     const uint4 w = philox(make_uint4(j, sweep, lid, wctr), rk);
+    const float hx = kDim == 3 ? a.x + b.x + c.x + d.x + e.x + f.x : a.x + b.x + c.x + d.x;
+    const float hy = kDim == 3 ? a.y + b.y + c.y + d.y + e.y + f.y : a.y + b.y + c.y + d.y;
+    const float hz = kDim == 3 ? a.z + b.z + c.z + d.z + e.z + f.z : a.z + b.z + c.z + d.z;
     const float4 n = unit_vector<kFast>(w.x, w.y);
     const float u3 = uniform24(w.z);
     const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;

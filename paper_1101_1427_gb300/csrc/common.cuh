@@ -217,6 +217,15 @@ __host__ __device__ __forceinline__ int slot_of(const Geom &g, int64_t lat) {
   return (int)((lat / g.n_real) % g.n_temps);
 }
 
+// Programmatic dependent launch.  A kernel launched with launch_dependent()
+// may start while the previous kernel of its stream is finishing: it calls
+// griddep_wait() before touching memory, which returns once that kernel has
+// completed and its writes are visible.  griddep_release() lets the next
+// such kernel's CTAs be scheduled once every CTA of this grid has started
+// (they wait in griddep_wait() until this grid is done).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // Warp-level sums.
 __device__ __forceinline__ long long warp_sum(long long v) {
 #pragma unroll

@@ -51,6 +51,8 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
                                                          const uint32_t *__restrict__ thr,
                                                          RoundKeys rk, uint32_t sweep,
                                                          int colour) {
+  griddep_wait();
+  griddep_release();
   const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N, half = N / 2;
   const bool single = g.n_real == 1 && g.n_temps == 1 && g.n_sets == 1;
   const float beta0 = __uint_as_float(__ldg(thr));
@@ -127,17 +129,11 @@ cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {
       float4 *sp = (float4 *)h->spins;
-      if (h->g.dim == 3) {
-        if (h->variant == 2)
-          heis_phase_kernel<true, 3><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
-        else
-          heis_phase_kernel<false, 3><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
-      } else {
-        if (h->variant == 2)
-          heis_phase_kernel<true, 2><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
-        else
-          heis_phase_kernel<false, 2><<<capped_grid(half), 256, 0, h->stream>>>(sp, h->g, half, h->d_thr, rk, sweep, colour);
-      }
+      auto *k = h->g.dim == 3 ? (h->variant == 2 ? heis_phase_kernel<true, 3> : heis_phase_kernel<false, 3>)
+                              : (h->variant == 2 ? heis_phase_kernel<true, 2> : heis_phase_kernel<false, 2>);
+      const cudaError_t le = launch_dependent(k, dim3(capped_grid(half)), dim3(256), 0, h->stream, sp, h->g, half,
+                                              h->d_thr, rk, sweep, colour);
+      if (le != cudaSuccess) return le;
     }
     if ((sweep + 1u) % 100u == 0u)
       heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>(

@@ -74,6 +74,24 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
 // [n_lat]), else NULL to compute them
 cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, const int64_t *energies);
 
+// Launches kernel k as a programmatic dependent of the previous work in
+// stream s (the kernel must call griddep_wait() before touching memory).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // rng.cu
 cudaError_t launch_rng_fill(uint64_t seed, uint32_t w, uint32_t lattice_id, uint32_t sweep,
                             uint64_t count, uint32_t *out, cudaStream_t s);

@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
                                                             const uint32_t *__restrict__ thr,
                                                             Geom g, RoundKeys rk, uint32_t sweep,
                                                             int colour) {
+  griddep_wait();
+  griddep_release();
   const int chunks = L >> 3;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -95,6 +97,8 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
 __global__ void __launch_bounds__(256) ising3d_phase_kernel(int8_t *__restrict__ spins, int L, int tiles_x,
                                                             int zlen, const uint32_t *__restrict__ thr, Geom g,
                                                             RoundKeys rk, uint32_t sweep, int colour) {
+  griddep_wait();
+  griddep_release();
   const int chunks = L >> 3;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
   const int m = tile_x * blockDim.x + threadIdx.x;
@@ -225,8 +229,10 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
         const int bx = chunks < 128 ? chunks : 128;
         const int by = 256 / bx;
         dim3 block(bx, by), grid((chunks + bx - 1) / bx, (g.L + by - 1) / by, (unsigned)h->n_lat);
-        ising2d_phase_kernel<<<grid, block, 0, h->stream>>>((int8_t *)h->spins, g.L, h->d_thr, g,
-                                                             rk, sweep, colour);
+        const cudaError_t e = launch_dependent(ising2d_phase_kernel, grid, block, 0, h->stream,
+                                               (int8_t *)h->spins, g.L, (const uint32_t *)h->d_thr, g, rk,
+                                               sweep, colour);
+        if (e != cudaSuccess) return e;
       } else if (fast3d) {
         const int chunks = g.L / 8;
         const int bx = chunks < 64 ? chunks : 64;
@@ -235,8 +241,10 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
         const int zlen = g.L < 16 ? g.L : 16;
         dim3 block(bx, by), grid((unsigned)(tiles_x * tiles_y), (unsigned)((g.L + zlen - 1) / zlen),
                                  (unsigned)h->n_lat);
-        ising3d_phase_kernel<<<grid, block, 0, h->stream>>>((int8_t *)h->spins, g.L, tiles_x, zlen, h->d_thr, g,
-                                                             rk, sweep, colour);
+        const cudaError_t e = launch_dependent(ising3d_phase_kernel, grid, block, 0, h->stream,
+                                               (int8_t *)h->spins, g.L, tiles_x, zlen, (const uint32_t *)h->d_thr,
+                                               g, rk, sweep, colour);
+        if (e != cudaSuccess) return e;
       } else {
         const uint32_t total = (uint32_t)(h->n_lat * ((g.N / 2 + 3) / 4));
         unsigned grid = grid_for(total, 256);

@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w
                                                         const uint32_t *__restrict__ thr,
                                                         RoundKeys rk, uint32_t sweep,
                                                         int colour) {
+  griddep_wait();
+  griddep_release();
   const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = (N / 2 + 3) / 4;
   const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
@@ -90,6 +92,8 @@ __global__ void __launch_bounds__(256) msc_phase_pair_kernel(uint32_t *__restric
                                                              uint32_t total,
                                                              const uint32_t *__restrict__ thr,
                                                              RoundKeys rk, uint32_t sweep, int colour) {
+  griddep_wait();
+  griddep_release();
   const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = (N / 2 + 3) / 4;
   const uint32_t G = (uint32_t)g.n_real / 32, G2 = G / 2, T = (uint32_t)g.n_temps;
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
@@ -174,15 +178,12 @@ cudaError_t launch_sweeps_msc_ea(spin_lattice *h, const uint32_t *J, int64_t n_s
   const uint32_t work = (uint32_t)((pair ? n_wl / 2 : n_wl) * ((g.N / 2 + 3) / 4));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
-    for (int colour = 0; colour < 2; ++colour)
-      if (pair)
-        msc_phase_pair_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
-                                                                   h->d_thr, rk, sweep, colour);
-      else
-        msc_phase_kernel<<<capped(work), 256, 0, h->stream>>>((uint32_t *)h->spins, J, g, work,
-                                                              h->d_thr, rk, sweep, colour);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    for (int colour = 0; colour < 2; ++colour) {
+      const cudaError_t e = launch_dependent(pair ? msc_phase_pair_kernel : msc_phase_kernel, dim3(capped(work)),
+                                             dim3(256), 0, h->stream, (uint32_t *)h->spins, J, g, work,
+                                             (const uint32_t *)h->d_thr, rk, sweep, colour);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(256) msc2d_phase_kernel(uint32_t *__restrict__
                                                           RoundKeys rk, uint32_t sweep,
                                                           int colour) {
   __shared__ uint4 masks[kWarps][32][2];
+  griddep_wait();
+  griddep_release();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t first = (blockIdx.x * kWarps + wib) * 32u;
   if (first >= total_blocks) return;
@@ -177,11 +179,12 @@ cudaError_t launch_sweeps_msc2d(spin_lattice *h, int64_t n_sweeps) {
   const unsigned grid = (unsigned)((blocks + 32 * kWarps - 1) / (32 * kWarps));
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
-    for (int colour = 0; colour < 2; ++colour)
-      msc2d_phase_kernel<<<grid, 32 * kWarps, 0, h->stream>>>(
-          (uint32_t *)h->spins, m, h->g, (uint32_t)blocks, h->d_thr, rk, sweep, colour);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    for (int colour = 0; colour < 2; ++colour) {
+      const cudaError_t e = launch_dependent(msc2d_phase_kernel, dim3(grid), dim3(32 * kWarps), 0, h->stream,
+                                             (uint32_t *)h->spins, m, h->g, (uint32_t)blocks,
+                                             (const uint32_t *)h->d_thr, rk, sweep, colour);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

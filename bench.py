@@ -51,8 +51,8 @@ WIDE_MULS_PER_CLK_PER_SM = 32
 # (mean of two launches captured with ncu, summarised in profiles/), valid
 # while the kernel's sources hash to KERNEL_TRAFFIC_SRC_SHA; otherwise
 # reported as null.
-KERNEL_TRAFFIC_BYTES = (100_703_488 + 10_839_040 + 100_700_928 + 7_587_840) // 2
-KERNEL_TRAFFIC_SRC_SHA = "aaa05b638e656a0b"
+KERNEL_TRAFFIC_BYTES = (100_703_232 + 11_326_464 + 100_742_912 + 7_770_880) // 2
+KERNEL_TRAFFIC_SRC_SHA = "206e08c055b635ba"
 
 
 def kernel_sha():

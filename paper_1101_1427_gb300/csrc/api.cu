@@ -246,6 +246,7 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
 
 int spin_sweep(spin_lattice *h, const void *couplings, const double *betas, int64_t n_sweeps,
                uint64_t seed) {
+  NvtxRange nvtx_range("spin_sweep");
   if (!h || n_sweeps < 0 || seed != h->d.seed) return SPIN_EINVAL;
   if (ea(h) && !couplings) return SPIN_EINVAL;
   if (couplings && !aligned16(couplings)) return SPIN_EALIGN;
@@ -264,6 +265,7 @@ int spin_sweep(spin_lattice *h, const void *couplings, const double *betas, int6
 
 int spin_measure(spin_lattice *h, const void *couplings, int64_t *E, int64_t *M, int64_t *Q,
                  double *Ef, double *Mf) {
+  NvtxRange nvtx_range("spin_measure");
   if (!h) return SPIN_EINVAL;
   if (ea(h) && !couplings) return SPIN_EINVAL;
   if (couplings && !aligned16(couplings)) return SPIN_EALIGN;
@@ -289,12 +291,14 @@ int pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_
 
 int spin_pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_t seed,
                  int64_t *accepted) {
+  NvtxRange nvtx_range("spin_pt_swap");
   return pt_swap(h, couplings, betas, seed, accepted, nullptr);
 }
 
 int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_t n_sweeps,
              int32_t measure_every, int32_t pt_every, int64_t *E_series, int64_t *M_series,
              int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted) {
+  NvtxRange nvtx_range("spin_run");
   if (!h || n_sweeps < 0) return SPIN_EINVAL;
   if (pt_every > 0 && h->d.model == SPIN_HEISENBERG) return SPIN_EINVAL;
   const bool measuring = measure_every > 0 && (E_series || M_series || Q_series || Ef_series || Mf_series);

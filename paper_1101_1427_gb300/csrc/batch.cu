@@ -977,6 +977,7 @@ static std::recursive_mutex g_batch_mutex;
 
 extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                               int32_t measure_every, int32_t pt_every, void *stream_v) {
+  NvtxRange nvtx_range("spin_batch_run");
   if (!items || n_items <= 0 || n_items > kMaxHandles || n_sweeps < 0 || measure_every < 0 || pt_every < 0)
     return SPIN_EINVAL;
   std::lock_guard<std::recursive_mutex> lock(g_batch_mutex);
@@ -1102,6 +1103,7 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
 extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                                int32_t measure_every, int32_t pt_every, void *stream_v,
                                int32_t *best_out) {
+  NvtxRange nvtx_range("spin_batch_tune");
   std::lock_guard<std::recursive_mutex> lock(g_batch_mutex);
   if (!items || n_items <= 0 || n_items > kMaxHandles) return SPIN_EINVAL;
   cudaStream_t st = (cudaStream_t)stream_v;

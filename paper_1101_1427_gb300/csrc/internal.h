@@ -5,8 +5,19 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/spin.h"
 #include "common.cuh"
+
+// NVTX range over one ABI call, so that a profiler's timeline shows which
+// entry point enqueued which kernels (no cost when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct spin_lattice {
   spin_desc d;

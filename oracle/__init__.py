@@ -62,6 +62,7 @@ def lib():
         L.or_ising_init_sites.argtypes = [i64, p, p, u64, u32, i32]
         L.or_dcb_sweeps.argtypes = [i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
         L.or_dcb_sweeps_dim.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
+        L.or_heis_dcb_sweeps.argtypes = [i32, i32, p, dbl, u64, u32, u32, i64, i32, i32, i32, i32, p]
         L.or_ising_slab_phase.argtypes = [i32, i32, i32, p, dbl, u64, u32, u32, i32, p]
         _lib = L
     return _lib
@@ -216,6 +217,16 @@ def heis_init(dim, L, seed, lid):
 def heis_sweep(dim, L, s, beta, seed, lid, sweep, want_margin=False):
     margin = np.empty(nsites(dim, L), np.float64) if want_margin else None
     lib().or_heis_sweep(dim, L, _ptr(s), beta, seed, lid, sweep, _ptr(margin))
+    return margin
+
+
+def heis_dcb_sweeps(dim, L, s, beta, seed, lid, first_sweep, n_sweeps, T, k, symmetric=False,
+                    renorm_every=100, want_margin=False):
+    """Heisenberg sweeps in the double-checkerboard multi-hit order, in place;
+    returns the per-site smallest decision margin if asked."""
+    margin = np.empty(nsites(dim, L), np.float64) if want_margin else None
+    lib().or_heis_dcb_sweeps(dim, L, _ptr(s), beta, seed, lid, first_sweep, n_sweeps, T, k,
+                             int(bool(symmetric)), renorm_every, _ptr(margin))
     return margin
 
 

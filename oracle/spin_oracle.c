@@ -436,36 +436,44 @@ void or_heis_init(int dim, int L, double *s, uint64_t seed, uint32_t lattice_id)
   }
 }
 
-/* One checkerboard sweep of the Heisenberg model: each site proposes a new,
- * uniformly drawn direction n (words 0, 1 of the HEIS call with counter
- * x = j, colour c) and accepts it with the Metropolis rule using word 2:
- * dE = -(n - s_i) . h_i, h_i the sum of the neighbour spins; accept iff
- * dE <= 0 or u3 < exp(-beta dE).  `margin` (optional) receives, per site,
- * |u3 - exp(-beta dE)|: how far the decision was from flipping. */
+/* One Metropolis update of Heisenberg site i (of colour `colour`): the site
+ * proposes a new, uniformly drawn direction n (words 0, 1 of the HEIS call
+ * with counter x = j = i >> 1, colour c, sweep number `sweep`) and accepts
+ * it with the Metropolis rule using word 2: dE = -(n - s_i) . h_i, h_i the
+ * sum of the neighbour spins; accept iff dE <= 0 or u3 < exp(-beta dE).
+ * Returns |u3 - exp(-beta dE)|: how far the decision was from flipping. */
+static double or_heis_site(int dim, int L, double *s, int64_t i, int colour, double beta, uint64_t seed,
+                           uint32_t lattice_id, uint32_t sweep) {
+  double h[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < dim; ++d) {
+    int64_t up = or_neighbour(dim, L, i, d, +1);
+    int64_t dn = or_neighbour(dim, L, i, d, -1);
+    for (int k = 0; k < 3; ++k) h[k] += s[3 * up + k] + s[3 * dn + k];
+  }
+  uint32_t w[4];
+  or_call(seed, OR_TAG_HEIS, (uint32_t)colour, 0, lattice_id, sweep, (uint32_t)(i >> 1), w);
+  double nv[3];
+  or_unit_vector(or_uniform(w[0]), or_uniform(w[1]), nv);
+  double u3 = or_uniform(w[2]);
+  double dE = 0.0;
+  for (int k = 0; k < 3; ++k) dE -= (nv[k] - s[3 * i + k]) * h[k];
+  double boltz = exp(-beta * dE);
+  if (dE <= 0.0 || u3 < boltz)
+    for (int k = 0; k < 3; ++k) s[3 * i + k] = nv[k];
+  return fabs(u3 - boltz);
+}
+
+/* One checkerboard sweep of the Heisenberg model (Sec. 5): every colour-0
+ * site, then every colour-1 site, takes or_heis_site.  `margin` (optional)
+ * receives the per-site distance of the decision from flipping. */
 void or_heis_sweep(int dim, int L, double *s, double beta, uint64_t seed,
                    uint32_t lattice_id, uint32_t sweep, double *margin) {
   int64_t n = or_nsites(dim, L);
   for (int colour = 0; colour < 2; ++colour) {
     for (int64_t i = 0; i < n; ++i) {
       if (or_colour(dim, L, i) != colour) continue;
-      double h[3] = {0.0, 0.0, 0.0};
-      for (int d = 0; d < dim; ++d) {
-        int64_t up = or_neighbour(dim, L, i, d, +1);
-        int64_t dn = or_neighbour(dim, L, i, d, -1);
-        for (int k = 0; k < 3; ++k) h[k] += s[3 * up + k] + s[3 * dn + k];
-      }
-      uint32_t w[4];
-      or_call(seed, OR_TAG_HEIS, (uint32_t)colour, 0, lattice_id, sweep,
-              (uint32_t)(i >> 1), w);
-      double nv[3];
-      or_unit_vector(or_uniform(w[0]), or_uniform(w[1]), nv);
-      double u3 = or_uniform(w[2]);
-      double dE = 0.0;
-      for (int k = 0; k < 3; ++k) dE -= (nv[k] - s[3 * i + k]) * h[k];
-      double boltz = exp(-beta * dE);
-      if (margin) margin[i] = fabs(u3 - boltz);
-      if (dE <= 0.0 || u3 < boltz)
-        for (int k = 0; k < 3; ++k) s[3 * i + k] = nv[k];
+      const double mg = or_heis_site(dim, L, s, i, colour, beta, seed, lattice_id, sweep);
+      if (margin) margin[i] = mg;
     }
   }
 }
@@ -477,6 +485,44 @@ void or_heis_renormalise(int dim, int L, double *s) {
     double r = sqrt(s[3 * i] * s[3 * i] + s[3 * i + 1] * s[3 * i + 1] +
                     s[3 * i + 2] * s[3 * i + 2]);
     for (int k = 0; k < 3; ++k) s[3 * i + k] /= r;
+  }
+}
+
+/* The Heisenberg model in the double-checkerboard order with multi-hit
+ * updates (Sec. 5 uses it for its GPU code): tiles, compound moves, hit
+ * numbering and the symmetric variant exactly as in or_dcb_sweeps_dim, each
+ * update being or_heis_site.  After a compound move the spins are
+ * renormalised if the move passed a sweep count (1-based) that is a
+ * multiple of renorm_every (> 0), the rule of the plain sweeps.  `margin`
+ * (optional) receives per site the smallest distance of its decisions from
+ * flipping over the whole call. */
+void or_heis_dcb_sweeps(int dim, int L, double *s, double beta, uint64_t seed, uint32_t lattice_id,
+                        uint32_t first_sweep, int64_t n_sweeps, int T, int k, int symmetric, int renorm_every,
+                        double *margin) {
+  const int64_t n = or_nsites(dim, L);
+  if (margin)
+    for (int64_t i = 0; i < n; ++i) margin[i] = 1e300;
+  for (int64_t mv = 0; mv < n_sweeps / k; ++mv) {
+    const uint32_t M = first_sweep / (uint32_t)k + (uint32_t)mv;
+    const int first = (symmetric && (M & 1u)) ? 1 : 0;
+    for (int cc = 0; cc < 2; ++cc) {
+      const int coarse = first ^ cc;
+      for (int h = 0; h < k; ++h) {
+        const uint32_t sweep = M * (uint32_t)k + (uint32_t)h;
+        for (int colour = 0; colour < 2; ++colour) {
+          for (int64_t i = 0; i < n; ++i) {
+            const int x = (int)(i % L), y = (int)((i / L) % L), z = dim == 3 ? (int)(i / ((int64_t)L * L)) : 0;
+            if (((x / T + y / T + z / T) & 1) != coarse) continue;
+            if (or_colour(dim, L, i) != colour) continue;
+            const double mg = or_heis_site(dim, L, s, i, colour, beta, seed, lattice_id, sweep);
+            if (margin && mg < margin[i]) margin[i] = mg;
+          }
+        }
+      }
+    }
+    const uint64_t before = (uint64_t)M * (uint64_t)k, after = before + (uint64_t)k;
+    if (renorm_every > 0 && after / (uint64_t)renorm_every > before / (uint64_t)renorm_every)
+      or_heis_renormalise(dim, L, s);
   }
 }
 

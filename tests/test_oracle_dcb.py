@@ -254,3 +254,46 @@ def test_3d_long_run_matches_plain_sweeps():
     a, ea = binned_mean(E[200:])
     b, eb = binned_mean(E2[400:])
     assert abs(a - b) <= 4.5 * np.hypot(ea, eb), (a, ea, b, eb)
+
+
+# ------------------------------------------------------------------ Heisenberg (Sec. 5)
+@pytest.mark.parametrize("dim,L,T,k,symmetric,move", [(2, 16, 4, 3, True, 1), (2, 16, 8, 2, False, 0),
+                                                      (3, 8, 2, 2, True, 3)])
+def test_heis_dcb_infinite_temperature_keeps_the_last_proposal(dim, L, T, k, symmetric, move):
+    """At beta = 0 every proposal is accepted, so after compound move m every
+    site holds the proposal of its last hit, whatever the order: the state
+    equals one plain sweep with sweep number m k + k - 1 from any start."""
+    lid = oracle.lattice_id(0, 0, 0)
+    a = oracle.heis_init(dim, L, 4, lid)
+    b = oracle.heis_init(dim, L, 5, lid)  # a different start
+    oracle.heis_dcb_sweeps(dim, L, a, 0.0, 4, lid, move * k, k, T, k, symmetric, renorm_every=0)
+    oracle.heis_sweep(dim, L, b, 0.0, 4, lid, move * k + k - 1)
+    assert np.array_equal(a, b)
+
+
+def test_heis_dcb_long_run_matches_plain_sweeps():
+    """2D L = 8 with 4 x 4 tiles and k = 2: the double-checkerboard chain and
+    the plain chain sample the same <E> at beta = 1.1."""
+    dim, L, beta, k, T = 2, 8, 1.1, 2, 4
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.heis_init(dim, L, 7, lid)
+    n = 6000
+    E = np.empty(n)
+    for m in range(n):
+        oracle.heis_dcb_sweeps(dim, L, s, beta, 7, lid, m * k, k, T, k, True)
+        E[m] = oracle.heis_energy(dim, L, s)
+    s2 = oracle.heis_init(dim, L, 8, lid)
+    E2, _ = oracle.heis_run(dim, L, s2, beta, 8, lid, 0, 2 * n)
+    a, ea = binned_mean(E[300:] / L ** 2)
+    b, eb = binned_mean(E2[600:] / L ** 2)
+    assert abs(a - b) <= 4.5 * np.hypot(ea, eb), (a, ea, b, eb)
+
+
+def test_heis_dcb_renormalises_when_a_move_passes_a_multiple():
+    dim, L, k = 2, 8, 3
+    lid = oracle.lattice_id(0, 0, 0)
+    s = oracle.heis_init(dim, L, 9, lid) * 1.25  # off the unit sphere
+    oracle.heis_dcb_sweeps(dim, L, s, 0.7, 9, lid, 0, k, 4, k, renorm_every=4)  # counts 1..3: no multiple of 4
+    assert np.max(np.abs(np.linalg.norm(s, axis=1) - 1)) > 0.1
+    oracle.heis_dcb_sweeps(dim, L, s, 0.7, 9, lid, k, k, 4, k, renorm_every=4)  # counts 4..6 pass 4
+    assert np.max(np.abs(np.linalg.norm(s, axis=1) - 1)) < 1e-14

@@ -194,6 +194,18 @@ def side_configs(torch, sp, B, stream):
         b.record(stream)
         torch.cuda.synchronize()
         out[name + "_flips_per_ns"] = 20 * 4096 ** 2 / (a.elapsed_time(b) * 1e6)
+    # ... in the paper's own GPU order: double checkerboard, 8 x 8 tiles, k = 100
+    lat.set_update_order(B.SPIN_ORDER_DCB, 8, 100)
+    for variant, name in ((0, "heisenberg2d_L4096_dcb_T8_k100_fp32"), (2, "heisenberg2d_L4096_dcb_T8_k100_fp32_fast")):
+        lat.set_variant(variant)
+        lat.set_counters(0, 0)
+        B.spin_sweep(lat.h, None, [1.1], 100, lat.seed)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, [1.1], 100, lat.seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_flips_per_ns"] = 100 * 4096 ** 2 / (a.elapsed_time(b) * 1e6)
     lat.close()
     betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
     ea = sp.Lattice(B.SPIN_EA, 3, 16, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=12)
@@ -630,6 +642,14 @@ def run_case(name):
     elif name == "pipes":
         print(json.dumps({"case": name, **pipe_rates(torch, B, stream)}), flush=True)
         return
+    elif name == "heis_dcb":
+        lat = sp.Lattice(B.SPIN_HEISENBERG, 2, 4096, B.SPIN_F32X4, seed=13)
+        lat.set_update_order(B.SPIN_ORDER_DCB, 8, 100)
+        B.spin_sweep(lat.h, None, [1.1], 100, lat.seed)
+        a.record(stream)
+        B.spin_sweep(lat.h, None, [1.1], 100, lat.seed)
+        b.record(stream)
+        flips = 100 * 4096 ** 2
     elif name == "rng":
         threads, calls = 152 * 2048, 256
         out = torch.empty(threads, dtype=torch.int32, device="cuda")
@@ -653,7 +673,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, rng, pipes, uneven, ising_pt, dcb, ising3d)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -363,7 +363,9 @@ int spin_set_msc_width(spin_lattice *lat, int32_t width);
  * The double-checkerboard orders take Ising ferromagnets in the int8
  * layout: 2D with tile in {8, 16, 32, 64, 128}, or 3D (Sec. 4: tile^3
  * cubes, coarse colour (x / tile + y / tile + z / tile) mod 2) with tile in
- * {8, 16}; tile divides L with L / tile even, and hits >= 1; spin_sweep then counts sweeps as updates per site and needs
+ * {8, 16}; and the 2D Heisenberg model (Sec. 5) with tile in {8, 16, 32},
+ * renormalised after every compound move that passes a sweep count
+ * divisible by 100; tile divides L with L / tile even, and hits >= 1; spin_sweep then counts sweeps as updates per site and needs
  * n_sweeps and the handle's sweep count to be multiples of hits (so must
  * spin_run's measure_every and pt_every).  Such handles cannot join a
  * batched launch.  tile and hits are ignored for SPIN_ORDER_CHECKERBOARD. */

@@ -213,7 +213,11 @@ cudaError_t launch_tiles3(spin_lattice *h, int coarse, uint32_t sweep0) {
 }  // namespace
 
 bool dcb_supported(const spin_lattice *h, int tile) {
-  if (h->d.model != SPIN_ISING || h->d.layout != SPIN_I8 || h->n_lat > 65535) return false;
+  if (h->n_lat > 65535) return false;
+  if (h->d.model == SPIN_HEISENBERG)  // 2D, T x T tiles of float4 in shared memory
+    return h->d.dim == 2 && (tile == 8 || tile == 16 || tile == 32) && h->g.L % tile == 0 &&
+           ((h->g.L / tile) & 1) == 0;
+  if (h->d.model != SPIN_ISING || h->d.layout != SPIN_I8) return false;
   if (h->d.dim == 2) {
     if (tile != 8 && tile != 16 && tile != 32 && tile != 64 && tile != 128) return false;
   } else if (h->d.dim == 3) {
@@ -235,7 +239,9 @@ cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps) {
       const int coarse = first ^ cc;
       const uint32_t sweep0 = M * (uint32_t)k;
       cudaError_t e;
-      if (h->g.dim == 3) {
+      if (h->d.model == SPIN_HEISENBERG) {
+        e = launch_heis_dcb_tiles(h, coarse, sweep0);
+      } else if (h->g.dim == 3) {
         e = h->order_tile == 8 ? launch_tiles3<8>(h, coarse, sweep0) : launch_tiles3<16>(h, coarse, sweep0);
       } else {
         switch (h->order_tile) {
@@ -246,6 +252,13 @@ cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps) {
           default: e = launch_tiles<128>(h, coarse, sweep0); break;
         }
       }
+      if (e != cudaSuccess) return e;
+    }
+    // Heisenberg: renormalise after a compound move that passed a sweep
+    // count (1-based) divisible by 100, the rule of the plain sweeps
+    const uint64_t before = (uint64_t)M * (uint64_t)k, after = before + (uint64_t)k;
+    if (h->d.model == SPIN_HEISENBERG && after / 100u > before / 100u) {
+      const cudaError_t e = launch_heis_renorm(h);
       if (e != cudaSuccess) return e;
     }
   }

@@ -92,6 +92,102 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
   }
 }
 
+// Double checkerboard with multi-hit updates for the 2D model (Sec. 5 runs
+// its GPU code this way; tiles and hits as Sec. 3.2, 3.4): one launch takes
+// every T x T tile of one coarse colour into shared memory with a one-site
+// halo (from tiles of the other colour, unchanged by this launch) and gives
+// it k hits, each updating the fine colour-0 and then the fine colour-1
+// sites; hit h of compound move m draws with sweep number m k + h.  Each
+// update is the arithmetic of heis_phase_kernel, in the same order.
+template <int kT, bool kFast>
+__global__ void __launch_bounds__(256) heis_dcb2_kernel(float4 *__restrict__ s, Geom g, int coarse,
+                                                        uint32_t sweep0, int k, const uint32_t *__restrict__ thr,
+                                                        RoundKeys rk) {
+  constexpr int kSide = kT + 2;
+  constexpr int kTileV = kSide * kSide;   // float4 per shared tile
+  constexpr int kPairs = kT * kT / 2;     // sites per fine colour per tile
+  constexpr int kTPT = kPairs < 256 ? kPairs : 256;
+  constexpr int kTiles = 256 / kTPT;
+  constexpr int kPer = kPairs / kTPT;
+  __shared__ float4 sm[kTiles * kTileV];
+  const int tsub = threadIdx.x / kTPT, tid = threadIdx.x - tsub * kTPT;
+  float4 *sw = sm + tsub * kTileV;
+  const int L = g.L, B = L / kT, half = B >> 1;
+  const int t = blockIdx.x * kTiles + tsub;
+  const bool active = t < B * half;
+  const int by = t / half, bx = 2 * (t % half) + ((by + coarse) & 1);
+  const uint32_t lat = blockIdx.y;
+  float4 *sl = s + (int64_t)lat * L * L;
+  const int x0 = bx * kT, y0 = by * kT;
+  if (active)
+    for (int q = tid; q < kTileV; q += kTPT) {
+      const int ry = q / kSide - 1, rx = q % kSide - 1;
+      const int gy = (y0 + ry + L) % L, gx = (x0 + rx + L) % L;
+      sw[q] = sl[(int64_t)gy * L + gx];
+    }
+  __syncthreads();
+  const uint32_t slot = slot_of32(g, lat), lid = lattice_id32(g, lat);
+  const float beta = __uint_as_float(__ldg(thr + 4 * slot));
+  PhiloxX1 pre[kPer][2];
+  if (active)
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int q = tid + i * kTPT, ty = q / (kT / 2), xh = q % (kT / 2);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int tx = 2 * xh + ((c + y0 + ty) & 1);
+        const uint32_t j = (uint32_t)(((int64_t)(y0 + ty) * L + x0 + tx) >> 1);
+        pre[i][c] = philox_x1_setup(j, lid, ctr_w(TAG_HEIS, (uint32_t)c, 0), rk);
+      }
+    }
+  for (int h = 0; h < k; ++h) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (active)
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          const int q = tid + i * kTPT, ty = q / (kT / 2), xh = q % (kT / 2);
+          const int tx = 2 * xh + ((c + y0 + ty) & 1);
+          const int at = (ty + 1) * kSide + tx + 1;
+          const float4 a = sw[at + 1], b = sw[at - 1], cc = sw[at + kSide], d = sw[at - kSide];
+          const float4 si = sw[at];
+          const uint4 w = philox_x1(pre[i][c], sweep0 + (uint32_t)h, rk);
+          const float hx = a.x + b.x + cc.x + d.x;
+          const float hy = a.y + b.y + cc.y + d.y;
+          const float hz = a.z + b.z + cc.z + d.z;
+          const float4 n = unit_vector<kFast>(w.x, w.y);
+          const float u3 = uniform24(w.z);
+          const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
+          const float boltz = kFast ? __expf(-beta * dE) : expf(-beta * dE);
+          if (dE <= 0.0f || u3 < boltz) sw[at] = n;
+        }
+      __syncthreads();
+    }
+  }
+  if (active)
+    for (int q = tid; q < kT * kT; q += kTPT) {
+      const int ty = q / kT, tx = q % kT;
+      sl[(int64_t)(y0 + ty) * L + x0 + tx] = sw[(ty + 1) * kSide + tx + 1];
+    }
+}
+
+template <int kT>
+cudaError_t launch_heis_tiles(spin_lattice *h, int coarse, uint32_t sweep0) {
+  constexpr int kPairs = kT * kT / 2;
+  constexpr int kTiles = kPairs < 256 ? 256 / kPairs : 1;
+  const int B = h->g.L / kT;
+  const int n_tiles = B * B / 2;
+  dim3 grid((unsigned)((n_tiles + kTiles - 1) / kTiles), (unsigned)h->n_lat);
+  const RoundKeys rk = make_round_keys(h->d.seed);
+  if (h->variant == 2)
+    heis_dcb2_kernel<kT, true><<<grid, 256, 0, h->stream>>>((float4 *)h->spins, h->g, coarse, sweep0,
+                                                             h->order_hits, h->d_thr, rk);
+  else
+    heis_dcb2_kernel<kT, false><<<grid, 256, 0, h->stream>>>((float4 *)h->spins, h->g, coarse, sweep0,
+                                                              h->order_hits, h->d_thr, rk);
+  return cudaGetLastError();
+}
+
 // s <- s / |s| with IEEE sqrt and division.
 __global__ void heis_renorm_kernel(float4 *__restrict__ s, int64_t total) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
@@ -142,6 +238,22 @@ cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// One double-checkerboard launch of the 2D model: the tiles of coarse
+// colour `coarse` through the handle's hits, starting at sweep0.
+cudaError_t launch_heis_dcb_tiles(spin_lattice *h, int coarse, uint32_t sweep0) {
+  switch (h->order_tile) {
+    case 8: return launch_heis_tiles<8>(h, coarse, sweep0);
+    case 16: return launch_heis_tiles<16>(h, coarse, sweep0);
+    default: return launch_heis_tiles<32>(h, coarse, sweep0);
+  }
+}
+
+cudaError_t launch_heis_renorm(spin_lattice *h) {
+  heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>((float4 *)h->spins,
+                                                                           h->n_lat * h->g.N);
+  return cudaGetLastError();
 }
 
 }  // namespace spin

@@ -113,6 +113,10 @@ cudaError_t launch_rng_probe(uint64_t seed, uint32_t threads, uint32_t calls, ui
 int launch_pipe_probe(int op, int blocks_per_sm, uint32_t iters, long long *clocks, uint32_t *sink,
                       int *sms, cudaStream_t s);
 
+// heis.cu (double checkerboard of the 2D Heisenberg model)
+cudaError_t launch_heis_dcb_tiles(spin_lattice *h, int coarse, uint32_t sweep0);
+cudaError_t launch_heis_renorm(spin_lattice *h);
+
 // dcb.cu
 bool dcb_supported(const spin_lattice *h, int tile);
 cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps);

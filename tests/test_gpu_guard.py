@@ -115,6 +115,8 @@ CASES = [
     ("ea3d_coded", (B.SPIN_EA, 3, 8, B.SPIN_MSC1), dict(n_real=64, n_temps=5, n_sets=2), None, None),
     ("heis3d", (B.SPIN_HEISENBERG, 3, 8, B.SPIN_F32X4), dict(n_temps=2), 2, None),
     ("heis2d", (B.SPIN_HEISENBERG, 2, 18, B.SPIN_F32X4), dict(n_temps=2), 0, None),
+    ("heis2d_dcb8", (B.SPIN_HEISENBERG, 2, 32, B.SPIN_F32X4), dict(n_temps=2), 2, (B.SPIN_ORDER_DCB, 8, 2)),
+    ("heis2d_dcb32", (B.SPIN_HEISENBERG, 2, 64, B.SPIN_F32X4), dict(), 0, (B.SPIN_ORDER_DCB_SYMMETRIC, 32, 1)),
 ]
 
 

@@ -480,44 +480,59 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the API with host buffers: every step copies the
     # coded lattices in from pinned memory and the lattices and observables
-    # out.  Two handles on two streams take alternate steps, so that the
-    # copies of one step (copy engines) overlap the sweeps of the other (SMs);
-    # every step's copies are inside the timed region.
+    # out, all inside the timed region.  Two handles (two device buffers)
+    # take alternate steps; their sweeps run in order on one compute stream,
+    # the host-to-device and device-to-host copies on two copy streams, tied
+    # by events: the copy-in of a buffer waits for the copy-out of its
+    # previous step, its sweeps wait for the copy-in, its copy-out waits for
+    # the sweeps.  The copies of one step thus overlap the sweeps of the
+    # other without the two handles' kernels competing for the SMs.
     host_in = torch.empty(lat.spins.numel(), dtype=lat.spins.dtype).pin_memory()
     host_in.copy_(lat.spins.cpu())
     spin_bytes = lat.spins.numel() * lat.spins.element_size()
     lat.close()
+    comp, cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     pipes = []
     for k in range(2):
-        st = torch.cuda.Stream(dev)
-        h = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, n_temps=n_lat, seed=1 + rank, stream=st)
+        h = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_MSC1, n_temps=n_lat, seed=1 + rank, stream=comp)
         Ek = torch.empty(n_lat, dtype=torch.int64, device=dev)
         Mk = torch.empty(n_lat, dtype=torch.int64, device=dev)
-        pipes.append((st, h, Ek, Mk, torch.empty_like(host_in).pin_memory(),
-                      torch.empty(2 * n_lat, dtype=torch.int64).pin_memory()))
+        pipes.append(dict(h=h, E=Ek, M=Mk, out=torch.empty_like(host_in).pin_memory(),
+                          obs=torch.empty(2 * n_lat, dtype=torch.int64).pin_memory(),
+                          copied_in=torch.cuda.Event(), swept=torch.cuda.Event(), copied_out=torch.cuda.Event()))
     torch.cuda.synchronize()
+    for p in pipes:
+        p["copied_out"].record(cout)
     e2e_count = [0]
 
     def e2e_step():
-        st, h, Ek, Mk, out, obs = pipes[e2e_count[0] % 2]
+        p = pipes[e2e_count[0] % 2]
         e2e_count[0] += 1
-        with torch.cuda.stream(st):
+        h = p["h"]
+        cin.wait_event(p["copied_out"])  # the buffer's previous copy-out is done
+        with torch.cuda.stream(cin):
             h.spins.copy_(host_in, non_blocking=True)
-            B.spin_sweep(h.h, None, BETAS, S, h.seed)
-            B.spin_measure(h.h, None, Ek, Mk)
-            out.copy_(h.spins, non_blocking=True)
-            obs[:n_lat].copy_(Ek, non_blocking=True)
-            obs[n_lat:].copy_(Mk, non_blocking=True)
+        p["copied_in"].record(cin)
+        comp.wait_event(p["copied_in"])
+        B.spin_sweep(h.h, None, BETAS, S, h.seed)
+        B.spin_measure(h.h, None, p["E"], p["M"])
+        p["swept"].record(comp)
+        cout.wait_event(p["swept"])
+        with torch.cuda.stream(cout):
+            p["out"].copy_(h.spins, non_blocking=True)
+            p["obs"][:n_lat].copy_(p["E"], non_blocking=True)
+            p["obs"][n_lat:].copy_(p["M"], non_blocking=True)
+        p["copied_out"].record(cout)
 
     def e2e_timed(k):
         barrier()
         a, b = _events(torch)
         a.record(stream)
-        for st, *_ in pipes:
+        for st in (comp, cin, cout):
             st.wait_stream(stream)
         for _ in range(k):
             e2e_step()
-        for st, *_ in pipes:
+        for st in (comp, cin, cout):
             stream.wait_stream(st)
         b.record(stream)
         barrier()
@@ -527,8 +542,8 @@ def run_gpu(args, rank, world, local_rank):
         e2e_step()
     e2e_ms = max_over_ranks(e2e_timed(args.steps))
     e2e_value = world * args.steps * flips_per_step / (e2e_ms * 1e6)
-    for _, h, *_ in pipes:
-        h.close()
+    for p in pipes:
+        p["h"].close()
 
     # the int8 layout of the same workload (fused out-of-place sweep)
     lat8 = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=n_lat, seed=1 + rank)
@@ -561,8 +576,9 @@ def run_gpu(args, rank, world, local_rank):
                    "sweeps_per_step": S, "layout": "1-bit synchronous multi-spin coding",
                    "i8_flips_per_ns": i8_value,
                    "l2": "coded lattices (96 MiB) fit in L2; int8 lattices (768 MiB) exceed it",
-            "e2e_form": "two handles on two streams take alternate steps; each step copies its 3 lattices "
-                        "in from pinned host memory and lattices + E, M out",
+                   "e2e_form": "two handles take alternate steps, their sweeps in order on one compute stream, "
+                               "copies on two copy streams ordered by events; each step copies its 3 lattices "
+                               "in from pinned host memory and lattices + E, M out",
                    "parallelism": f"replicas x{world}", **side},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s",
                      "frac": achieved / peak, "traffic": traffic,

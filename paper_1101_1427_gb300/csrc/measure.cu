@@ -19,6 +19,8 @@ __device__ __forceinline__ void add_ll(long long *p, long long v) {
 // atomic accumulation order does not matter.
 __global__ void measure_i8_kernel(const int8_t *__restrict__ s, const int8_t *__restrict__ J,
                                   Geom g, long long *__restrict__ E, long long *__restrict__ M) {
+  griddep_wait();
+  griddep_release();
   const int64_t lat = blockIdx.y;
   const int8_t *sl = s + lat * g.N;
   const int8_t *Jr = J ? J + (lat % g.n_real) * (int64_t)g.dim * g.N : nullptr;
@@ -53,6 +55,8 @@ __global__ void measure_i8_kernel(const int8_t *__restrict__ s, const int8_t *__
 // M = N - 2 n_down.
 __global__ void measure2d_i8_kernel(const int8_t *__restrict__ s, int L, long long *__restrict__ E,
                                     long long *__restrict__ M) {
+  griddep_wait();
+  griddep_release();
   const int64_t lat = blockIdx.y;
   const int8_t *sl = s + lat * (int64_t)L * L;
   const uint32_t segs = (uint32_t)(L >> 4);
@@ -82,6 +86,8 @@ __global__ void measure2d_i8_kernel(const int8_t *__restrict__ s, int L, long lo
 }
 
 __global__ void add_per_lattice_kernel(long long *__restrict__ v, int64_t n, long long c) {
+  griddep_wait();
+  griddep_release();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     v[k] += c;
@@ -89,6 +95,8 @@ __global__ void add_per_lattice_kernel(long long *__restrict__ v, int64_t n, lon
 
 // q_{t,r} = sum_i s_i^(0) s_i^(1) between sets 0 and 1.
 __global__ void overlap_i8_kernel(const int8_t *__restrict__ s, Geom g, long long *__restrict__ Q) {
+  griddep_wait();
+  griddep_release();
   const int64_t tr = blockIdx.y;  // t * n_real + r
   const int64_t set_stride = (int64_t)g.n_temps * g.n_real * g.N;
   const int8_t *s0 = s + tr * g.N, *s1 = s0 + set_stride;
@@ -157,6 +165,8 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
                                                           long long *__restrict__ E,
                                                           long long *__restrict__ M,
                                                           long long *__restrict__ Q) {
+  griddep_wait();
+  griddep_release();
   __shared__ uint32_t sm[8][kWarp];
   const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
   const uint32_t wl = blockIdx.y;
@@ -219,15 +229,22 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   const int64_t lat = ((int64_t)a * T + t) * g.n_real + 32 * grp + lane;
   // E = 2 unsat - 3N, M = N - 2 down, Q = N - 2 diff: block 0 adds the constants
   const long long n0 = blockIdx.x == 0 ? (long long)N : 0;
+  // one block per word-lattice stores its counts; several add them to
+  // outputs the host has zeroed
+  const bool direct = gridDim.x == 1;
+  auto put = [direct](long long *p, long long v) {
+    if (direct) *p = v;
+    else add_ll(p, v);
+  };
   const long long unsat = vc_block_total(CE, sm);
-  if (threadIdx.x < 32 && E) add_ll(&E[lat], 2 * unsat - 3 * n0);
+  if (threadIdx.x < 32 && E) put(&E[lat], 2 * unsat - 3 * n0);
   if (M) {
     const long long down = vc_block_total(CM, sm);
-    if (threadIdx.x < 32) add_ll(&M[lat], n0 - 2 * down);
+    if (threadIdx.x < 32) put(&M[lat], n0 - 2 * down);
   }
   if (do_q) {
     const long long diff = vc_block_total(CQ, sm);
-    if (threadIdx.x < 32) add_ll(&Q[(int64_t)t * g.n_real + 32 * grp + lane], n0 - 2 * diff);
+    if (threadIdx.x < 32) put(&Q[(int64_t)t * g.n_real + 32 * grp + lane], n0 - 2 * diff);
   }
 }
 
@@ -239,6 +256,8 @@ constexpr int kHeisBlocks = 64;
 
 __global__ void measure_heis_kernel(const float4 *__restrict__ s, Geom g,
                                     double *__restrict__ partial) {
+  griddep_wait();
+  griddep_release();
   const int64_t lat = blockIdx.y;
   const float4 *sl = s + lat * g.N;
   const int L = g.L;
@@ -286,6 +305,8 @@ __global__ void measure_heis_kernel(const float4 *__restrict__ s, Geom g,
 
 __global__ void finish_heis_kernel(const double *__restrict__ partial, int64_t n_lat, int nb,
                                    double *__restrict__ Ef, double *__restrict__ Mf) {
+  griddep_wait();
+  griddep_release();
   const int64_t lat = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (lat >= n_lat) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -308,6 +329,8 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
                                  const uint32_t *__restrict__ tab, const int32_t *__restrict__ off,
                                  const int32_t *__restrict__ len, RoundKeys rk, uint32_t step,
                                  uint8_t *__restrict__ decision, long long *__restrict__ accepted) {
+  griddep_wait();
+  griddep_release();
   const int parity = (int)(step & 1u);
   const int n_pairs = (g.n_temps - parity) / 2;  // pairs (t, t+1), t = parity + 2k
   const int64_t total = (int64_t)g.n_sets * n_pairs * g.n_real;
@@ -347,6 +370,8 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
 // otherwise (e.g. 6^3 = 216-byte int8 lattices).
 __global__ void pt_swap_bytes_kernel(uint8_t *__restrict__ s, const uint8_t *__restrict__ decision,
                                      Geom g, int parity, int64_t lat_bytes) {
+  griddep_wait();
+  griddep_release();
   const int64_t lat0 = blockIdx.y;
   const int t = (int)slot_of32(g, (uint32_t)lat0);
   if (((t - parity) & 1) || t + 1 >= g.n_temps || !decision[lat0]) return;
@@ -374,6 +399,8 @@ __global__ void pt_swap_bytes_kernel(uint8_t *__restrict__ s, const uint8_t *__r
 // multiple of 8 and every word-lattice starts 32-byte aligned).
 __global__ void pt_swap_msc_kernel(uint32_t *__restrict__ w, const uint8_t *__restrict__ decision,
                                    Geom g, int parity) {
+  griddep_wait();
+  griddep_release();
   const int G = g.n_real / 32;
   const int64_t wl = blockIdx.y;  // (a, grp, t)
   const int t = (int)(wl % g.n_temps);
@@ -409,41 +436,51 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
   if (h->d.model == SPIN_HEISENBERG) {
     if (!Ef && !Mf) return cudaSuccess;
     double *partial = (double *)h->d_scratch64;
-    measure_heis_kernel<<<dim3(kHeisBlocks, (unsigned)nl), 256, 0, st>>>((const float4 *)h->spins,
-                                                                         g, partial);
-    finish_heis_kernel<<<grid_for(nl, 128), 128, 0, st>>>(partial, nl, kHeisBlocks, Ef, Mf);
-    return cudaGetLastError();
+    cudaError_t e = launch_dependent(measure_heis_kernel, dim3(kHeisBlocks, (unsigned)nl), dim3(256), 0, st,
+                                     (const float4 *)h->spins, g, partial);
+    if (e != cudaSuccess) return e;
+    return launch_dependent(finish_heis_kernel, dim3(grid_for(nl, 128)), dim3(128), 0, st,
+                            (const double *)partial, nl, kHeisBlocks, Ef, Mf);
   }
   if (h->d.layout == SPIN_MSC1 && h->d.model == SPIN_ISING) {
     if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
     return launch_measure_msc2d(h, E, M);
   }
-  if (E) cudaMemsetAsync(E, 0, sizeof(int64_t) * nl, st);
-  if (M) cudaMemsetAsync(M, 0, sizeof(int64_t) * nl, st);
-  if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
+  // EA coded words: blocks per word-lattice (at most 16 sites per thread:
+  // 3 * 16 * 256 * 2^k stays inside the 16 planes); with one block per
+  // word-lattice the counts are stored, not added, and need no zeroing
+  const unsigned gx = (unsigned)((g.N + 256 * 16 - 1) / (256 * 16));
+  const bool coded_direct = h->d.layout == SPIN_MSC1 && gx == 1;
+  if (!coded_direct) {
+    if (E) cudaMemsetAsync(E, 0, sizeof(int64_t) * nl, st);
+    if (M) cudaMemsetAsync(M, 0, sizeof(int64_t) * nl, st);
+    if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
+  }
+  cudaError_t e = cudaSuccess;
   if (h->d.layout == SPIN_I8) {
     if ((E || M) && !J && g.dim == 2 && g.L % 16 == 0) {
       const int64_t segs = (int64_t)g.L * (g.L / 16);
-      measure2d_i8_kernel<<<dim3(capped(segs, 2048), (unsigned)nl), 256, 0, st>>>(
-          (const int8_t *)h->spins, g.L, (long long *)E, (long long *)M);
-      if (E) add_per_lattice_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)E, nl, -2 * (long long)g.N);
-      if (M) add_per_lattice_kernel<<<capped(nl, 4096), 256, 0, st>>>((long long *)M, nl, (long long)g.N);
-    } else if (E || M)
-      measure_i8_kernel<<<dim3(capped(g.N, 1024), (unsigned)nl), 256, 0, st>>>(
-          (const int8_t *)h->spins, (const int8_t *)J, g, (long long *)E, (long long *)M);
-    if (Q && g.n_sets >= 2)
-      overlap_i8_kernel<<<dim3(capped(g.N, 1024), (unsigned)(g.n_temps * g.n_real)), 256, 0, st>>>(
-          (const int8_t *)h->spins, g, (long long *)Q);
-    return cudaGetLastError();
+      e = launch_dependent(measure2d_i8_kernel, dim3(capped(segs, 2048), (unsigned)nl), dim3(256), 0, st,
+                           (const int8_t *)h->spins, g.L, (long long *)E, (long long *)M);
+      if (e == cudaSuccess && E)
+        e = launch_dependent(add_per_lattice_kernel, dim3(capped(nl, 4096)), dim3(256), 0, st, (long long *)E, nl,
+                             -2 * (long long)g.N);
+      if (e == cudaSuccess && M)
+        e = launch_dependent(add_per_lattice_kernel, dim3(capped(nl, 4096)), dim3(256), 0, st, (long long *)M, nl,
+                             (long long)g.N);
+    } else if (E || M) {
+      e = launch_dependent(measure_i8_kernel, dim3(capped(g.N, 1024), (unsigned)nl), dim3(256), 0, st,
+                           (const int8_t *)h->spins, (const int8_t *)J, g, (long long *)E, (long long *)M);
+    }
+    if (e == cudaSuccess && Q && g.n_sets >= 2)
+      e = launch_dependent(overlap_i8_kernel, dim3(capped(g.N, 1024), (unsigned)(g.n_temps * g.n_real)),
+                           dim3(256), 0, st, (const int8_t *)h->spins, g, (long long *)Q);
+    return e;
   }
-  // EA coded words
   const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-  // at most 16 sites per thread: 3 * 16 * 256 * 2^k stays inside the 16 planes
-  unsigned gx = (unsigned)((g.N + 256 * 16 - 1) / (256 * 16));
-  measure_msc_kernel<<<dim3(gx, (unsigned)n_wl), 256, 0, st>>>(
-      (const uint32_t *)h->spins, (const uint32_t *)J, g, (long long *)E, (long long *)M,
-      (g.n_sets >= 2) ? (long long *)Q : nullptr);
-  return cudaGetLastError();
+  return launch_dependent(measure_msc_kernel, dim3(gx, (unsigned)n_wl), dim3(256), 0, st, (const uint32_t *)h->spins,
+                          (const uint32_t *)J, g, (long long *)E, (long long *)M,
+                          (g.n_sets >= 2) ? (long long *)Q : nullptr);
 }
 
 cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, const int64_t *energies) {
@@ -460,20 +497,23 @@ cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, co
   uint8_t *decision = (uint8_t *)(h->d_energy + 2 * h->n_lat);
   if (n_pairs <= 0) return cudaSuccess;
   const int64_t total = (int64_t)g.n_sets * n_pairs * g.n_real;
-  pt_decide_kernel<<<grid_for(total, 256), 256, 0, st>>>(
-      (const long long *)energies, g, h->d_pt_dbeta, h->d_pt_thr, h->d_pt_off, h->d_pt_len,
-      make_round_keys(h->d.seed), step, decision, (long long *)accepted);
+  cudaError_t e = launch_dependent(pt_decide_kernel, dim3(grid_for(total, 256)), dim3(256), 0, st,
+                                   (const long long *)energies, g, (const double *)h->d_pt_dbeta,
+                                   (const uint32_t *)h->d_pt_thr, (const int32_t *)h->d_pt_off,
+                                   (const int32_t *)h->d_pt_len, make_round_keys(h->d.seed), step, decision,
+                                   (long long *)accepted);
+  if (e != cudaSuccess) return e;
   if (h->d.layout == SPIN_MSC1 && h->d.model == SPIN_EA) {
     const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-    pt_swap_msc_kernel<<<dim3(capped(g.N / 4, 64), (unsigned)n_wl), 256, 0, st>>>(
-        (uint32_t *)h->spins, decision, g, parity);
+    return launch_dependent(pt_swap_msc_kernel, dim3(capped(g.N / 4, 64), (unsigned)n_wl), dim3(256), 0, st,
+                            (uint32_t *)h->spins, (const uint8_t *)decision, g, parity);
   } else {
     int64_t lat_bytes = g.N;  // int8
     if (h->d.layout == SPIN_MSC1) lat_bytes = g.N / 8;
     if (h->d.layout == SPIN_F32X4) lat_bytes = g.N * 16;
     const int64_t units = (lat_bytes & 15) == 0 ? lat_bytes / 16 : lat_bytes;
-    pt_swap_bytes_kernel<<<dim3(capped(units, 1024), (unsigned)h->n_lat), 256, 0, st>>>(
-        (uint8_t *)h->spins, decision, g, parity, lat_bytes);
+    return launch_dependent(pt_swap_bytes_kernel, dim3(capped(units, 1024), (unsigned)h->n_lat), dim3(256), 0, st,
+                            (uint8_t *)h->spins, (const uint8_t *)decision, g, parity, lat_bytes);
   }
   return cudaGetLastError();
 }

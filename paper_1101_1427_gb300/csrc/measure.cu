@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
   const uint32_t wl = blockIdx.y;
   const uint32_t t = wl % T, grp = (wl / T) % G, a = wl / (T * G);
-  const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N;
+  const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N;
   const uint32_t *s = w + (size_t)wl * N;
   const uint32_t *Jg = J + (size_t)grp * 3 * N;
   const bool do_q = Q && a == 0 && g.n_sets >= 2;

@@ -11,10 +11,6 @@
 namespace spin {
 namespace {
 
-__host__ __device__ inline int64_t word_lattice(const Geom &g, int a, int grp, int t) {
-  return ((int64_t)a * (g.n_real / 32) + grp) * g.n_temps + t;
-}
-
 __global__ void init_msc_kernel(uint32_t *__restrict__ w, Geom g, RoundKeys rk) {
   const int G = g.n_real / 32;
   const int64_t quads = (g.N + 3) / 4;

@@ -267,6 +267,20 @@ def side_configs(torch, sp, B, stream):
     torch.cuda.synchronize()
     out["ea_L16_w32_sweep_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
     ea.close()
+    # the paper's own multi-spin-coding benchmark is the 2D glass, L = 16 (Sec. 6):
+    # 16384 realisations x 32 temperatures x 2 sets (2^28 spins), sweeps only
+    ea2 = sp.Lattice(B.SPIN_EA, 2, 16, B.SPIN_MSC1, n_real=16384, n_temps=32, n_sets=2, seed=14)
+    flips2 = n * 16 ** 2 * 16384 * 32 * 2
+    for width in (32, 64):
+        ea2.set_msc_width(width)
+        B.spin_run(ea2.h, ea2.couplings, betas, 2, 0, 0, None, None, None, None, None, None)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_run(ea2.h, ea2.couplings, betas, n, 0, 0, None, None, None, None, None, None)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"ea2d_L16_w{width}_sweep_flips_per_ns"] = flips2 / (a.elapsed_time(b) * 1e6)
+    ea2.close()
     out.update(uneven_batch(torch, sp, B, stream))
     out.update(ising_pt(torch, sp, B, stream))
     out.update(dcb(torch, sp, B, stream))

@@ -59,9 +59,9 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *  SPIN_I8     int8 +-1, [n_sets][n_temps][n_real][L^dim].  Ising (2D, 3D) and
  *              EA (3D, one spin per byte: the per-realisation form).
  *  SPIN_MSC1   1 bit per spin, bit set <=> s = -1, uint32 words.
- *              EA (3D, asynchronous coding, Sec. 6): word-lattices
+ *              EA (2D or 3D, asynchronous coding, Sec. 6): word-lattices
  *              [n_sets][n_real/32][n_temps], each stored colour-split as
- *              [2 colours][L^3/2] (site i of colour c at c L^3/2 + (i >> 1));
+ *              [2 colours][L^dim/2] (site i of colour c at c L^dim/2 + (i >> 1));
  *              bit b of a word is realisation 32 g + b.
  *              Ising 2D ferromagnet (synchronous coding): per lattice
  *              [2 colours][L rows][L/64 words]; in row y the colour-c sites
@@ -71,15 +71,15 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *              (Heisenberg, 2D as in Sec. 5 or 3D).
  * Couplings (EA only; NULL for the ferromagnet, J = 1):
  *  SPIN_I8     int8 +-1, [n_real][dim][L^dim]: bond (i, i + e_d).
- *  SPIN_MSC1   uint32 [n_real/32][dim][2 colours][L^3/2] (bond (i, i + e_d)
- *              at d L^3 + c(i) L^3/2 + (i >> 1)), bit b set <=> J = -1 for
+ *  SPIN_MSC1   uint32 [n_real/32][dim][2 colours][L^dim/2] (bond (i, i + e_d)
+ *              at d L^dim + c(i) L^dim/2 + (i >> 1)), bit b set <=> J = -1 for
  *              realisation 32 g + b.
  * All device buffers must be 16-byte aligned. */
 typedef enum { SPIN_I8 = 0, SPIN_MSC1 = 1, SPIN_F32X4 = 2 } spin_layout;
 
 typedef struct {
   int32_t model;     /* spin_model                                             */
-  int32_t dim;       /* 2 or 3 (coded EA: 3)                                   */
+  int32_t dim;       /* 2 or 3                                                 */
   int32_t L;         /* edge length: even, >= 4                                */
   int32_t layout;    /* spin_layout                                            */
   int32_t n_real;    /* lattices per (set, slot): EA disorder realisations     */

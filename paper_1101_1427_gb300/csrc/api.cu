@@ -120,7 +120,8 @@ int validate_desc(const spin_desc *d) {
       if (d->layout == SPIN_I8)
         return ((d->dim == 2 || d->dim == 3) && d->n_real <= 131072) ? SPIN_OK : SPIN_EINVAL;
       if (d->layout == SPIN_MSC1)
-        return (d->dim == 3 && d->n_real % 32 == 0 && d->n_real / 32 < 4096) ? SPIN_OK : SPIN_EINVAL;
+        return ((d->dim == 2 || d->dim == 3) && d->n_real % 32 == 0 && d->n_real / 32 < 4096) ? SPIN_OK
+                                                                                               : SPIN_EINVAL;
       return SPIN_EINVAL;
     case SPIN_HEISENBERG:
       return ((d->dim == 2 || d->dim == 3) && d->layout == SPIN_F32X4 && d->n_real <= 4096) ? SPIN_OK

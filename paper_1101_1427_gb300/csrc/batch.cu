@@ -948,7 +948,8 @@ static bool batch_item_ok(const spin_batch_item &it, int32_t pt_every) {
   const spin_lattice *h = it.lat;
   if (!h || !it.betas) return false;
   if (h->d.model == SPIN_EA)
-    return h->d.layout == SPIN_MSC1 && it.couplings != nullptr && h->g.L <= 32 && h->d.n_sets <= 32;
+    return h->d.layout == SPIN_MSC1 && h->d.dim == 3 && it.couplings != nullptr && h->g.L <= 32 &&
+           h->d.n_sets <= 32;
   if (h->d.model == SPIN_ISING)
     return h->g.dim == 2 && it.Q_series == nullptr &&
            ((h->d.layout == SPIN_I8 && h->g.L % 16 == 0) || (h->d.layout == SPIN_MSC1 && h->g.L % 256 == 0)) &&

@@ -164,4 +164,122 @@ __device__ __forceinline__ void ea_cs_quad(uint32_t *__restrict__ w, const uint3
   }
 }
 
+// ---------------------------------------------------------------- 2D
+// The square lattice (the paper's own Sec. 6 benchmark is 2D): four bonds,
+// dE = 8 - 4u per realisation; flip iff u >= 2 or r < thr(dE).  Storage and
+// couplings as in 3D with two directions ([2][colour][N/2] per group).
+
+// Colour index j (colour c) of an L x L lattice: site i, row start and the
+// linear indices of the four neighbours.
+__device__ __forceinline__ CsSite cs_site2(uint32_t j, int colour, uint32_t L, const FastDiv &fL) {
+  const uint32_t i0 = 2u * j;
+  const uint32_t y = fdiv(i0, fL);
+  const uint32_t x0 = i0 - y * L;
+  const uint32_t x = x0 + ((colour + y) & 1u);
+  const uint32_t rb = i0 - x0, i = rb + x;
+  CsSite s;
+  s.i = i;
+  s.rb = rb;
+  s.xp = rb + (x == L - 1 ? 0 : x + 1);
+  s.xm = rb + (x == 0 ? L - 1 : x - 1);
+  s.yp = y == L - 1 ? i - (L - 1) * L : i + L;
+  s.ym = y == 0 ? i + (L - 1) * L : i - L;
+  s.zp = s.zm = i;
+  return s;
+}
+
+// Flip mask of one word-site from its four bond words (1 = unsatisfied)
+// and the bit-sliced count (b0, b1, b2) of u in 0..4.
+__device__ __forceinline__ Flip ea_flip2(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, uint32_t r,
+                                         uint32_t t4, uint32_t t8) {
+  const uint32_t s1 = u0 ^ u1, c1 = u0 & u1, s2 = u2 ^ u3, c2 = u2 & u3;
+  Flip f;
+  f.b0 = s1 ^ s2;
+  const uint32_t c3 = s1 & s2;
+  f.b1 = c1 ^ c2 ^ c3;
+  f.b2 = c1 & c2;
+  const uint32_t R4 = r < t4 ? ~0u : 0u, R8 = r < t8 ? ~0u : 0u;
+  const uint32_t ge2 = f.b2 | f.b1;
+  const uint32_t eq1 = ~f.b2 & ~f.b1 & f.b0, eq0 = ~(f.b2 | f.b1 | f.b0);
+  f.F = ge2 | (eq1 & R4) | (eq0 & R8);
+  return f;
+}
+
+// Post-update count (bit-sliced): a flip turns u into 4 - u.
+__device__ __forceinline__ void ea_after2(const Flip &f, uint32_t &a0, uint32_t &a1, uint32_t &a2) {
+  const uint32_t v1 = ~f.b2 & (f.b1 ^ f.b0), v2 = ~(f.b2 | f.b1 | f.b0);
+  a0 = f.b0;
+  a1 = (f.F & v1) | (~f.F & f.b1);
+  a2 = (f.F & v2) | (~f.F & f.b2);
+}
+
+// Update of the quad j = 4 j4 .. 4 j4 + 3 of colour `colour` in one 2D
+// word-lattice w with group couplings J ([2][colour][N/2]), as ea_cs_quad.
+template <bool kCount, typename AddFn>
+__device__ __forceinline__ void ea_cs_quad2(uint32_t *__restrict__ w, const uint32_t *__restrict__ J,
+                                            uint32_t j4, int colour, uint32_t L, uint32_t N,
+                                            const FastDiv &fL, uint4 r, uint32_t t4, uint32_t t8, AddFn add) {
+  const uint32_t half = N >> 1;
+  const uint32_t oc = (uint32_t)colour ^ 1u;
+  uint32_t *own = w + (uint32_t)colour * half;
+  const uint32_t *oth = w + oc * half;
+  const uint32_t *Jx = J, *Jy = J + N;
+  const uint32_t co = (uint32_t)colour * half, ot = oc * half;
+  const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+  if ((L & 7u) == 0) {
+    // the quad is 4 consecutive colour indices of one row: 16-byte loads
+    const uint32_t j0 = 4 * j4;
+    const CsSite st = cs_site2(j0, colour, L, fL);
+    const uint32_t p = st.i & 1u;
+    const uint32_t jr = st.rb >> 1, LH = L >> 1;
+    const uint4 O = ldv4(oth + j0);
+    const uint32_t jx = p ? (j0 + 4 == jr + LH ? jr : j0 + 4) : (j0 == jr ? jr + LH - 1 : j0 - 1);
+    const uint32_t Ox = oth[jx];
+    const uint4 JXo = ldv4(Jx + ot + j0);
+    const uint32_t JXx = Jx[ot + jx];
+    const uint4 S = ldv4(own + j0);
+    const uint4 YP = ldv4(oth + (st.yp >> 1)), YM = ldv4(oth + (st.ym >> 1));
+    const uint4 JXs = ldv4(Jx + co + j0), JYs = ldv4(Jy + co + j0);
+    const uint4 JYm = ldv4(Jy + ot + (st.ym >> 1));
+    const uint32_t s_[4] = {S.x, S.y, S.z, S.w}, o_[4] = {O.x, O.y, O.z, O.w};
+    const uint32_t jo_[4] = {JXo.x, JXo.y, JXo.z, JXo.w};
+    const uint32_t yp_[4] = {YP.x, YP.y, YP.z, YP.w}, ym_[4] = {YM.x, YM.y, YM.z, YM.w};
+    const uint32_t jx_[4] = {JXs.x, JXs.y, JXs.z, JXs.w}, jy_[4] = {JYs.x, JYs.y, JYs.z, JYs.w};
+    const uint32_t jym_[4] = {JYm.x, JYm.y, JYm.z, JYm.w};
+    uint32_t nw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t xm = p ? o_[k] : (k ? o_[k - 1] : Ox);
+      const uint32_t xp = p ? (k < 3 ? o_[k + 1] : Ox) : o_[k];
+      const uint32_t jxm = p ? jo_[k] : (k ? jo_[k - 1] : JXx);
+      const Flip f = ea_flip2(s_[k] ^ xp ^ jx_[k], s_[k] ^ xm ^ jxm, s_[k] ^ yp_[k] ^ jy_[k],
+                              s_[k] ^ ym_[k] ^ jym_[k], rr[k], t4, t8);
+      nw[k] = s_[k] ^ f.F;
+      if (kCount) {
+        uint32_t a0, a1, a2;
+        ea_after2(f, a0, a1, a2);
+        add(a0, a1, a2);
+      }
+    }
+    *reinterpret_cast<uint4 *>(own + j0) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+    return;
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < 4; ++k) {
+    const uint32_t j = 4 * j4 + k;
+    if (j >= half) break;
+    const CsSite st = cs_site2(j, colour, L, fL);
+    const uint32_t S = own[j];
+    const Flip f = ea_flip2(S ^ oth[st.xp >> 1] ^ Jx[co + j], S ^ oth[st.xm >> 1] ^ Jx[ot + (st.xm >> 1)],
+                            S ^ oth[st.yp >> 1] ^ Jy[co + j], S ^ oth[st.ym >> 1] ^ Jy[ot + (st.ym >> 1)], rr[k],
+                            t4, t8);
+    own[j] = S ^ f.F;
+    if (kCount) {
+      uint32_t a0, a1, a2;
+      ea_after2(f, a0, a1, a2);
+      add(a0, a1, a2);
+    }
+  }
+}
+
 }  // namespace spin

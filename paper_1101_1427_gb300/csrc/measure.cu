@@ -160,6 +160,7 @@ __device__ long long vc_block_total(const uint32_t (&c)[kThr], uint32_t (*sm)[kW
   return tot;
 }
 
+template <int kDim>
 __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__restrict__ w,
                                                           const uint32_t *__restrict__ J, Geom g,
                                                           long long *__restrict__ E,
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   const uint32_t t = wl % T, grp = (wl / T) % G, a = wl / (T * G);
   const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N;
   const uint32_t *s = w + (size_t)wl * N;
-  const uint32_t *Jg = J + (size_t)grp * 3 * N;
+  const uint32_t *Jg = J + (size_t)grp * kDim * N;
   const bool do_q = Q && a == 0 && g.n_sets >= 2;
   const uint32_t *s1 = s + (size_t)G * T * N;  // set 1, same (g, t)
   uint32_t CE[kThr] = {}, CM[kThr] = {}, CQ[kThr] = {};
@@ -186,14 +187,16 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
       const int c = q >= quads ? 1 : 0;
       const uint32_t j0 = 4 * (q - (uint32_t)c * quads);
       const uint32_t co = (uint32_t)c * half, oc = (uint32_t)(c ^ 1) * half;
-      const CsSite st = cs_site(j0, c, L, g.fL);
+      const CsSite st = kDim == 3 ? cs_site(j0, c, L, g.fL) : cs_site2(j0, c, L, g.fL);
       const uint32_t p = st.i & 1u, jr = st.rb >> 1;
       const uint4 S = ldv4(s + co + j0), O = ldv4(s + oc + j0);
       // x + 1: the other colour at the same index (p = 0) or the next (p = 1)
       const uint32_t jx = j0 + 4 == jr + LH ? jr : j0 + 4;
       const uint32_t Ox = p ? s[oc + jx] : 0u;
-      const uint4 YP = ldv4(s + oc + (st.yp >> 1)), ZP = ldv4(s + oc + (st.zp >> 1));
-      const uint4 JX = ldv4(Jg + co + j0), JY = ldv4(Jg + N + co + j0), JZ = ldv4(Jg + 2 * N + co + j0);
+      const uint4 YP = ldv4(s + oc + (st.yp >> 1));
+      const uint4 ZP = kDim == 3 ? ldv4(s + oc + (st.zp >> 1)) : make_uint4(0, 0, 0, 0);
+      const uint4 JX = ldv4(Jg + co + j0), JY = ldv4(Jg + N + co + j0);
+      const uint4 JZ = kDim == 3 ? ldv4(Jg + 2 * N + co + j0) : make_uint4(0, 0, 0, 0);
       const uint4 S1 = do_q ? ldv4(s1 + co + j0) : make_uint4(0, 0, 0, 0);
       const uint32_t sv[4] = {S.x, S.y, S.z, S.w}, ov[4] = {O.x, O.y, O.z, O.w};
       const uint32_t yv[4] = {YP.x, YP.y, YP.z, YP.w}, zv[4] = {ZP.x, ZP.y, ZP.z, ZP.w};
@@ -202,7 +205,8 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const uint32_t xp = p ? (k < 3 ? ov[k + 1] : Ox) : ov[k];
-        const uint32_t u0 = sv[k] ^ xp ^ jxv[k], u1 = sv[k] ^ yv[k] ^ jyv[k], u2 = sv[k] ^ zv[k] ^ jzv[k];
+        const uint32_t u0 = sv[k] ^ xp ^ jxv[k], u1 = sv[k] ^ yv[k] ^ jyv[k];
+        const uint32_t u2 = kDim == 3 ? sv[k] ^ zv[k] ^ jzv[k] : 0u;
         vc_add(CE, u0 ^ u1 ^ u2, 0);
         vc_add(CE, (u0 & u1) | (u2 & (u0 ^ u1)), 1);
         if (M) vc_add(CM, sv[k], 0);
@@ -214,12 +218,12 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     const int c = k >= half ? 1 : 0;
     const uint32_t j = k - (uint32_t)c * half;
-    const CsSite st = cs_site(j, c, L, g.fL);
+    const CsSite st = kDim == 3 ? cs_site(j, c, L, g.fL) : cs_site2(j, c, L, g.fL);
     const uint32_t oc = (uint32_t)(c ^ 1) * half;
     const uint32_t S = s[k];
     const uint32_t u0 = S ^ s[oc + (st.xp >> 1)] ^ Jg[k];
     const uint32_t u1 = S ^ s[oc + (st.yp >> 1)] ^ Jg[N + k];
-    const uint32_t u2 = S ^ s[oc + (st.zp >> 1)] ^ Jg[2 * N + k];
+    const uint32_t u2 = kDim == 3 ? S ^ s[oc + (st.zp >> 1)] ^ Jg[2 * N + k] : 0u;
     vc_add(CE, u0 ^ u1 ^ u2, 0);
     vc_add(CE, (u0 & u1) | (u2 & (u0 ^ u1)), 1);
     if (M) vc_add(CM, S, 0);
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
   }
   const uint32_t lane = threadIdx.x & 31;
   const int64_t lat = ((int64_t)a * T + t) * g.n_real + 32 * grp + lane;
-  // E = 2 unsat - 3N, M = N - 2 down, Q = N - 2 diff: block 0 adds the constants
+  // E = 2 unsat - kDim N, M = N - 2 down, Q = N - 2 diff: block 0 adds the constants
   const long long n0 = blockIdx.x == 0 ? (long long)N : 0;
   // one block per word-lattice stores its counts; several add them to
   // outputs the host has zeroed
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
     else add_ll(p, v);
   };
   const long long unsat = vc_block_total(CE, sm);
-  if (threadIdx.x < 32 && E) put(&E[lat], 2 * unsat - 3 * n0);
+  if (threadIdx.x < 32 && E) put(&E[lat], 2 * unsat - kDim * n0);
   if (M) {
     const long long down = vc_block_total(CM, sm);
     if (threadIdx.x < 32) put(&M[lat], n0 - 2 * down);
@@ -478,7 +482,8 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
     return e;
   }
   const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
-  return launch_dependent(measure_msc_kernel, dim3(gx, (unsigned)n_wl), dim3(256), 0, st, (const uint32_t *)h->spins,
+  return launch_dependent(g.dim == 3 ? measure_msc_kernel<3> : measure_msc_kernel<2>, dim3(gx, (unsigned)n_wl),
+                          dim3(256), 0, st, (const uint32_t *)h->spins,
                           (const uint32_t *)J, g, (long long *)E, (long long *)M,
                           (g.n_sets >= 2) ? (long long *)Q : nullptr);
 }

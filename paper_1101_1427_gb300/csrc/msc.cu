@@ -1,8 +1,9 @@
-// +-J Edwards-Anderson glass in 3D with asynchronous multi-spin coding
-// (Sec. 6): bit b of a 32-bit word is the spin of realisation 32 g + b at
-// one site, bit set <=> s = -1; word-lattices [n_sets][groups][n_temps],
-// each stored colour-split (ea_cs.cuh).  Coupling words [groups][3][colour]
-// [N/2], bit set <=> J = -1.  The 32 realisations of a word share one
+// +-J Edwards-Anderson glass in 3D (and on the square lattice of the
+// paper's own Sec. 6 benchmark) with asynchronous multi-spin coding: bit b
+// of a 32-bit word is the spin of realisation 32 g + b at one site, bit set
+// <=> s = -1; word-lattices [n_sets][groups][n_temps], each stored
+// colour-split (ea_cs.cuh).  Coupling words [groups][dim][colour][N/2], bit
+// set <=> J = -1.  The 32 realisations of a word share one
 // uniform per site and sweep (the paper's footnote to Sec. 6), so one Philox
 // call serves four word-sites.
 #include "ea_cs.cuh"
@@ -35,11 +36,11 @@ __global__ void init_msc_kernel(uint32_t *__restrict__ w, Geom g, RoundKeys rk) 
 __global__ void couplings_msc_kernel(uint32_t *__restrict__ J, Geom g, RoundKeys rk) {
   const int G = g.n_real / 32;
   const int64_t quads = (g.N + 3) / 4;
-  const int64_t rows = (int64_t)G * 3;
+  const int64_t rows = (int64_t)G * g.dim;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < rows * quads;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t gd = k / quads, q4 = k - gd * quads;
-    const int grp = (int)(gd / 3), d = (int)(gd % 3);
+    const int grp = (int)(gd / g.dim), d = (int)(gd % g.dim);
     const uint4 r = philox(make_uint4((uint32_t)q4, 0u, lattice_id(0, grp, 0),
                                       ctr_w(TAG_COUPLING, 0, (uint32_t)d)), rk);
     uint32_t *out = J + gd * g.N;
@@ -58,6 +59,18 @@ struct NoAdd {
   __device__ void operator()(uint32_t, uint32_t, uint32_t) const {}
 };
 
+// One quad update in kDim dimensions (the group's couplings start at J).
+template <int kDim>
+__device__ __forceinline__ void ea_quad(uint32_t *w, const uint32_t *J, uint32_t j4, int colour, uint32_t L,
+                                        uint32_t N, const FastDiv &fL, uint4 r, uint32_t t4, uint32_t t8,
+                                        uint32_t t12) {
+  if (kDim == 3)
+    ea_cs_quad<false>(w, J, j4, colour, L, N, fL, r, t4, t8, t12, NoAdd());
+  else
+    ea_cs_quad2<false>(w, J, j4, colour, L, N, fL, r, t4, t8, NoAdd());
+}
+
+template <int kDim>
 __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w,
                                                         const uint32_t *__restrict__ J, Geom g,
                                                         uint32_t total,
@@ -75,14 +88,14 @@ __global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w
     const uint32_t a = fdiv(st, g.fgrp), grp = st - a * G;
     const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, grp, t), wctr), rk);
     const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
-    ea_cs_quad<false>(w + (size_t)wl * N, J + (size_t)grp * 3 * N, j4, colour, L, N, g.fL, r, t4, t8,
-                      t12, NoAdd());
+    ea_quad<kDim>(w + (size_t)wl * N, J + (size_t)grp * kDim * N, j4, colour, L, N, g.fL, r, t4, t8, t12);
   }
 }
 
 // w = 64 (Sec. 6: 64 spins per variable): realisation groups 2q and 2q + 1
 // of one (set, slot) share their uniforms, keyed by q, so one Philox call
 // serves the same quad of both word-lattices.
+template <int kDim>
 __global__ void __launch_bounds__(256) msc_phase_pair_kernel(uint32_t *__restrict__ w,
                                                              const uint32_t *__restrict__ J, Geom g,
                                                              uint32_t total,
@@ -100,10 +113,9 @@ __global__ void __launch_bounds__(256) msc_phase_pair_kernel(uint32_t *__restric
     const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, q, t), wctr), rk);
     const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
     const size_t wl0 = ((size_t)a * G + 2 * q) * T + t;  // group 2q; group 2q + 1 is T word-lattices on
-    ea_cs_quad<false>(w + wl0 * N, J + (size_t)(2 * q) * 3 * N, j4, colour, L, N, g.fL, r, t4, t8, t12,
-                      NoAdd());
-    ea_cs_quad<false>(w + (wl0 + T) * N, J + (size_t)(2 * q + 1) * 3 * N, j4, colour, L, N, g.fL, r, t4, t8,
-                      t12, NoAdd());
+    ea_quad<kDim>(w + wl0 * N, J + (size_t)(2 * q) * kDim * N, j4, colour, L, N, g.fL, r, t4, t8, t12);
+    ea_quad<kDim>(w + (wl0 + T) * N, J + (size_t)(2 * q + 1) * kDim * N, j4, colour, L, N, g.fL, r, t4, t8,
+                  t12);
   }
 }
 
@@ -161,7 +173,7 @@ cudaError_t launch_init_msc(spin_lattice *h) {
 
 cudaError_t launch_couplings_msc(spin_lattice *h) {
   const Geom &g = h->g;
-  couplings_msc_kernel<<<capped((int64_t)(g.n_real / 32) * 3 * g.N / 4 + 1), 256, 0, h->stream>>>(
+  couplings_msc_kernel<<<capped((int64_t)(g.n_real / 32) * g.dim * g.N / 4 + 1), 256, 0, h->stream>>>(
       (uint32_t *)h->couplings, g, make_round_keys(h->d.seed));
   return cudaGetLastError();
 }
@@ -175,9 +187,11 @@ cudaError_t launch_sweeps_msc_ea(spin_lattice *h, const uint32_t *J, int64_t n_s
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {
-      const cudaError_t e = launch_dependent(pair ? msc_phase_pair_kernel : msc_phase_kernel, dim3(capped(work)),
-                                             dim3(256), 0, h->stream, (uint32_t *)h->spins, J, g, work,
-                                             (const uint32_t *)h->d_thr, rk, sweep, colour);
+      auto *k3 = pair ? msc_phase_pair_kernel<3> : msc_phase_kernel<3>;
+      auto *k2 = pair ? msc_phase_pair_kernel<2> : msc_phase_kernel<2>;
+      const cudaError_t e = launch_dependent(g.dim == 3 ? k3 : k2, dim3(capped(work)), dim3(256), 0, h->stream,
+                                             (uint32_t *)h->spins, J, g, work, (const uint32_t *)h->d_thr, rk,
+                                             sweep, colour);
       if (e != cudaSuccess) return e;
     }
   }

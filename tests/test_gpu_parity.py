@@ -130,7 +130,7 @@ def test_fused_many_lattices_short_strips():
 
 
 # ------------------------------------------------------------------ EA
-def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None, width=32):
+def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None, width=32, dim=3):
     """Oracle runs of single realisations; `width` realisations share each
     update uniform (key r >> 5 for 32, r >> 6 for 64)."""
     n_temps = len(betas)
@@ -138,13 +138,47 @@ def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None,
     reals = range(n_real) if reals is None else reals
     res = {}
     for r in reals:
-        J = oracle.ea_couplings(3, L, r, seed)
-        sp_ = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t),
+        J = oracle.ea_couplings(dim, L, r, seed)
+        sp_ = np.stack([np.stack([oracle.ising_init(dim, L, seed, oracle.lattice_id(a, r >> 5, t),
                                                     bit=r & 31) for t in range(n_temps)])
                         for a in range(n_sets)]).copy()
-        E, Q, acc, _ = oracle.pt_run(3, L, sp_, betas, seed, r, r >> shift, 0, n_sweeps, pt_every, J=J)
+        E, Q, acc, _ = oracle.pt_run(dim, L, sp_, betas, seed, r, r >> shift, 0, n_sweeps, pt_every, J=J)
         res[r] = (J, sp_, E, Q, acc)
     return res
+
+
+@pytest.mark.parametrize("L,width", [(16, 32), (10, 32), (16, 64)])
+def test_ea2d_coded_bit_exact(L, width):
+    """The coded EA glass on the square lattice (the paper's Sec. 6 benchmark
+    is 2D): exchange and E, M, Q every sweep, vectorised (L % 8 == 0) and
+    per-site (L = 10) paths, w = 32 and 64; sampled realisations equal the
+    oracle (int8 per realisation, four bonds)."""
+    seed, n_real, n = 31, 128, 8
+    betas = list(1.0 / np.geomspace(0.8, 3.0, 5))
+    lat = sp.Lattice(B.SPIN_EA, 2, L, B.SPIN_MSC1, n_real=n_real, n_temps=5, n_sets=2, seed=seed)
+    if width == 64:
+        lat.set_msc_width(64)
+    acc = torch.zeros(10, dtype=torch.int64, device="cuda")
+    out = lat.run(betas, n, measure_every=1, pt_every=1, accepted=acc)
+    got = host(lat.unpack())
+    E = host(out["E"]).reshape(n, 2, 5, n_real)
+    Q = host(out["Q"]).reshape(n, 5, n_real)
+    _, M_now, _ = lat.measure()  # of the final state (the series precede each sweep's exchange)
+    M_now = host(M_now).reshape(2, 5, n_real)
+    ref = _ea_oracle(L, seed, betas, n_real, 2, n, pt_every=1, reals=(0, 33, 64, 127), width=width, dim=2)
+    for r, (J, s, Es, Qs, ac) in ref.items():
+        assert np.array_equal(got[:, :, r], s), r
+        assert np.array_equal(E[:, :, :, r], Es), r
+        assert np.array_equal(Q[:, :, r], Qs), r
+        assert np.array_equal(M_now[:, :, r], s.astype(np.int64).sum(axis=2)), r
+    # the couplings equal the oracle's draws (bit r of group r >> 5)
+    Jw = host(lat.couplings).view(np.uint32).reshape(n_real // 32, 2, 2, L * L // 2)
+    for r in (0, 127):
+        Jo = oracle.ea_couplings(2, L, r, seed).reshape(2, L * L)
+        for d in range(2):
+            for i in (0, 1, L + 1, L * L - 1):
+                c = ((i % L) + (i // L)) & 1
+                assert ((Jw[r >> 5, d, c, i >> 1] >> (r & 31)) & 1) == (Jo[d, i] < 0), (r, d, i)
 
 
 @pytest.mark.parametrize("L", [8, 6])

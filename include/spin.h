@@ -167,7 +167,7 @@ typedef struct {
  * lattice of every handle, with the measurements and exchange steps of
  * spin_run, in ONE cooperative kernel launch on `stream`.  Results
  * (lattices, series, exchange decisions) are identical to calling spin_run
- * on each handle.  Supported handles: EA in the coded layout (L <= 32) and
+ * on each handle.  Supported handles: 3D EA in the coded layout (L <= 32) and
  * 2D ferromagnets, int8 with L % 16 == 0 or coded with L % 256 == 0, in the
  * checkerboard order and without exchange between their slots; at most 16
  * handles and 96 work units (one unit per EA realisation group or Ising

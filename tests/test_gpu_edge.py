@@ -176,3 +176,13 @@ def test_binding_checks_arrays_against_the_handle():
     ok = torch.zeros(12, dtype=torch.int64, device="cuda")
     B.spin_run(lat.h, None, [0.4, 0.5, 0.6], 8, 2, 0, ok)
     assert lat.sweeps_done == 8
+
+
+def test_batched_launch_refuses_2d_coded_glass():
+    """The batched launch takes 3D coded EA handles only; a 2D one is
+    refused before anything runs."""
+    ea = sp.Lattice(B.SPIN_EA, 2, 16, B.SPIN_MSC1, n_real=32, n_temps=2, n_sets=2, seed=3)
+    before = ea.spins.clone()
+    with pytest.raises(B.SpinError):
+        sp.batch_run([ea.batch_item([0.5, 0.7])], 2, 0, 0)
+    assert torch.equal(ea.spins, before) and ea.sweeps_done == 0

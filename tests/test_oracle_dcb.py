@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from oracle import exact
-from tests.stats import assert_within, binned_mean
+from tests.stats import assert_within, binned_mean, tau_int
 
 L4, T2 = 4, 2
 
@@ -114,6 +114,7 @@ def test_long_run_matches_enumeration(k, symmetric):
         oracle.dcb_sweeps(L4, s, beta, 17, lid, m * k, k, T2, k, symmetric)
         E[m] = oracle.ising_energy(2, L4, s)
     bf = exact.brute_force(2, L4, beta)
+    assert (n - 200) / 50 > 20 * tau_int(E[200:])  # bins much longer than the autocorrelation time
     e_mc, e_err = binned_mean(E[200:])
     assert_within(e_mc, e_err, bf["E"], what="<E>")
 
@@ -233,6 +234,7 @@ def test_3d_long_run_matches_enumeration():
     for m in range(n):
         oracle.dcb_sweeps(2, s, beta, 23, lid, m * k, k, 1, k, True, dim=3)
         E[m] = oracle.ising_energy(3, 2, s)
+    assert (n - 200) / 50 > 20 * tau_int(E[200:])
     e_mc, e_err = binned_mean(E[200:])
     assert_within(e_mc, e_err, exact.brute_force(3, 2, beta)["E"], what="<E>")
 

@@ -45,7 +45,8 @@ __device__ __forceinline__ CsSite cs_site(uint32_t j, int colour, uint32_t L, co
 
 // Metropolis flip mask of one word-site from its six bond words
 // u_k = s ^ s_nb ^ J (1 = unsatisfied) and the shared uniform r:
-// dE = 12 - 4u per realisation; flip iff u >= 3 or r < thr(dE).
+// dE = 12 - 4u per realisation; flip iff u >= 3 or r < thr(dE).  The
+// thresholds decrease with dE (thr12 <= thr8 <= thr4).
 // Also returns the bit-sliced count (b0, b1, b2) of u.
 struct Flip {
   uint32_t F, b0, b1, b2;
@@ -60,10 +61,11 @@ __device__ __forceinline__ Flip ea_flip(uint32_t u0, uint32_t u1, uint32_t u2, u
   const uint32_t c3 = s1 & s2;
   f.b1 = c1 ^ c2 ^ c3;
   f.b2 = (c1 & c2) | (c3 & (c1 ^ c2));
-  const uint32_t R4 = r < t4 ? ~0u : 0u, R8 = r < t8 ? ~0u : 0u, R12 = r < t12 ? ~0u : 0u;
-  const uint32_t ge3 = f.b2 | (f.b1 & f.b0);
-  const uint32_t eq2 = ~f.b2 & f.b1 & ~f.b0, eq1 = ~f.b2 & ~f.b1 & f.b0, eq0 = ~(f.b2 | f.b1 | f.b0);
-  f.F = ge3 | (eq2 & R4) | (eq1 & R8) | (eq0 & R12);
+  // thr12 <= thr8 <= thr4, so the tests are nested: r < thr12 flips every
+  // bit, else r < thr8 those with u >= 1, else r < thr4 those with u >= 2,
+  // else those with u >= 3
+  const uint32_t ge3 = f.b2 | (f.b1 & f.b0), ge2 = f.b2 | f.b1, ge1 = ge2 | f.b0;
+  f.F = r < t12 ? ~0u : (r < t8 ? ge1 : (r < t4 ? ge2 : ge3));
   return f;
 }
 
@@ -198,10 +200,10 @@ __device__ __forceinline__ Flip ea_flip2(uint32_t u0, uint32_t u1, uint32_t u2, 
   const uint32_t c3 = s1 & s2;
   f.b1 = c1 ^ c2 ^ c3;
   f.b2 = c1 & c2;
-  const uint32_t R4 = r < t4 ? ~0u : 0u, R8 = r < t8 ? ~0u : 0u;
-  const uint32_t ge2 = f.b2 | f.b1;
-  const uint32_t eq1 = ~f.b2 & ~f.b1 & f.b0, eq0 = ~(f.b2 | f.b1 | f.b0);
-  f.F = ge2 | (eq1 & R4) | (eq0 & R8);
+  // nested tests as in ea_flip: r < thr8 flips every bit, else r < thr4
+  // those with u >= 1, else those with u >= 2
+  const uint32_t ge2 = f.b2 | f.b1, ge1 = ge2 | f.b0;
+  f.F = r < t8 ? ~0u : (r < t4 ? ge1 : ge2);
   return f;
 }
 

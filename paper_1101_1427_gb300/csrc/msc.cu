@@ -53,13 +53,11 @@ __global__ void couplings_msc_kernel(uint32_t *__restrict__ J, Geom g, RoundKeys
   }
 }
 
-// One colour phase over all word-lattices: thread per (word-lattice, quad of
-// colour sites); see ea_cs.cuh for the update of a quad.
 struct NoAdd {
   __device__ void operator()(uint32_t, uint32_t, uint32_t) const {}
 };
 
-// One quad update in kDim dimensions (the group's couplings start at J).
+// One quad update in kDim dimensions (the group's couplings start at J), any L.
 template <int kDim>
 __device__ __forceinline__ void ea_quad(uint32_t *w, const uint32_t *J, uint32_t j4, int colour, uint32_t L,
                                         uint32_t N, const FastDiv &fL, uint4 r, uint32_t t4, uint32_t t8,
@@ -70,52 +68,57 @@ __device__ __forceinline__ void ea_quad(uint32_t *w, const uint32_t *J, uint32_t
     ea_cs_quad2<false>(w, J, j4, colour, L, N, fL, r, t4, t8, NoAdd());
 }
 
-template <int kDim>
-__global__ void __launch_bounds__(256) msc_phase_kernel(uint32_t *__restrict__ w,
-                                                        const uint32_t *__restrict__ J, Geom g,
-                                                        uint32_t total,
-                                                        const uint32_t *__restrict__ thr,
-                                                        RoundKeys rk, uint32_t sweep,
-                                                        int colour) {
-  griddep_wait();
-  griddep_release();
-  const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = (N / 2 + 3) / 4;
-  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
-  const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
-    const uint32_t wl = fdiv(k, g.fquads), j4 = k - wl * quads;
-    const uint32_t st = fdiv(wl, g.ftemps), t = wl - st * T;  // wl = (a G + grp) T + t
-    const uint32_t a = fdiv(st, g.fgrp), grp = st - a * G;
-    const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, grp, t), wctr), rk);
-    const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
-    ea_quad<kDim>(w + (size_t)wl * N, J + (size_t)grp * kDim * N, j4, colour, L, N, g.fL, r, t4, t8, t12);
-  }
-}
+// Slots per thread of msc_phase_kernel: four when the updates can share the
+// quad's geometry and couplings (L % 8 == 0), else one.
+__host__ __device__ constexpr uint32_t ea_slots(bool row_quads) { return row_quads ? 4u : 1u; }
 
-// w = 64 (Sec. 6: 64 spins per variable): realisation groups 2q and 2q + 1
-// of one (set, slot) share their uniforms, keyed by q, so one Philox call
-// serves the same quad of both word-lattices.
-template <int kDim>
-__global__ void __launch_bounds__(256) msc_phase_pair_kernel(uint32_t *__restrict__ w,
-                                                             const uint32_t *__restrict__ J, Geom g,
-                                                             uint32_t total,
-                                                             const uint32_t *__restrict__ thr,
-                                                             RoundKeys rk, uint32_t sweep, int colour) {
+// One colour phase over all word-lattices.  Thread k takes one quad of
+// colour sites (j4) in the word-lattices (a, grp, t) of kS consecutive
+// slots t of one replica set a and group grp, one slot after the other.
+// When L % 8 == 0 those updates share the quad's geometry and coupling
+// words, read once (ea_cs.cuh); each word-lattice draws its own uniforms,
+// so the mapping of updates to threads does not change the result.
+// kPair (w = 64, Sec. 6: 64 spins per variable): groups 2q and 2q + 1 of
+// one (set, slot) share their uniforms, keyed by q.  kRowQuads: L % 8 == 0
+// (else every site takes its own neighbour indices).  ftb divides by the
+// number of slot blocks ceil(n_temps / kS).  Register bounds: two CTAs per
+// SM for the shared form (its coupling words stay live across the slots),
+// three for the generic one.
+template <int kDim, bool kPair, bool kRowQuads>
+__global__ void __launch_bounds__(256, kRowQuads ? 2 : 3)
+    msc_phase_kernel(uint32_t *__restrict__ w, const uint32_t *__restrict__ J, Geom g, uint32_t total,
+                     FastDiv ftb, const uint32_t *__restrict__ thr, RoundKeys rk, uint32_t sweep, int colour) {
   griddep_wait();
   griddep_release();
   const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, quads = (N / 2 + 3) / 4;
-  const uint32_t G = (uint32_t)g.n_real / 32, G2 = G / 2, T = (uint32_t)g.n_temps;
+  constexpr uint32_t kS = ea_slots(kRowQuads);
+  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps, TB = (T + kS - 1) / kS;
   const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
-    const uint32_t pl = fdiv(k, g.fquads), j4 = k - pl * quads;
-    const uint32_t st = fdiv(pl, g.ftemps), t = pl - st * T;  // pl = (a G2 + q) T + t
-    const uint32_t a = fdiv(st, g.fgrp2), q = st - a * G2;
-    const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, q, t), wctr), rk);
-    const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2), t12 = __ldg(thr + 4 * t + 3);
-    const size_t wl0 = ((size_t)a * G + 2 * q) * T + t;  // group 2q; group 2q + 1 is T word-lattices on
-    ea_quad<kDim>(w + wl0 * N, J + (size_t)(2 * q) * kDim * N, j4, colour, L, N, g.fL, r, t4, t8, t12);
-    ea_quad<kDim>(w + (wl0 + T) * N, J + (size_t)(2 * q + 1) * kDim * N, j4, colour, L, N, g.fL, r, t4, t8,
-                  t12);
+    const uint32_t sb = fdiv(k, g.fquads), j4 = k - sb * quads;
+    const uint32_t st = fdiv(sb, ftb), tb = sb - st * TB;  // sb = (a G + grp) TB + tb
+    const uint32_t a = fdiv(st, g.fgrp), grp = st - a * G;
+    const uint32_t rkey = kPair ? grp >> 1 : grp;
+    uint32_t *ws = w + (size_t)st * T * N;  // slot t of (a, grp) is word-lattice st T + t
+    const uint32_t *Jg = J + (size_t)grp * kDim * N;
+    const uint32_t t0 = tb * kS, t1 = t0 + kS < T ? t0 + kS : T;
+    if (kRowQuads) {
+      const EaQuadGeom q = ea_quad_geom<kDim>(j4, colour, L, g.fL);
+      const EaQuadJ c = ea_quad_couplings<kDim>(Jg, q, colour, N);
+#pragma unroll 1
+      for (uint32_t t = t0; t < t1; ++t) {
+        const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, rkey, t), wctr), rk);
+        const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2);
+        const uint32_t t12 = kDim == 3 ? __ldg(thr + 4 * t + 3) : 0u;
+        ea_quad_update<kDim, false>(ws + (size_t)t * N, q, c, colour, N, r, t4, t8, t12, NoAdd());
+      }
+    } else {
+      const uint32_t t = t0;  // kS = 1: the slot block is the slot
+      const uint4 r = philox(make_uint4(j4, sweep, lattice_id(a, rkey, t), wctr), rk);
+      const uint32_t t4 = __ldg(thr + 4 * t + 1), t8 = __ldg(thr + 4 * t + 2);
+      const uint32_t t12 = kDim == 3 ? __ldg(thr + 4 * t + 3) : 0u;
+      ea_quad<kDim>(ws + (size_t)t * N, Jg, j4, colour, L, N, g.fL, r, t4, t8, t12);
+    }
   }
 }
 
@@ -181,17 +184,24 @@ cudaError_t launch_couplings_msc(spin_lattice *h) {
 cudaError_t launch_sweeps_msc_ea(spin_lattice *h, const uint32_t *J, int64_t n_sweeps) {
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
-  const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
   const bool pair = h->msc_width == 64;
-  const uint32_t work = (uint32_t)((pair ? n_wl / 2 : n_wl) * ((g.N / 2 + 3) / 4));
+  const bool row_quads = g.L % 8 == 0;
+  const uint32_t TB = ((uint32_t)g.n_temps + ea_slots(row_quads) - 1) / ea_slots(row_quads);
+  const uint32_t work = (uint32_t)g.n_sets * (uint32_t)(g.n_real / 32) * TB * (uint32_t)((g.N / 2 + 3) / 4);
+  const FastDiv ftb = make_fastdiv(TB);
+  using Kern = decltype(&msc_phase_kernel<3, false, true>);
+  const Kern kerns[2][2][2] = {
+      {{msc_phase_kernel<2, false, false>, msc_phase_kernel<2, false, true>},
+       {msc_phase_kernel<2, true, false>, msc_phase_kernel<2, true, true>}},
+      {{msc_phase_kernel<3, false, false>, msc_phase_kernel<3, false, true>},
+       {msc_phase_kernel<3, true, false>, msc_phase_kernel<3, true, true>}}};
+  const Kern kern = kerns[g.dim == 3][pair][row_quads];
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {
-      auto *k3 = pair ? msc_phase_pair_kernel<3> : msc_phase_kernel<3>;
-      auto *k2 = pair ? msc_phase_pair_kernel<2> : msc_phase_kernel<2>;
-      const cudaError_t e = launch_dependent(g.dim == 3 ? k3 : k2, dim3(capped(work)), dim3(256), 0, h->stream,
-                                             (uint32_t *)h->spins, J, g, work, (const uint32_t *)h->d_thr, rk,
-                                             sweep, colour);
+      const cudaError_t e = launch_dependent(kern, dim3(capped(work)), dim3(256), 0, h->stream,
+                                             (uint32_t *)h->spins, J, g, work, ftb, (const uint32_t *)h->d_thr,
+                                             rk, sweep, colour);
       if (e != cudaSuccess) return e;
     }
   }

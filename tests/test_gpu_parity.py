@@ -181,26 +181,27 @@ def test_ea2d_coded_bit_exact(L, width):
                 assert ((Jw[r >> 5, d, c, i >> 1] >> (r & 31)) & 1) == (Jo[d, i] < 0), (r, d, i)
 
 
-@pytest.mark.parametrize("L", [8, 6])
-def test_ea_w64_shared_uniforms_bit_exact(L):
+@pytest.mark.parametrize("L,T", [(8, 4), (6, 4), (8, 6)])
+def test_ea_w64_shared_uniforms_bit_exact(L, T):
     """w = 64 (Sec. 6): realisations r and r' with r >> 6 == r' >> 6 share
     every update uniform; plain per-handle path with exchange and
-    measurement every sweep, sampled realisations of both words of a pair."""
+    measurement every sweep, sampled realisations of both words of a pair.
+    T = 6 leaves the second block of four slots of a thread half empty."""
     seed, n_real, n = 23, 128, 10
-    betas = list(1.0 / np.geomspace(0.9, 2.0, 4))
-    lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=4, n_sets=2, seed=seed)
+    betas = list(1.0 / np.geomspace(0.9, 2.0, T))
+    lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=T, n_sets=2, seed=seed)
     lat.set_msc_width(64)
     out = lat.run(betas, n, measure_every=1, pt_every=1)
     got = host(lat.unpack())
-    E = host(out["E"]).reshape(n, 2, 4, n_real)
-    Q = host(out["Q"]).reshape(n, 4, n_real)
+    E = host(out["E"]).reshape(n, 2, T, n_real)
+    Q = host(out["Q"]).reshape(n, T, n_real)
     ref = _ea_oracle(L, seed, betas, n_real, 2, n, pt_every=1, reals=(0, 31, 32, 63, 64, 127), width=64)
     for r, (J, s, Es, Qs, ac) in ref.items():
         assert np.array_equal(got[:, :, r], s), r
         assert np.array_equal(E[:, :, :, r], Es), r
         assert np.array_equal(Q[:, :, r], Qs), r
     # and w = 32 gives a different chain from the same start
-    lat32 = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=4, n_sets=2, seed=seed)
+    lat32 = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=n_real, n_temps=T, n_sets=2, seed=seed)
     lat32.run(betas, n, measure_every=0, pt_every=1, series=False)
     assert not torch.equal(lat32.spins, lat.spins)
 

@@ -253,6 +253,203 @@ __global__ void __launch_bounds__(256) measure_msc_kernel(const uint32_t *__rest
 }
 
 
+// The same counts when L % 8 == 0, counted with carry-save adders.  Each
+// word-lattice gets one block of kRowThreads threads (small blocks, so that
+// all of them are resident at once) or, for large lattices, several; a
+// thread takes at most kRowItems quads of four consecutive colour indices of
+// one row.  Per quad the four unsatisfied-bond sums (weight 1) and carries
+// (weight 2) of E, and the four words of M and of Q (weight 1), go through
+// carry-save adders into running planes of weight 1, 2, 4 (and 8 for E);
+// only what carries out of those is rippled into the counter.  Then one
+// butterfly per counter over the warp, and the warps of a word-lattice add
+// their counts through shared memory.
+constexpr int kRowThreads = 64;
+constexpr int kRowItems = 16;
+constexpr int kRP = 8;   // per-thread planes: at most 16 quads x 4 sites x 3 bonds = 192 < 256
+constexpr int kRW = 13;  // per-warp planes: at most 32 x 192 = 6144 < 8192
+
+__device__ __forceinline__ void csa3(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t u = a ^ b;
+  h = (a & b) | (u & c);
+  l = u ^ c;
+}
+
+// counter planes from level W up += x (weight 2^W)
+template <int W, int K>
+__device__ __forceinline__ void ripple_at(uint32_t (&C)[K], uint32_t x) {
+#pragma unroll
+  for (int k = W; k < K; ++k) {
+    const uint32_t n = C[k] & x;
+    C[k] ^= x;
+    x = n;
+  }
+}
+
+// Running count of weight-1 words: planes o1, o2, o4 and the counter above.
+struct CsaCount {
+  uint32_t C[kRP];
+  uint32_t o1, o2, o4;
+  __device__ CsaCount() : o1(0), o2(0), o4(0) {
+#pragma unroll
+    for (int k = 0; k < kRP; ++k) C[k] = 0;
+  }
+  __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    uint32_t t1, t2, f;
+    csa3(t1, o1, o1, x0, x1);
+    csa3(t2, o1, o1, x2, x3);
+    csa3(f, o2, o2, t1, t2);
+    const uint32_t e = o4 & f;
+    o4 ^= f;
+    ripple_at<3>(C, e);
+  }
+  __device__ __forceinline__ void flush() {
+    ripple_at<2>(C, o4);
+    ripple_at<1>(C, o2);
+    ripple_at<0>(C, o1);
+    o1 = o2 = o4 = 0;
+  }
+};
+
+// The same for four weight-1 words s and four weight-2 words c at a time.
+struct CsaCount2 {
+  uint32_t C[kRP];
+  uint32_t o1, o2, o4, o8;
+  __device__ CsaCount2() : o1(0), o2(0), o4(0), o8(0) {
+#pragma unroll
+    for (int k = 0; k < kRP; ++k) C[k] = 0;
+  }
+  __device__ __forceinline__ void add(const uint32_t (&sv)[4], const uint32_t (&cv)[4]) {
+    uint32_t t1, t2, f1, f2, f3, e1, x;
+    csa3(t1, o1, o1, sv[0], sv[1]);
+    csa3(t2, o1, o1, sv[2], sv[3]);
+    csa3(f1, o2, o2, t1, t2);
+    csa3(f2, o2, o2, cv[0], cv[1]);
+    csa3(f3, o2, o2, cv[2], cv[3]);
+    csa3(e1, o4, o4, f1, f2);
+    const uint32_t e2 = o4 & f3;
+    o4 ^= f3;
+    csa3(x, o8, o8, e1, e2);
+    ripple_at<4>(C, x);
+  }
+  __device__ __forceinline__ void flush() {
+    ripple_at<3>(C, o8);
+    ripple_at<2>(C, o4);
+    ripple_at<1>(C, o2);
+    ripple_at<0>(C, o1);
+    o1 = o2 = o4 = o8 = 0;
+  }
+};
+
+// Sum of the warp's counters; lane b returns the count of bit b.
+__device__ __forceinline__ int warp_count(const uint32_t (&C)[kRP]) {
+  uint32_t P[kRW];
+#pragma unroll
+  for (int k = 0; k < kRW; ++k) P[k] = k < kRP ? C[k] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < kRW; ++k) {
+      const uint32_t a = P[k], b = __shfl_xor_sync(0xffffffffu, P[k], o);
+      P[k] = a ^ b ^ carry;
+      carry = (a & b) | (carry & (a ^ b));
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+#pragma unroll
+  for (int k = 0; k < kRW; ++k) cnt += (int)((P[k] >> lane) & 1u) << k;
+  return cnt;
+}
+
+// grid: (blocks per word-lattice, word-lattices), kRowThreads threads; the
+// register bound lets 14 blocks share an SM.
+template <int kDim>
+__global__ void __launch_bounds__(kRowThreads, 14) measure_msc_rows_kernel(const uint32_t *__restrict__ w,
+                                                               const uint32_t *__restrict__ J, Geom g,
+                                                               long long *__restrict__ E,
+                                                               long long *__restrict__ M,
+                                                               long long *__restrict__ Q) {
+  griddep_wait();
+  griddep_release();
+  constexpr int kWarps = kRowThreads / 32;
+  __shared__ int cnt[3][kWarps][32];
+  const uint32_t G = (uint32_t)g.n_real / 32, T = (uint32_t)g.n_temps;
+  const uint32_t wl = blockIdx.y, lt = threadIdx.x;
+  const uint32_t t = wl % T, grp = (wl / T) % G, a = wl / (T * G);
+  const uint32_t L = (uint32_t)g.L, N = (uint32_t)g.N, half = N / 2, quads = half / 4, LH = L / 2;
+  const uint32_t *s = w + (size_t)wl * N;
+  const uint32_t *Jg = J + (size_t)grp * kDim * N;
+  const bool do_q = Q && a == 0 && g.n_sets >= 2;
+  const uint32_t *s1 = s + (size_t)G * T * N;  // set 1, same (g, t)
+  CsaCount2 ce;
+  CsaCount cm, cq;
+  for (uint32_t q = blockIdx.x * kRowThreads + lt; q < 2 * quads; q += gridDim.x * kRowThreads) {
+      const uint32_t c = q >= quads ? 1u : 0u;
+      const uint32_t j0 = 4 * (q - c * quads);
+      const uint32_t co = c * half, oc = (c ^ 1u) * half;
+      const CsSite st = kDim == 3 ? cs_site(j0, (int)c, L, g.fL) : cs_site2(j0, (int)c, L, g.fL);
+      const uint32_t p = st.i & 1u, jr = st.rb >> 1;
+      const uint4 S = ldv4(s + co + j0), O = ldv4(s + oc + j0);
+      // x + 1: the other colour at the same index (p = 0) or the next (p = 1)
+      const uint32_t jx = j0 + 4 == jr + LH ? jr : j0 + 4;
+      const uint32_t Ox = p ? s[oc + jx] : 0u;
+      const uint4 YP = ldv4(s + oc + (st.yp >> 1));
+      const uint4 ZP = kDim == 3 ? ldv4(s + oc + (st.zp >> 1)) : make_uint4(0, 0, 0, 0);
+      const uint4 JX = ldv4(Jg + co + j0), JY = ldv4(Jg + N + co + j0);
+      const uint4 JZ = kDim == 3 ? ldv4(Jg + 2 * N + co + j0) : make_uint4(0, 0, 0, 0);
+      const uint32_t sv[4] = {S.x, S.y, S.z, S.w}, ov[4] = {O.x, O.y, O.z, O.w};
+      const uint32_t yv[4] = {YP.x, YP.y, YP.z, YP.w}, zv[4] = {ZP.x, ZP.y, ZP.z, ZP.w};
+      const uint32_t jxv[4] = {JX.x, JX.y, JX.z, JX.w}, jyv[4] = {JY.x, JY.y, JY.z, JY.w};
+      const uint32_t jzv[4] = {JZ.x, JZ.y, JZ.z, JZ.w};
+      // the bonds (i, i + e_d) of every site count each bond once
+      uint32_t sum[4], car[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t xp = p ? (k < 3 ? ov[k + 1] : Ox) : ov[k];
+        const uint32_t u0 = sv[k] ^ xp ^ jxv[k], u1 = sv[k] ^ yv[k] ^ jyv[k];
+        const uint32_t u2 = kDim == 3 ? sv[k] ^ zv[k] ^ jzv[k] : 0u;
+        sum[k] = u0 ^ u1 ^ u2;
+        car[k] = (u0 & u1) | (u2 & (u0 ^ u1));
+      }
+      ce.add(sum, car);
+      if (M) cm.add4(sv[0], sv[1], sv[2], sv[3]);
+      if (do_q) {
+        const uint4 S1 = ldv4(s1 + co + j0);
+        cq.add4(S.x ^ S1.x, S.y ^ S1.y, S.z ^ S1.z, S.w ^ S1.w);
+      }
+    }
+  ce.flush();
+  cm.flush();
+  cq.flush();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cnt[0][warp][lane] = warp_count(ce.C);
+  if (M) cnt[1][warp][lane] = warp_count(cm.C);
+  if (Q) cnt[2][warp][lane] = warp_count(cq.C);
+  __syncthreads();
+  if (warp != 0) return;
+  // lane b of warp 0 adds the warps' counts of bit b
+  long long e = 0, m = 0, d = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) {
+    e += cnt[0][k][lane];
+    if (M) m += cnt[1][k][lane];
+    if (do_q) d += cnt[2][k][lane];
+  }
+  const int64_t lat = ((int64_t)a * T + t) * g.n_real + 32 * grp + lane;
+  // E = 2 unsat - kDim N, M = N - 2 down, Q = N - 2 diff: part 0 adds the
+  // constants; with one part per word-lattice the counts are stored
+  const long long n0 = blockIdx.x == 0 ? (long long)N : 0;
+  const bool direct = gridDim.x == 1;
+  auto put = [direct](long long *ptr, long long v) {
+    if (direct) *ptr = v;
+    else add_ll(ptr, v);
+  };
+  if (E) put(&E[lat], 2 * e - kDim * n0);
+  if (M) put(&M[lat], n0 - 2 * m);
+  if (do_q) put(&Q[(int64_t)t * g.n_real + 32 * grp + lane], n0 - 2 * d);
+}
+
 // ---------------------------------------------------------------- Heisenberg
 // Per-block partial sums in double, then a fixed-order second pass, so the
 // result does not depend on scheduling.
@@ -450,10 +647,13 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
     if (Q) cudaMemsetAsync(Q, 0, sizeof(int64_t) * g.n_temps * g.n_real, st);
     return launch_measure_msc2d(h, E, M);
   }
-  // EA coded words: blocks per word-lattice (at most 16 sites per thread:
-  // 3 * 16 * 256 * 2^k stays inside the 16 planes); with one block per
-  // word-lattice the counts are stored, not added, and need no zeroing
-  const unsigned gx = (unsigned)((g.N + 256 * 16 - 1) / (256 * 16));
+  // EA coded words: blocks (or, with L % 8 == 0, parts of kRowThreads
+  // threads) per word-lattice, at most 16 sites (quads) per thread; with one
+  // per word-lattice the counts are stored, not added, and need no zeroing
+  const bool rows = h->d.layout == SPIN_MSC1 && g.L % 8 == 0;
+  const int64_t row_items = 2 * (g.N / 8);  // quads of both colours
+  const unsigned gx = rows ? (unsigned)((row_items + kRowThreads * kRowItems - 1) / (kRowThreads * kRowItems))
+                           : (unsigned)((g.N + 256 * 16 - 1) / (256 * 16));
   const bool coded_direct = h->d.layout == SPIN_MSC1 && gx == 1;
   if (!coded_direct) {
     if (E) cudaMemsetAsync(E, 0, sizeof(int64_t) * nl, st);
@@ -482,6 +682,11 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
     return e;
   }
   const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;
+  if (rows)
+    return launch_dependent(g.dim == 3 ? measure_msc_rows_kernel<3> : measure_msc_rows_kernel<2>,
+                            dim3(gx, (unsigned)n_wl), dim3(kRowThreads), 0, st,
+                            (const uint32_t *)h->spins, (const uint32_t *)J, g, (long long *)E, (long long *)M,
+                            (g.n_sets >= 2) ? (long long *)Q : nullptr);
   return launch_dependent(g.dim == 3 ? measure_msc_kernel<3> : measure_msc_kernel<2>, dim3(gx, (unsigned)n_wl),
                           dim3(256), 0, st, (const uint32_t *)h->spins,
                           (const uint32_t *)J, g, (long long *)E, (long long *)M,

@@ -652,10 +652,19 @@ def run_case(name):
         B.spin_sweep(lat.h, None, BETAS, 2, lat.seed)
         b.record(stream)
         flips = 2 * 3 * L * L
-    elif name in ("ea", "ea_batch"):
+    elif name in ("ea", "ea_batch", "ea_measure"):
         betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
         lat = sp.Lattice(B.SPIN_EA, 3, 16, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=1)
-        if name == "ea":
+        if name == "ea_measure":
+            # E, M and Q of every realisation, slot and set after two sweeps
+            B.spin_sweep(lat.h, lat.couplings, betas, 2, lat.seed)
+            lat.measure()
+            a.record(stream)
+            for _ in range(4):
+                lat.measure()
+            b.record(stream)
+            flips = 4 * 2 ** 28  # spins read
+        elif name == "ea":
             B.spin_sweep(lat.h, lat.couplings, betas, 2, lat.seed)
             a.record(stream)
             B.spin_sweep(lat.h, lat.couplings, betas, 2, lat.seed)
@@ -722,7 +731,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, heis, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, ea_measure, heis, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -204,10 +204,8 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   h->g.fgrp = make_fastdiv((uint32_t)std::max(1, desc->n_real / 32));
   h->g.fgrp2 = make_fastdiv((uint32_t)std::max(1, desc->n_real / 64));
   h->n_lat = (int64_t)desc->n_sets * desc->n_temps * desc->n_real;
-  h->variant = (desc->model == SPIN_ISING && desc->dim == 2 && desc->layout == SPIN_I8 &&
-                fused2d_supported(desc->L))
-                   ? 1
-                   : 0;
+  const bool i8_2d = desc->model == SPIN_ISING && desc->dim == 2 && desc->layout == SPIN_I8;
+  h->variant = i8_2d && resident2d_supported(desc->L) ? 3 : (i8_2d && fused2d_supported(desc->L) ? 1 : 0);
   const int nt = desc->n_temps;
   bool ok = cudaMalloc(&h->d_thr, 16 * (size_t)nt) == cudaSuccess &&
             cudaMalloc(&h->d_pt_off, 4 * (size_t)nt) == cudaSuccess &&
@@ -445,10 +443,10 @@ int spin_set_update_order(spin_lattice *h, int32_t order, int32_t tile, int32_t 
 }
 
 int spin_set_variant(spin_lattice *h, int32_t variant) {
-  if (!h || variant < 0 || variant > 2) return SPIN_EINVAL;
-  if (variant == 1 && !(h->d.model == SPIN_ISING && h->d.dim == 2 && h->d.layout == SPIN_I8 &&
-                        fused2d_supported(h->g.L)))
-    return SPIN_EINVAL;
+  if (!h || variant < 0 || variant > 3) return SPIN_EINVAL;
+  const bool i8_2d = h->d.model == SPIN_ISING && h->d.dim == 2 && h->d.layout == SPIN_I8;
+  if (variant == 1 && !(i8_2d && fused2d_supported(h->g.L))) return SPIN_EINVAL;
+  if (variant == 3 && !(i8_2d && resident2d_supported(h->g.L))) return SPIN_EINVAL;
   if (variant == 2 && h->d.model != SPIN_HEISENBERG) return SPIN_EINVAL;
   h->variant = variant;
   return SPIN_OK;

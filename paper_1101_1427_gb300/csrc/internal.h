@@ -117,6 +117,11 @@ int launch_pipe_probe(int op, int blocks_per_sm, uint32_t iters, long long *cloc
 cudaError_t launch_heis_dcb_tiles(spin_lattice *h, int coarse, uint32_t sweep0);
 cudaError_t launch_heis_renorm(spin_lattice *h);
 
+// ising_i8.cu: whole-lattice-in-shared-memory sweeps of small 2D int8
+// ferromagnets (variant 3)
+constexpr int kResidentMaxL = 128;
+bool resident2d_supported(int L);
+
 // dcb.cu
 bool dcb_supported(const spin_lattice *h, int tile);
 cudaError_t launch_sweeps_dcb(spin_lattice *h, int64_t n_sweeps);

@@ -83,6 +83,55 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
       ising_chunk<0>(C, U, D, lb, rb, r, p, thr4, thr8, unused_a, unused_d);
 }
 
+// ---------------------------------------------------------------- 2D resident, small L
+// Small lattices (L % 8 == 0, L <= kResidentMaxL): one CTA keeps a whole
+// lattice in shared memory and runs every sweep of the call on it, the two
+// colour phases separated by a CTA barrier, then writes it back.  Each
+// chunk update is ising2d_phase_kernel's (same chunks, same Philox
+// counters), so n sweeps give the lattice of 2n phase launches; lattices
+// (replicas) map to CTAs, as the paper's tempering code maps replicas to
+// thread blocks (Sec. 7).  Grid: one CTA per lattice; shared memory L^2
+// bytes.
+__global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restrict__ spins, int L,
+                                                               const uint32_t *__restrict__ thr, Geom g,
+                                                               RoundKeys rk, uint32_t sweep0, int n_sweeps) {
+  extern __shared__ __align__(16) uint8_t sl[];  // the lattice, row-major
+  griddep_wait();
+  griddep_release();
+  const uint32_t lat = blockIdx.x;
+  const int LL = L * L;
+  int8_t *base = spins + (int64_t)lat * LL;
+  for (int k = threadIdx.x; k < LL / 16; k += blockDim.x)
+    reinterpret_cast<uint4 *>(sl)[k] = reinterpret_cast<const uint4 *>(base)[k];
+  const int chunks = L >> 3, total = L * chunks;
+  const uint32_t t = slot_of32(g, lat);
+  const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
+  const uint32_t lid = lattice_id32(g, lat);
+  uint64_t *rows = reinterpret_cast<uint64_t *>(sl);
+  __syncthreads();
+  for (int s = 0; s < n_sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+      for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const int y = k / chunks, m = k - y * chunks;
+        const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+        const uint64_t C = rows[k], U = rows[yu * chunks + m], D = rows[yd * chunks + m];
+        // only the byte beyond the chunk on the side the phase needs is read
+        const int p = (colour + y) & 1;
+        const int xe = p ? (m == chunks - 1 ? 0 : 8 * m + 8) : (m == 0 ? L - 1 : 8 * m - 1);
+        const uint64_t e = sl[y * L + xe];
+        // the draw does not depend on the lattice: it overlaps the loads above
+        const uint4 r = philox(make_uint4((uint32_t)k, sweep0 + (uint32_t)s, lid, wctr), rk);
+        long long unused_a = 0, unused_d = 0;
+        rows[k] = ising_chunk<0>(C, U, D, e, e, r, p, thr4, thr8, unused_a, unused_d);
+      }
+      __syncthreads();
+    }
+  }
+  for (int k = threadIdx.x; k < LL / 16; k += blockDim.x)
+    reinterpret_cast<uint4 *>(base)[k] = reinterpret_cast<const uint4 *>(sl)[k];
+}
+
 // ---------------------------------------------------------------- 3D phase, L % 8 == 0
 // The 3D form of the 2D phase kernel: a thread owns the eight bytes
 // x = 8m .. 8m+7 of row y in the planes z0 .. z0+zlen-1 and marches down z.
@@ -215,12 +264,29 @@ cudaError_t launch_couplings_i8(spin_lattice *h) {
 cudaError_t launch_fused2d_i8(spin_lattice *h, int64_t n_sweeps);  // fused2d.cu
 bool fused2d_supported(int L);                                     // fused2d.cu
 
+// Whole lattice in one CTA's shared memory (16 KB at L = 128).
+bool resident2d_supported(int L) { return L % 8 == 0 && L >= 8 && L <= kResidentMaxL; }
+
 cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps) {
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
   const bool fast2d = g.dim == 2 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   const bool fast3d = g.dim == 3 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   if (fast2d && h->variant == 1 && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
+  if (fast2d && h->variant == 3 && resident2d_supported(g.L)) {
+    const int chunks = g.L / 8 * g.L;
+    const int threads = chunks < 512 ? (chunks + 31) / 32 * 32 : 512;
+    // at most 4096 sweeps per launch, so that no launch runs for long
+    for (int64_t done = 0; done < n_sweeps; done += 4096) {
+      const int n = (int)(n_sweeps - done < 4096 ? n_sweeps - done : 4096);
+      const cudaError_t e = launch_dependent(ising2d_resident_kernel, dim3((unsigned)h->n_lat), dim3(threads),
+                                             (size_t)g.L * g.L, h->stream, (int8_t *)h->spins, g.L,
+                                             (const uint32_t *)h->d_thr, g, rk,
+                                             (uint32_t)(h->sweeps_done + done), n);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {

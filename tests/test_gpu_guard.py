@@ -104,6 +104,7 @@ def _run_all(hd, betas, order=None):
 CASES = [
     ("ising2d_i8_phases", (B.SPIN_ISING, 2, 40, B.SPIN_I8), dict(n_temps=3), 0, None),
     ("ising2d_i8_fused", (B.SPIN_ISING, 2, 48, B.SPIN_I8), dict(n_temps=2), 1, None),
+    ("ising2d_i8_resident", (B.SPIN_ISING, 2, 40, B.SPIN_I8), dict(n_temps=3, n_real=2), 3, None),
     ("ising2d_i8_generic", (B.SPIN_ISING, 2, 6, B.SPIN_I8), dict(n_temps=2, n_real=2), 0, None),
     ("ising2d_coded", (B.SPIN_ISING, 2, 256, B.SPIN_MSC1), dict(n_temps=2), None, None),
     ("ising3d_i8_chunks", (B.SPIN_ISING, 3, 24, B.SPIN_I8), dict(n_temps=2), None, None),

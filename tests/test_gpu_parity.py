@@ -64,7 +64,7 @@ def _ising_run_oracle(dim, L, seed, betas, n_real, n_sweeps, first=0):
     return s, E, M
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_ising2d_L64_1000_sweeps_bit_exact(variant):
     """2D Ising L=64, beta = 0.4407, 1000 sweeps, E and M after every sweep."""
     L, seed, beta, n = 64, 1, 0.4407, 1000
@@ -83,6 +83,9 @@ def test_ising2d_L64_1000_sweeps_bit_exact(variant):
     (2, 24, [0.5], 1, 0),             # 2D kernel, L % 16 != 0
     (2, 48, [0.4, 0.45, 0.9], 2, 1),  # fused kernel, several lattices, ragged strips
     (2, 32, [0.0, 5.0], 1, 1),        # infinite and (near) zero temperature
+    (2, 8, [0.3, 0.44], 2, 3),        # resident kernel, one chunk per row
+    (2, 24, [0.5, 0.0], 1, 3),        # resident kernel, three chunks per row
+    (2, 128, [0.4407, 5.0], 2, 3),    # resident kernel, largest lattice
     (3, 8, [0.22, 0.3], 1, 0),        # 3D chunk kernel, one chunk per row
     (3, 16, [0.0, 0.2216, 50.0], 2, 0),  # 3D chunk kernel, degenerate temperatures
     (3, 24, [0.25], 1, 0),            # 3D chunk kernel, odd number of chunks per row
@@ -90,14 +93,31 @@ def test_ising2d_L64_1000_sweeps_bit_exact(variant):
 def test_ising_sweeps_bit_exact(dim, L, betas, n_real, variant):
     seed, n = 5, 13
     lat = sp.Lattice(B.SPIN_ISING, dim, L, B.SPIN_I8, n_real=n_real, n_temps=len(betas), seed=seed)
-    if variant:
-        lat.set_variant(1)
+    lat.set_variant(variant)
     lat.sweep(betas, 5)
     lat.sweep(betas, 8)  # continues the chain
     s, E, M = _ising_run_oracle(dim, L, seed, betas, n_real, n)
     assert np.array_equal(host(lat.spins), s.ravel())
     Eg, Mg, _ = lat.measure()
     assert np.array_equal(host(Eg), E[-1].ravel()) and np.array_equal(host(Mg), M[-1].ravel())
+
+
+def test_resident_long_call_equals_phases_and_oracle():
+    """5000 sweeps in one call: the resident kernel splits them over two
+    launches (at most 4096 sweeps each); the lattices equal those of the
+    in-place phases and of the oracle."""
+    L, seed, n = 16, 9, 5000
+    betas = [0.35, 0.4407, 0.6]
+    a = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=3, seed=seed)
+    b = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=3, seed=seed)
+    a.set_variant(0)
+    assert b.sweeps_done == 0
+    a.sweep(betas, n)
+    b.sweep(betas, n)  # default variant for L <= 128: resident
+    torch.cuda.synchronize()
+    assert torch.equal(a.spins, b.spins)
+    s, _, _ = _ising_run_oracle(2, L, seed, betas, 1, n)
+    assert np.array_equal(host(b.spins), s.ravel())
 
 
 def test_fused_equals_phases_on_large_lattice():

@@ -302,6 +302,36 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
   if (pt_every > 0 && h->d.model == SPIN_HEISENBERG) return SPIN_EINVAL;
   const bool measuring = measure_every > 0 && (E_series || M_series || Q_series || Ef_series || Mf_series);
   int64_t done = 0, k_meas = 0;
+  // small 2D int8 ferromagnets: the resident kernel measures E and M itself,
+  // so a call is one launch per exchange interval
+  const bool resident = measuring && h->d.model == SPIN_ISING && h->d.layout == SPIN_I8 && h->d.dim == 2 &&
+                        h->variant == 3 && resident2d_supported(h->g.L) &&
+                        h->order == SPIN_ORDER_CHECKERBOARD && !Q_series && !Ef_series && !Mf_series;
+  while (resident && done < n_sweeps) {
+    const int64_t cur = h->sweeps_done;
+    int64_t next = n_sweeps - done;
+    if (pt_every > 0) {
+      const int64_t to = pt_every - (cur % pt_every);
+      if (to < next) next = to;
+    }
+    if (cur + next > (int64_t)0xFFFFFFFFll) return SPIN_EINVAL;
+    int rc = upload_thresholds(h, betas);
+    if (rc) return rc;
+    const int64_t nl = h->n_lat;
+    const int first = (int)(measure_every - cur % measure_every);
+    if (launch_resident2d(h, next, E_series ? E_series + k_meas * nl : nullptr,
+                          M_series ? M_series + k_meas * nl : nullptr, measure_every, first) != cudaSuccess)
+      return SPIN_ECUDA;
+    h->sweeps_done += next;
+    done += next;
+    const int64_t now = h->sweeps_done;
+    k_meas += now / measure_every - cur / measure_every;
+    if (pt_every > 0 && now % pt_every == 0) {
+      const int64_t *energies = E_series && now % measure_every == 0 ? E_series + (k_meas - 1) * nl : nullptr;
+      rc = pt_swap(h, couplings, betas, h->d.seed, accepted, energies);
+      if (rc) return rc;
+    }
+  }
   while (done < n_sweeps) {
     // sweep up to the next measurement or exchange point
     const int64_t cur = h->sweeps_done;

@@ -121,6 +121,9 @@ cudaError_t launch_heis_renorm(spin_lattice *h);
 // ferromagnets (variant 3)
 constexpr int kResidentMaxL = 128;
 bool resident2d_supported(int L);
+// n sweeps; with E or M (device, rows of n_lat) also measures after the
+// sweeps first, first + every, ... (1-based in the call) into rows 0, 1, ...
+cudaError_t launch_resident2d(spin_lattice *h, int64_t n_sweeps, int64_t *E, int64_t *M, int every, int first);
 
 // dcb.cu
 bool dcb_supported(const spin_lattice *h, int tile);

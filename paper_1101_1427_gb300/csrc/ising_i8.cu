@@ -91,11 +91,19 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
 // counters), so n sweeps give the lattice of 2n phase launches; lattices
 // (replicas) map to CTAs, as the paper's tempering code maps replicas to
 // thread blocks (Sec. 7).  Grid: one CTA per lattice; shared memory L^2
-// bytes.
+// bytes.  With E or M the kernel also measures after the sweeps s (0-based
+// in the launch) with s + 1 = first + j * every, j = 0, 1, ...: row j of E
+// and M (n_lat entries each) gets E = 2 anti - 2 N and M = N - 2 down of
+// every lattice, the counts of antiparallel bonds (right and down of each
+// site) and of down spins.
 __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restrict__ spins, int L,
                                                                const uint32_t *__restrict__ thr, Geom g,
-                                                               RoundKeys rk, uint32_t sweep0, int n_sweeps) {
+                                                               RoundKeys rk, uint32_t sweep0, int n_sweeps,
+                                                               long long *__restrict__ E,
+                                                               long long *__restrict__ M, int64_t n_lat,
+                                                               int every, int first) {
   extern __shared__ __align__(16) uint8_t sl[];  // the lattice, row-major
+  __shared__ int red[512 / 32][2];
   griddep_wait();
   griddep_release();
   const uint32_t lat = blockIdx.x;
@@ -126,6 +134,36 @@ __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restric
         rows[k] = ising_chunk<0>(C, U, D, e, e, r, p, thr4, thr8, unused_a, unused_d);
       }
       __syncthreads();
+    }
+    const int since = s + 1 - first;
+    if ((E || M) && since >= 0 && since % every == 0) {
+      // bit 1 of a +-1 byte is set for -1: (a ^ b) & 2 marks an antiparallel pair
+      constexpr uint64_t kBit1 = 0x0202020202020202ull;
+      int anti = 0, down = 0;
+      for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const int y = k / chunks, m = k - y * chunks;
+        const int yd = y == L - 1 ? 0 : y + 1;
+        const uint64_t C = rows[k], D = rows[yd * chunks + m];
+        const uint64_t nx = rows[y * chunks + (m == chunks - 1 ? 0 : m + 1)];  // next chunk of the row
+        const uint64_t R = (C >> 8) | (nx << 56);  // right neighbours of the chunk's bytes
+        anti += __popcll((C ^ R) & kBit1) + __popcll((C ^ D) & kBit1);
+        down += __popcll(C & kBit1);
+      }
+      anti = __reduce_add_sync(0xffffffffu, anti);
+      down = __reduce_add_sync(0xffffffffu, down);
+      if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = anti;
+        red[threadIdx.x >> 5][1] = down;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long a = 0, d = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w][0], d += red[w][1];
+        const int64_t at = (int64_t)(since / every) * n_lat + lat;
+        if (E) E[at] = 2 * a - 2 * (long long)LL;
+        if (M) M[at] = (long long)LL - 2 * d;
+      }
+      // the next measurement rewrites red only after this sweep's barriers
     }
   }
   for (int k = threadIdx.x; k < LL / 16; k += blockDim.x)
@@ -267,26 +305,38 @@ bool fused2d_supported(int L);                                     // fused2d.cu
 // Whole lattice in one CTA's shared memory (16 KB at L = 128).
 bool resident2d_supported(int L) { return L % 8 == 0 && L >= 8 && L <= kResidentMaxL; }
 
+cudaError_t launch_resident2d(spin_lattice *h, int64_t n_sweeps, int64_t *E, int64_t *M, int every, int first) {
+  const Geom &g = h->g;
+  const RoundKeys rk = make_round_keys(h->d.seed);
+  const int chunks = g.L / 8 * g.L;
+  const int threads = chunks < 512 ? (chunks + 31) / 32 * 32 : 512;
+  // at most 4096 sweeps per launch, so that no launch runs for long; the
+  // measurement rows continue from launch to launch
+  for (int64_t done = 0; done < n_sweeps; done += 4096) {
+    const int n = (int)(n_sweeps - done < 4096 ? n_sweeps - done : 4096);
+    int64_t row = 0, f = first - done;  // f: first measured sweep, 1-based within this launch
+    if (f < 1) {
+      row = (done - first + every) / every;  // measurements before this launch
+      f = first + row * every - done;
+    }
+    const cudaError_t e = launch_dependent(
+        ising2d_resident_kernel, dim3((unsigned)h->n_lat), dim3(threads), (size_t)g.L * g.L, h->stream,
+        (int8_t *)h->spins, g.L, (const uint32_t *)h->d_thr, g, rk, (uint32_t)(h->sweeps_done + done), n,
+        (long long *)(E ? E + row * h->n_lat : nullptr), (long long *)(M ? M + row * h->n_lat : nullptr),
+        h->n_lat, every, (int)f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps) {
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
   const bool fast2d = g.dim == 2 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   const bool fast3d = g.dim == 3 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   if (fast2d && h->variant == 1 && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
-  if (fast2d && h->variant == 3 && resident2d_supported(g.L)) {
-    const int chunks = g.L / 8 * g.L;
-    const int threads = chunks < 512 ? (chunks + 31) / 32 * 32 : 512;
-    // at most 4096 sweeps per launch, so that no launch runs for long
-    for (int64_t done = 0; done < n_sweeps; done += 4096) {
-      const int n = (int)(n_sweeps - done < 4096 ? n_sweeps - done : 4096);
-      const cudaError_t e = launch_dependent(ising2d_resident_kernel, dim3((unsigned)h->n_lat), dim3(threads),
-                                             (size_t)g.L * g.L, h->stream, (int8_t *)h->spins, g.L,
-                                             (const uint32_t *)h->d_thr, g, rk,
-                                             (uint32_t)(h->sweeps_done + done), n);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  }
+  if (fast2d && h->variant == 3 && resident2d_supported(g.L))
+    return launch_resident2d(h, n_sweeps, nullptr, nullptr, 1, 1);
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {

@@ -283,6 +283,7 @@ def side_configs(torch, sp, B, stream):
     ea2.close()
     out.update(uneven_batch(torch, sp, B, stream))
     out.update(ising_pt(torch, sp, B, stream))
+    out.update(ising2d_small(torch, sp, B, stream))
     out.update(dcb(torch, sp, B, stream))
     out.update(ising3d(torch, sp, B, stream))
     return out
@@ -334,6 +335,27 @@ def dcb(torch, sp, B, stream):
         torch.cuda.synchronize()
         out[f"ising2d_dcb_T{T}_k{k}_flips_per_ns"] = k * len(BETAS) * L * L / (a.elapsed_time(b) * 1e6)
     lat.close()
+    return out
+
+
+def ising2d_small(torch, sp, B, stream):
+    """2D Ising L = 64, int8, beta = 0.4407, 1000 sweeps with E and M after
+    every sweep (one spin_run call), with the resident kernel (which
+    measures itself: one launch) and with the fused pass plus a separate
+    measurement per sweep."""
+    out = {}
+    for variant, name in ((3, "resident"), (1, "fused")):
+        lat = sp.Lattice(B.SPIN_ISING, 2, 64, B.SPIN_I8, seed=1)
+        lat.set_variant(variant)
+        ser = lat.series_buffers(1000)
+        B.spin_run(lat.h, None, [0.4407], 20, 1, 0, ser["E"], ser["M"], None, None, None, None)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_run(lat.h, None, [0.4407], 1000, 1, 0, ser["E"], ser["M"], None, None, None, None)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"ising2d_L64_1000sweeps_EM_every_sweep_{name}_flips_per_ns"] = 1000 * 64 * 64 / (a.elapsed_time(b) * 1e6)
+        lat.close()
     return out
 
 
@@ -686,7 +708,8 @@ def run_case(name):
         print(json.dumps({"case": name, **dcb(torch, sp, B, stream)}), flush=True)
         return
     elif name == "ising_pt":
-        print(json.dumps({"case": name, **ising_pt(torch, sp, B, stream)}), flush=True)
+        print(json.dumps({"case": name, **ising_pt(torch, sp, B, stream), **ising2d_small(torch, sp, B, stream)}),
+              flush=True)
         return
     elif name == "uneven":
         print(json.dumps({"case": name, **uneven_batch(torch, sp, B, stream, n=8)}), flush=True)

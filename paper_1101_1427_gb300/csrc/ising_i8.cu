@@ -96,6 +96,11 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
 // and M (n_lat entries each) gets E = 2 anti - 2 N and M = N - 2 down of
 // every lattice, the counts of antiparallel bonds (right and down of each
 // site) and of down spins.
+// kPer: chunks per thread (total chunks <= 512 kPer).  A thread's chunks,
+// their neighbour chunks and edge bytes, and (for kPer <= 2, where the
+// registers allow) the part of each Philox call that does not depend on the
+// sweep (PhiloxX1) are set up once per launch.
+template <int kPer>
 __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restrict__ spins, int L,
                                                                const uint32_t *__restrict__ thr, Geom g,
                                                                RoundKeys rk, uint32_t sweep0, int n_sweeps,
@@ -116,22 +121,42 @@ __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restric
   const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2);
   const uint32_t lid = lattice_id32(g, lat);
   uint64_t *rows = reinterpret_cast<uint64_t *>(sl);
+  constexpr bool kHoist = kPer <= 2;
+  int ku[kPer], kd[kPer], xe[kPer][2], py[kPer];
+  PhiloxX1 pre[kPer][2];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int k = threadIdx.x + i * blockDim.x;
+    if (k >= total) break;
+    const int y = k / chunks, m = k - y * chunks;
+    const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+    ku[i] = yu * chunks + m;
+    kd[i] = yd * chunks + m;
+    py[i] = y & 1;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      // only the byte beyond the chunk on the side the phase needs is read
+      const int p = (c + y) & 1;
+      xe[i][c] = y * L + (p ? (m == chunks - 1 ? 0 : 8 * m + 8) : (m == 0 ? L - 1 : 8 * m - 1));
+      if (kHoist) pre[i][c] = philox_x1_setup((uint32_t)k, lid, ctr_w(TAG_UPDATE, (uint32_t)c, 0), rk);
+    }
+  }
   __syncthreads();
   for (int s = 0; s < n_sweeps; ++s) {
+#pragma unroll
     for (int colour = 0; colour < 2; ++colour) {
-      const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
-      for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const int y = k / chunks, m = k - y * chunks;
-        const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
-        const uint64_t C = rows[k], U = rows[yu * chunks + m], D = rows[yd * chunks + m];
-        // only the byte beyond the chunk on the side the phase needs is read
-        const int p = (colour + y) & 1;
-        const int xe = p ? (m == chunks - 1 ? 0 : 8 * m + 8) : (m == 0 ? L - 1 : 8 * m - 1);
-        const uint64_t e = sl[y * L + xe];
-        // the draw does not depend on the lattice: it overlaps the loads above
-        const uint4 r = philox(make_uint4((uint32_t)k, sweep0 + (uint32_t)s, lid, wctr), rk);
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k >= total) break;
+        const uint64_t C = rows[k], U = rows[ku[i]], D = rows[kd[i]];
+        const uint64_t e = sl[xe[i][colour]];
+        const uint4 r = kHoist ? philox_x1(pre[i][colour], sweep0 + (uint32_t)s, rk)
+                               : philox(make_uint4((uint32_t)k, sweep0 + (uint32_t)s, lid,
+                                                   ctr_w(TAG_UPDATE, (uint32_t)colour, 0)),
+                                        rk);
         long long unused_a = 0, unused_d = 0;
-        rows[k] = ising_chunk<0>(C, U, D, e, e, r, p, thr4, thr8, unused_a, unused_d);
+        rows[k] = ising_chunk<0>(C, U, D, e, e, r, colour ^ py[i], thr4, thr8, unused_a, unused_d);
       }
       __syncthreads();
     }
@@ -319,8 +344,10 @@ cudaError_t launch_resident2d(spin_lattice *h, int64_t n_sweeps, int64_t *E, int
       row = (done - first + every) / every;  // measurements before this launch
       f = first + row * every - done;
     }
+    auto *kern = chunks <= 512 ? ising2d_resident_kernel<1>
+                               : (chunks <= 1024 ? ising2d_resident_kernel<2> : ising2d_resident_kernel<4>);
     const cudaError_t e = launch_dependent(
-        ising2d_resident_kernel, dim3((unsigned)h->n_lat), dim3(threads), (size_t)g.L * g.L, h->stream,
+        kern, dim3((unsigned)h->n_lat), dim3(threads), (size_t)g.L * g.L, h->stream,
         (int8_t *)h->spins, g.L, (const uint32_t *)h->d_thr, g, rk, (uint32_t)(h->sweeps_done + done), n,
         (long long *)(E ? E + row * h->n_lat : nullptr), (long long *)(M ? M + row * h->n_lat : nullptr),
         h->n_lat, every, (int)f);

@@ -85,7 +85,8 @@ def test_ising2d_L64_1000_sweeps_bit_exact(variant):
     (2, 32, [0.0, 5.0], 1, 1),        # infinite and (near) zero temperature
     (2, 8, [0.3, 0.44], 2, 3),        # resident kernel, one chunk per row
     (2, 24, [0.5, 0.0], 1, 3),        # resident kernel, three chunks per row
-    (2, 128, [0.4407, 5.0], 2, 3),    # resident kernel, largest lattice
+    (2, 80, [0.44, 0.3], 1, 3),       # resident kernel, two chunks per thread
+    (2, 128, [0.4407, 5.0], 2, 3),    # resident kernel, largest lattice (four chunks per thread)
     (3, 8, [0.22, 0.3], 1, 0),        # 3D chunk kernel, one chunk per row
     (3, 16, [0.0, 0.2216, 50.0], 2, 0),  # 3D chunk kernel, degenerate temperatures
     (3, 24, [0.25], 1, 0),            # 3D chunk kernel, odd number of chunks per row

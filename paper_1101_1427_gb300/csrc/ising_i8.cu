@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restric
   const uint32_t lid = lattice_id32(g, lat);
   uint64_t *rows = reinterpret_cast<uint64_t *>(sl);
   constexpr bool kHoist = kPer <= 2;
-  int ku[kPer], kd[kPer], xe[kPer][2], py[kPer];
+  int ku[kPer], kd[kPer], kn[kPer], xe[kPer][2], py[kPer];  // kn: next chunk of the row
   PhiloxX1 pre[kPer][2];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restric
     const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
     ku[i] = yu * chunks + m;
     kd[i] = yd * chunks + m;
+    kn[i] = y * chunks + (m == chunks - 1 ? 0 : m + 1);
     py[i] = y & 1;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -165,11 +166,11 @@ __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restric
       // bit 1 of a +-1 byte is set for -1: (a ^ b) & 2 marks an antiparallel pair
       constexpr uint64_t kBit1 = 0x0202020202020202ull;
       int anti = 0, down = 0;
-      for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const int y = k / chunks, m = k - y * chunks;
-        const int yd = y == L - 1 ? 0 : y + 1;
-        const uint64_t C = rows[k], D = rows[yd * chunks + m];
-        const uint64_t nx = rows[y * chunks + (m == chunks - 1 ? 0 : m + 1)];  // next chunk of the row
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k >= total) break;
+        const uint64_t C = rows[k], D = rows[kd[i]], nx = rows[kn[i]];
         const uint64_t R = (C >> 8) | (nx << 56);  // right neighbours of the chunk's bytes
         anti += __popcll((C ^ R) & kBit1) + __popcll((C ^ D) & kBit1);
         down += __popcll(C & kBit1);

@@ -338,6 +338,34 @@ def dcb(torch, sp, B, stream):
     return out
 
 
+def ising_pt_sizes(torch, sp, B, stream):
+    """The tempering benchmark over lattice sizes (the paper plots its flip
+    time against L, Sec. 7): 20 int8 replicas, beta in [0.1, 0.15], one
+    exchange per 100 sweeps, with the resident kernel (L <= 128) and the
+    fused pass (L >= 32)."""
+    import numpy as np
+    out = {}
+    betas = list(np.linspace(0.1, 0.15, 20))
+    for Lp in (16, 32, 64, 128, 256, 512, 1024, 2048):
+        n = 400 if Lp <= 256 else 200
+        for variant, name in ((3, "resident"), (1, "fused")):
+            lat = sp.Lattice(B.SPIN_ISING, 2, Lp, B.SPIN_I8, n_temps=20, seed=70)
+            try:
+                lat.set_variant(variant)
+            except B.SpinError:
+                lat.close()
+                continue
+            B.spin_run(lat.h, None, betas, 100, 0, 100, None, None, None, None, None, None)
+            a, b = _events(torch)
+            a.record(stream)
+            B.spin_run(lat.h, None, betas, n, 0, 100, None, None, None, None, None, None)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out[f"L{Lp}_{name}"] = round(n * 20 * Lp * Lp / (a.elapsed_time(b) * 1e6), 2)
+            lat.close()
+    return out
+
+
 def ising2d_small(torch, sp, B, stream):
     """2D Ising L = 64, int8, beta = 0.4407, 1000 sweeps with E and M after
     every sweep (one spin_run call), with the resident kernel (which
@@ -707,6 +735,9 @@ def run_case(name):
     elif name == "dcb":
         print(json.dumps({"case": name, **dcb(torch, sp, B, stream)}), flush=True)
         return
+    elif name == "ising_pt_sizes":
+        print(json.dumps({"case": name, **ising_pt_sizes(torch, sp, B, stream)}), flush=True)
+        return
     elif name == "ising_pt":
         print(json.dumps({"case": name, **ising_pt(torch, sp, B, stream), **ising2d_small(torch, sp, B, stream)}),
               flush=True)
@@ -755,7 +786,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, ea_measure, heis, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
+                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, ea_measure, ising_pt_sizes, heis, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

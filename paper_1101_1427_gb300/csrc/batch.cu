@@ -24,6 +24,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bitslice.cuh"
 #include "ea_cs.cuh"
 #include "i8chunk.cuh"
 #include "internal.h"
@@ -155,33 +156,6 @@ __device__ __forceinline__ void add3(uint32_t (&C)[kPl], uint32_t x0, uint32_t x
   }
 }
 
-__device__ __forceinline__ void add1(uint32_t (&C)[kPl], uint32_t x) {
-#pragma unroll
-  for (int k = 0; k < kPl; ++k) {
-    const uint32_t n = C[k] & x;
-    C[k] ^= x;
-    x = n;
-  }
-}
-
-// counter planes += bit-plane x of weight 2^w (w > 0), ripple from level w
-template <int W>
-__device__ __forceinline__ void add_at(uint32_t (&C)[kPl], uint32_t x) {
-#pragma unroll
-  for (int k = W; k < kPl; ++k) {
-    const uint32_t n = C[k] & x;
-    C[k] ^= x;
-    x = n;
-  }
-}
-
-// carry-save adder: (h, l) = 2h + l = a + b + c per bit
-__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
-  const uint32_t u = a ^ b;
-  h = (a & b) | (u & c);
-  l = u ^ c;
-}
-
 // Harley-Seal counting of 1-bit planes: eight planes go through seven
 // carry-save adders into (ones, twos, fours) and one plane of weight 8,
 // which is rippled into the counter; flush() adds the remainders.
@@ -201,12 +175,12 @@ struct HsCount {
     csa(twosB, ones, ones, x[6], x[7]);
     csa(foursB, twos, twos, twosA, twosB);
     csa(eights, fours, fours, foursA, foursB);
-    add_at<3>(C, eights);
+    ripple_at<3>(C, eights);
   }
   __device__ __forceinline__ void flush() {
-    add_at<2>(C, fours);
-    add_at<1>(C, twos);
-    add1(C, ones);
+    ripple_at<2>(C, fours);
+    ripple_at<1>(C, twos);
+    ripple_at<0>(C, ones);
     ones = twos = fours = 0;
   }
 };
@@ -325,7 +299,7 @@ __device__ __forceinline__ void count_words(HsCount &hc, const uint32_t *a, cons
     hc.add8(x);
   }
   hc.flush();
-  for (; i < N; i += stride) add1(hc.C, b ? (a[i] ^ b[i]) : a[i]);
+  for (; i < N; i += stride) ripple_at<0>(hc.C, b ? (a[i] ^ b[i]) : a[i]);
 }
 
 // Per-bit counts of the set bits of n_items word arrays of N words each

@@ -1,6 +1,7 @@
 // Reductions (energy, magnetisation, overlap; Sec. 4 measurements by
 // parallel reduction, double accumulation for continuous spins, Sec. 5)
 // and the replica-exchange step (Eq. parallel_tempering, Sec. 7).
+#include "bitslice.cuh"
 #include "ea_cs.cuh"
 #include "internal.h"
 
@@ -268,23 +269,6 @@ constexpr int kRowItems = 16;
 constexpr int kRP = 8;   // per-thread planes: at most 16 quads x 4 sites x 3 bonds = 192 < 256
 constexpr int kRW = 13;  // per-warp planes: at most 32 x 192 = 6144 < 8192
 
-__device__ __forceinline__ void csa3(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
-  const uint32_t u = a ^ b;
-  h = (a & b) | (u & c);
-  l = u ^ c;
-}
-
-// counter planes from level W up += x (weight 2^W)
-template <int W, int K>
-__device__ __forceinline__ void ripple_at(uint32_t (&C)[K], uint32_t x) {
-#pragma unroll
-  for (int k = W; k < K; ++k) {
-    const uint32_t n = C[k] & x;
-    C[k] ^= x;
-    x = n;
-  }
-}
-
 // Running count of weight-1 words: planes o1, o2, o4 and the counter above.
 struct CsaCount {
   uint32_t C[kRP];
@@ -295,9 +279,9 @@ struct CsaCount {
   }
   __device__ __forceinline__ void add4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
     uint32_t t1, t2, f;
-    csa3(t1, o1, o1, x0, x1);
-    csa3(t2, o1, o1, x2, x3);
-    csa3(f, o2, o2, t1, t2);
+    csa(t1, o1, o1, x0, x1);
+    csa(t2, o1, o1, x2, x3);
+    csa(f, o2, o2, t1, t2);
     const uint32_t e = o4 & f;
     o4 ^= f;
     ripple_at<3>(C, e);
@@ -320,15 +304,15 @@ struct CsaCount2 {
   }
   __device__ __forceinline__ void add(const uint32_t (&sv)[4], const uint32_t (&cv)[4]) {
     uint32_t t1, t2, f1, f2, f3, e1, x;
-    csa3(t1, o1, o1, sv[0], sv[1]);
-    csa3(t2, o1, o1, sv[2], sv[3]);
-    csa3(f1, o2, o2, t1, t2);
-    csa3(f2, o2, o2, cv[0], cv[1]);
-    csa3(f3, o2, o2, cv[2], cv[3]);
-    csa3(e1, o4, o4, f1, f2);
+    csa(t1, o1, o1, sv[0], sv[1]);
+    csa(t2, o1, o1, sv[2], sv[3]);
+    csa(f1, o2, o2, t1, t2);
+    csa(f2, o2, o2, cv[0], cv[1]);
+    csa(f3, o2, o2, cv[2], cv[3]);
+    csa(e1, o4, o4, f1, f2);
     const uint32_t e2 = o4 & f3;
     o4 ^= f3;
-    csa3(x, o8, o8, e1, e2);
+    csa(x, o8, o8, e1, e2);
     ripple_at<4>(C, x);
   }
   __device__ __forceinline__ void flush() {

@@ -304,11 +304,13 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
 /* Kernel variant.  2D int8 ferromagnet: 0 = two in-place colour phases per
  * sweep, 1 = one fused out-of-place pass per sweep (default for L > 128),
  * 3 = resident: one CTA per lattice holds the whole lattice in shared
- * memory for all sweeps of a call (default for L % 8 == 0, L <= 128; the
- * paper's tempering code likewise maps replicas to thread blocks, Sec. 7);
- * all three give identical results.  Heisenberg: 0 = the full-accuracy FP32 library
- * functions (default), 2 = hardware approximations of sin, cos and exp (the
- * paper's "fast_math" mode, Sec. 5), within the same tolerances. */
+ * memory for all sweeps of a call and measures E and M itself (default for
+ * L % 8 == 0, L <= 128; the paper's tempering code likewise maps replicas
+ * to thread blocks, Sec. 7); all three give identical results.  3D int8
+ * ferromagnet: 0 = colour phases, 3 = resident (default for L % 8 == 0,
+ * L <= 24), identical results.  Heisenberg: 0 = the full-accuracy FP32
+ * library functions (default), 2 = hardware approximations of sin, cos and
+ * exp (the paper's "fast_math" mode, Sec. 5), within the same tolerances. */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
 /* Slab decomposition of one 2D int8 ferromagnet over several GPUs (the

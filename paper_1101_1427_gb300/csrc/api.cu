@@ -204,8 +204,8 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   h->g.fgrp = make_fastdiv((uint32_t)std::max(1, desc->n_real / 32));
   h->g.fgrp2 = make_fastdiv((uint32_t)std::max(1, desc->n_real / 64));
   h->n_lat = (int64_t)desc->n_sets * desc->n_temps * desc->n_real;
-  const bool i8_2d = desc->model == SPIN_ISING && desc->dim == 2 && desc->layout == SPIN_I8;
-  h->variant = i8_2d && resident2d_supported(desc->L) ? 3 : (i8_2d && fused2d_supported(desc->L) ? 1 : 0);
+  const bool i8 = desc->model == SPIN_ISING && desc->layout == SPIN_I8, i8_2d = i8 && desc->dim == 2;
+  h->variant = i8 && resident_supported(desc->dim, desc->L) ? 3 : (i8_2d && fused2d_supported(desc->L) ? 1 : 0);
   const int nt = desc->n_temps;
   bool ok = cudaMalloc(&h->d_thr, 16 * (size_t)nt) == cudaSuccess &&
             cudaMalloc(&h->d_pt_off, 4 * (size_t)nt) == cudaSuccess &&
@@ -302,11 +302,11 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
   if (pt_every > 0 && h->d.model == SPIN_HEISENBERG) return SPIN_EINVAL;
   const bool measuring = measure_every > 0 && (E_series || M_series || Q_series || Ef_series || Mf_series);
   int64_t done = 0, k_meas = 0;
-  // small 2D int8 ferromagnets: the resident kernel measures E and M itself,
+  // small int8 ferromagnets: the resident kernel measures E and M itself,
   // so a call is one launch per exchange interval
-  const bool resident = measuring && h->d.model == SPIN_ISING && h->d.layout == SPIN_I8 && h->d.dim == 2 &&
-                        h->variant == 3 && resident2d_supported(h->g.L) &&
-                        h->order == SPIN_ORDER_CHECKERBOARD && !Q_series && !Ef_series && !Mf_series;
+  const bool resident = measuring && h->d.model == SPIN_ISING && h->d.layout == SPIN_I8 && h->variant == 3 &&
+                        resident_supported(h->d.dim, h->g.L) && h->order == SPIN_ORDER_CHECKERBOARD &&
+                        !Q_series && !Ef_series && !Mf_series;
   while (resident && done < n_sweeps) {
     const int64_t cur = h->sweeps_done;
     int64_t next = n_sweeps - done;
@@ -319,7 +319,7 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
     if (rc) return rc;
     const int64_t nl = h->n_lat;
     const int first = (int)(measure_every - cur % measure_every);
-    if (launch_resident2d(h, next, E_series ? E_series + k_meas * nl : nullptr,
+    if (launch_resident(h, next, E_series ? E_series + k_meas * nl : nullptr,
                           M_series ? M_series + k_meas * nl : nullptr, measure_every, first) != cudaSuccess)
       return SPIN_ECUDA;
     h->sweeps_done += next;
@@ -474,9 +474,9 @@ int spin_set_update_order(spin_lattice *h, int32_t order, int32_t tile, int32_t 
 
 int spin_set_variant(spin_lattice *h, int32_t variant) {
   if (!h || variant < 0 || variant > 3) return SPIN_EINVAL;
-  const bool i8_2d = h->d.model == SPIN_ISING && h->d.dim == 2 && h->d.layout == SPIN_I8;
+  const bool i8 = h->d.model == SPIN_ISING && h->d.layout == SPIN_I8, i8_2d = i8 && h->d.dim == 2;
   if (variant == 1 && !(i8_2d && fused2d_supported(h->g.L))) return SPIN_EINVAL;
-  if (variant == 3 && !(i8_2d && resident2d_supported(h->g.L))) return SPIN_EINVAL;
+  if (variant == 3 && !(i8 && resident_supported(h->d.dim, h->g.L))) return SPIN_EINVAL;
   if (variant == 2 && h->d.model != SPIN_HEISENBERG) return SPIN_EINVAL;
   h->variant = variant;
   return SPIN_OK;

@@ -117,13 +117,14 @@ int launch_pipe_probe(int op, int blocks_per_sm, uint32_t iters, long long *cloc
 cudaError_t launch_heis_dcb_tiles(spin_lattice *h, int coarse, uint32_t sweep0);
 cudaError_t launch_heis_renorm(spin_lattice *h);
 
-// ising_i8.cu: whole-lattice-in-shared-memory sweeps of small 2D int8
-// ferromagnets (variant 3)
-constexpr int kResidentMaxL = 128;
-bool resident2d_supported(int L);
+// ising_i8.cu: whole-lattice-in-shared-memory sweeps of small 2D and 3D
+// int8 ferromagnets (variant 3)
+constexpr int kResidentMaxL = 128;  // 2D
+constexpr int kResident3MaxL = 24;  // 3D (four chunks per thread of 512)
+bool resident_supported(int dim, int L);
 // n sweeps; with E or M (device, rows of n_lat) also measures after the
 // sweeps first, first + every, ... (1-based in the call) into rows 0, 1, ...
-cudaError_t launch_resident2d(spin_lattice *h, int64_t n_sweeps, int64_t *E, int64_t *M, int every, int first);
+cudaError_t launch_resident(spin_lattice *h, int64_t n_sweeps, int64_t *E, int64_t *M, int every, int first);
 
 // dcb.cu
 bool dcb_supported(const spin_lattice *h, int tile);

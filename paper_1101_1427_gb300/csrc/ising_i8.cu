@@ -96,6 +96,26 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
 // and M (n_lat entries each) gets E = 2 anti - 2 N and M = N - 2 down of
 // every lattice, the counts of antiparallel bonds (right and down of each
 // site) and of down spins.
+// Adds the CTA's counts of antiparallel bonds and down spins and stores
+// E = 2 anti - bonds and M = sites - 2 down at E[at], M[at].
+__device__ __forceinline__ void resident_put(int anti, int down, int (*red)[2], long long *E, long long *M,
+                                             int64_t at, long long sites, long long bonds) {
+  anti = __reduce_add_sync(0xffffffffu, anti);
+  down = __reduce_add_sync(0xffffffffu, down);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = anti;
+    red[threadIdx.x >> 5][1] = down;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long a = 0, d = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w][0], d += red[w][1];
+    if (E) E[at] = 2 * a - bonds;
+    if (M) M[at] = sites - 2 * d;
+  }
+  // the next measurement rewrites red only after the next sweep's barriers
+}
+
 // kPer: chunks per thread (total chunks <= 512 kPer).  A thread's chunks,
 // their neighbour chunks and edge bytes, and (for kPer <= 2, where the
 // registers allow) the part of each Philox call that does not depend on the
@@ -175,24 +195,94 @@ __global__ void __launch_bounds__(512) ising2d_resident_kernel(int8_t *__restric
         anti += __popcll((C ^ R) & kBit1) + __popcll((C ^ D) & kBit1);
         down += __popcll(C & kBit1);
       }
-      anti = __reduce_add_sync(0xffffffffu, anti);
-      down = __reduce_add_sync(0xffffffffu, down);
-      if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5][0] = anti;
-        red[threadIdx.x >> 5][1] = down;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        long long a = 0, d = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w][0], d += red[w][1];
-        const int64_t at = (int64_t)(since / every) * n_lat + lat;
-        if (E) E[at] = 2 * a - 2 * (long long)LL;
-        if (M) M[at] = (long long)LL - 2 * d;
-      }
-      // the next measurement rewrites red only after this sweep's barriers
+      resident_put(anti, down, red, E, M, (int64_t)(since / every) * n_lat + lat, LL, 2 * (long long)LL);
     }
   }
   for (int k = threadIdx.x; k < LL / 16; k += blockDim.x)
+    reinterpret_cast<uint4 *>(base)[k] = reinterpret_cast<const uint4 *>(sl)[k];
+}
+
+// The 3D form (L % 8 == 0, L <= kResident3MaxL, the cube in shared memory):
+// chunk k = (z L + y) L / 8 + m is the chunk of ising3d_phase_kernel with the
+// same Philox counter; its neighbours are the same chunk column's words in
+// rows y -+ 1 and planes z -+ 1 and one edge byte (ising3d_chunk).  E counts
+// the bonds to x + 1, y + 1 and z + 1 of every site (3 N bonds).
+template <int kPer>
+__global__ void __launch_bounds__(512) ising3d_resident_kernel(int8_t *__restrict__ spins, int L,
+                                                               const uint32_t *__restrict__ thr, Geom g,
+                                                               RoundKeys rk, uint32_t sweep0, int n_sweeps,
+                                                               long long *__restrict__ E,
+                                                               long long *__restrict__ M, int64_t n_lat,
+                                                               int every, int first) {
+  extern __shared__ __align__(16) uint8_t sl[];  // the cube, [z][y][x]
+  __shared__ int red[512 / 32][2];
+  griddep_wait();
+  griddep_release();
+  const uint32_t lat = blockIdx.x;
+  const int LL = L * L, N = LL * L;
+  int8_t *base = spins + (int64_t)lat * N;
+  for (int k = threadIdx.x; k < N / 16; k += blockDim.x)
+    reinterpret_cast<uint4 *>(sl)[k] = reinterpret_cast<const uint4 *>(base)[k];
+  const int chunks = L >> 3, plane = L * chunks, total = L * plane;  // chunks per row, plane, cube
+  const uint32_t t = slot_of32(g, lat);
+  const uint32_t thr4 = __ldg(thr + 4 * t + 1), thr8 = __ldg(thr + 4 * t + 2), thr12 = __ldg(thr + 4 * t + 3);
+  const uint32_t lid = lattice_id32(g, lat);
+  uint64_t *w = reinterpret_cast<uint64_t *>(sl);
+  // per chunk: rows y - 1, y + 1, planes z - 1, z + 1, the next chunk of the
+  // row, the edge byte of each colour and the parity of y + z
+  int ku[kPer], kd[kPer], kf[kPer], kb[kPer], kn[kPer], xe[kPer][2], pyz[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int k = threadIdx.x + i * blockDim.x;
+    if (k >= total) break;
+    const int z = k / plane, r = k - z * plane, y = r / chunks, m = r - y * chunks;
+    const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+    const int zf = z == 0 ? L - 1 : z - 1, zb = z == L - 1 ? 0 : z + 1;
+    ku[i] = z * plane + yu * chunks + m;
+    kd[i] = z * plane + yd * chunks + m;
+    kf[i] = zf * plane + y * chunks + m;
+    kb[i] = zb * plane + y * chunks + m;
+    kn[i] = z * plane + y * chunks + (m == chunks - 1 ? 0 : m + 1);
+    pyz[i] = (y + z) & 1;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      // only the byte beyond the chunk on the side the phase needs is read
+      const int p = (c + y + z) & 1;
+      xe[i][c] = z * LL + y * L + (p ? (m == chunks - 1 ? 0 : 8 * m + 8) : (m == 0 ? L - 1 : 8 * m - 1));
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < n_sweeps; ++s) {
+#pragma unroll
+    for (int colour = 0; colour < 2; ++colour) {
+      const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k >= total) break;
+        const uint64_t C = w[k], U = w[ku[i]], D = w[kd[i]], F = w[kf[i]], Bk = w[kb[i]];
+        const uint32_t edge = sl[xe[i][colour]];
+        const uint4 r = philox(make_uint4((uint32_t)k, sweep0 + (uint32_t)s, lid, wctr), rk);
+        w[k] = ising3d_chunk(C, U, D, F, Bk, edge, r, colour ^ pyz[i], thr4, thr8, thr12);
+      }
+      __syncthreads();
+    }
+    const int since = s + 1 - first;
+    if ((E || M) && since >= 0 && since % every == 0) {
+      constexpr uint64_t kBit1 = 0x0202020202020202ull;  // bit 1 of a +-1 byte: set for -1
+      int anti = 0, down = 0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k >= total) break;
+        const uint64_t C = w[k], R = (C >> 8) | (w[kn[i]] << 56);
+        anti += __popcll((C ^ R) & kBit1) + __popcll((C ^ w[kd[i]]) & kBit1) + __popcll((C ^ w[kb[i]]) & kBit1);
+        down += __popcll(C & kBit1);
+      }
+      resident_put(anti, down, red, E, M, (int64_t)(since / every) * n_lat + lat, N, 3 * (long long)N);
+    }
+  }
+  for (int k = threadIdx.x; k < N / 16; k += blockDim.x)
     reinterpret_cast<uint4 *>(base)[k] = reinterpret_cast<const uint4 *>(sl)[k];
 }
 
@@ -328,14 +418,27 @@ cudaError_t launch_couplings_i8(spin_lattice *h) {
 cudaError_t launch_fused2d_i8(spin_lattice *h, int64_t n_sweeps);  // fused2d.cu
 bool fused2d_supported(int L);                                     // fused2d.cu
 
-// Whole lattice in one CTA's shared memory (16 KB at L = 128).
-bool resident2d_supported(int L) { return L % 8 == 0 && L >= 8 && L <= kResidentMaxL; }
+// Whole lattice in one CTA's shared memory: 16 KB at L = 128 in 2D, 13.5 KB
+// at L = 24 in 3D (at most four chunks per thread, so that each thread's
+// chunk geometry stays in registers).
+bool resident_supported(int dim, int L) {
+  return L % 8 == 0 && L >= 8 && L <= (dim == 2 ? kResidentMaxL : dim == 3 ? kResident3MaxL : 0);
+}
 
-cudaError_t launch_resident2d(spin_lattice *h, int64_t n_sweeps, int64_t *E, int64_t *M, int every, int first) {
+cudaError_t launch_resident(spin_lattice *h, int64_t n_sweeps, int64_t *E, int64_t *M, int every, int first) {
   const Geom &g = h->g;
   const RoundKeys rk = make_round_keys(h->d.seed);
-  const int chunks = g.L / 8 * g.L;
+  const int64_t sites = g.N;
+  const int chunks = (int)(sites / 8);
   const int threads = chunks < 512 ? (chunks + 31) / 32 * 32 : 512;
+  using Kern = decltype(&ising2d_resident_kernel<1>);
+  Kern kern;
+  if (g.dim == 2)
+    kern = chunks <= 512 ? ising2d_resident_kernel<1>
+                         : (chunks <= 1024 ? ising2d_resident_kernel<2> : ising2d_resident_kernel<4>);
+  else
+    kern = chunks <= 512 ? ising3d_resident_kernel<1>
+                         : (chunks <= 1024 ? ising3d_resident_kernel<2> : ising3d_resident_kernel<4>);
   // at most 4096 sweeps per launch, so that no launch runs for long; the
   // measurement rows continue from launch to launch
   for (int64_t done = 0; done < n_sweeps; done += 4096) {
@@ -345,11 +448,9 @@ cudaError_t launch_resident2d(spin_lattice *h, int64_t n_sweeps, int64_t *E, int
       row = (done - first + every) / every;  // measurements before this launch
       f = first + row * every - done;
     }
-    auto *kern = chunks <= 512 ? ising2d_resident_kernel<1>
-                               : (chunks <= 1024 ? ising2d_resident_kernel<2> : ising2d_resident_kernel<4>);
     const cudaError_t e = launch_dependent(
-        kern, dim3((unsigned)h->n_lat), dim3(threads), (size_t)g.L * g.L, h->stream,
-        (int8_t *)h->spins, g.L, (const uint32_t *)h->d_thr, g, rk, (uint32_t)(h->sweeps_done + done), n,
+        kern, dim3((unsigned)h->n_lat), dim3(threads), (size_t)sites, h->stream, (int8_t *)h->spins, g.L,
+        (const uint32_t *)h->d_thr, g, rk, (uint32_t)(h->sweeps_done + done), n,
         (long long *)(E ? E + row * h->n_lat : nullptr), (long long *)(M ? M + row * h->n_lat : nullptr),
         h->n_lat, every, (int)f);
     if (e != cudaSuccess) return e;
@@ -363,8 +464,8 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
   const bool fast2d = g.dim == 2 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   const bool fast3d = g.dim == 3 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   if (fast2d && h->variant == 1 && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
-  if (fast2d && h->variant == 3 && resident2d_supported(g.L))
-    return launch_resident2d(h, n_sweeps, nullptr, nullptr, 1, 1);
+  if ((fast2d || fast3d) && h->variant == 3 && resident_supported(g.dim, g.L))
+    return launch_resident(h, n_sweeps, nullptr, nullptr, 1, 1);
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {

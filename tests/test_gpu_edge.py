@@ -189,13 +189,15 @@ def test_batched_launch_refuses_2d_coded_glass():
 
 
 def test_variant_is_checked_against_the_handle():
-    """Variant 3 (whole lattice in one CTA's shared memory) exists for 2D
-    int8 ferromagnets with L % 8 == 0 and L <= 128 only, and is their
-    default; elsewhere it is refused and the handle keeps its variant."""
+    """Variant 3 (whole lattice in one CTA's shared memory) exists for int8
+    ferromagnets with L % 8 == 0 and L <= 128 (2D) or L <= 24 (3D) only, and
+    is their default; elsewhere it is refused."""
     small = sp.Lattice(B.SPIN_ISING, 2, 128, B.SPIN_I8, seed=3)
     small.set_variant(3)
+    sp.Lattice(B.SPIN_ISING, 3, 24, B.SPIN_I8, seed=3).set_variant(3)
     for args in ((B.SPIN_ISING, 2, 256, B.SPIN_I8), (B.SPIN_ISING, 2, 20, B.SPIN_I8),
-                 (B.SPIN_ISING, 2, 256, B.SPIN_MSC1), (B.SPIN_ISING, 3, 16, B.SPIN_I8)):
+                 (B.SPIN_ISING, 2, 256, B.SPIN_MSC1), (B.SPIN_ISING, 3, 32, B.SPIN_I8),
+                 (B.SPIN_ISING, 3, 12, B.SPIN_I8)):
         lat = sp.Lattice(*args, seed=3)
         with pytest.raises(B.SpinError):
             lat.set_variant(3)

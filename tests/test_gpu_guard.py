@@ -107,7 +107,8 @@ CASES = [
     ("ising2d_i8_resident", (B.SPIN_ISING, 2, 40, B.SPIN_I8), dict(n_temps=3, n_real=2), 3, None),
     ("ising2d_i8_generic", (B.SPIN_ISING, 2, 6, B.SPIN_I8), dict(n_temps=2, n_real=2), 0, None),
     ("ising2d_coded", (B.SPIN_ISING, 2, 256, B.SPIN_MSC1), dict(n_temps=2), None, None),
-    ("ising3d_i8_chunks", (B.SPIN_ISING, 3, 24, B.SPIN_I8), dict(n_temps=2), None, None),
+    ("ising3d_i8_chunks", (B.SPIN_ISING, 3, 24, B.SPIN_I8), dict(n_temps=2), 0, None),
+    ("ising3d_i8_resident", (B.SPIN_ISING, 3, 16, B.SPIN_I8), dict(n_temps=2, n_real=2), 3, None),
     ("ising3d_i8_generic", (B.SPIN_ISING, 3, 6, B.SPIN_I8), dict(n_temps=3), None, None),
     ("ising2d_dcb", (B.SPIN_ISING, 2, 64, B.SPIN_I8), dict(n_temps=2), None, (B.SPIN_ORDER_DCB_SYMMETRIC, 16, 2)),
     ("ising3d_dcb8", (B.SPIN_ISING, 3, 32, B.SPIN_I8), dict(n_temps=2), None, (B.SPIN_ORDER_DCB, 8, 2)),

@@ -90,6 +90,9 @@ def test_ising2d_L64_1000_sweeps_bit_exact(variant):
     (3, 8, [0.22, 0.3], 1, 0),        # 3D chunk kernel, one chunk per row
     (3, 16, [0.0, 0.2216, 50.0], 2, 0),  # 3D chunk kernel, degenerate temperatures
     (3, 24, [0.25], 1, 0),            # 3D chunk kernel, odd number of chunks per row
+    (3, 8, [0.22, 0.3], 2, 3),        # 3D resident kernel, one chunk per row
+    (3, 16, [0.0, 0.2216, 50.0], 1, 3),  # 3D resident kernel, degenerate temperatures
+    (3, 24, [0.25], 1, 3),            # 3D resident kernel, four chunks per thread
     (3, 12, [0.25], 2, 0)])           # generic kernel (L % 8 != 0)
 def test_ising_sweeps_bit_exact(dim, L, betas, n_real, variant):
     seed, n = 5, 13

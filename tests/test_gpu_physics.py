@@ -40,6 +40,26 @@ def test_ising2d_parallel_tempering_bit_exact(L, pt_every, me, n):
     assert np.array_equal(acc.cpu().numpy(), acc_o[0])
 
 
+@pytest.mark.parametrize("L,pt_every,me,n", [(8, 2, 1, 9), (16, 4, 3, 12), (24, 1, 1, 5), (12, 2, 1, 6)])
+def test_ising3d_parallel_tempering_bit_exact(L, pt_every, me, n):
+    """The 3D ferromagnet with replica exchange: 10 int8 replicas around the
+    critical coupling, E every `me` sweeps; L % 8 == 0 (L <= 24) runs the
+    resident kernel, which measures itself, L = 12 the colour phases."""
+    n_t, seed = 10, 23
+    betas = list(np.linspace(0.18, 0.26, n_t))
+    lat = sp.Lattice(B.SPIN_ISING, 3, L, B.SPIN_I8, n_temps=n_t, seed=seed)
+    acc = torch.zeros(n_t, dtype=torch.int64, device="cuda")
+    out = lat.run(betas, n, me, pt_every, accepted=acc)
+    s = np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(0, 0, t)) for t in range(n_t)])[None].copy()
+    Es, _, acc_o, _ = oracle.pt_run(3, L, s, betas, seed, 0, 0, 0, n, pt_every)
+    assert np.array_equal(lat.unpack().cpu().numpy()[:, :, 0], s)
+    assert np.array_equal(out["E"].view(n // me, 1, n_t).cpu().numpy(), Es[me - 1::me])
+    assert np.array_equal(acc.cpu().numpy(), acc_o[0])
+    if n % me == 0 and n % pt_every != 0:  # last row measured after the last exchange
+        M = out["M"].view(n // me, n_t).cpu().numpy()[-1]
+        assert np.array_equal(M, s[0].astype(np.int64).sum(axis=1))
+
+
 def _exact_row():
     for line in open(os.path.join(HERE, "golden", "tab_rng_exact.txt")):
         if line.strip() and not line.startswith("#"):

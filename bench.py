@@ -315,6 +315,20 @@ def ising3d(torch, sp, B, stream):
         torch.cuda.synchronize()
         out[f"ising3d_dcb_T{T}_k{k}_flips_per_ns"] = k * L ** 3 / (a.elapsed_time(b) * 1e6)
     lat.close()
+    # small lattices: 20 int8 replicas of L = 16 near the critical coupling,
+    # 200 sweeps in one call, resident kernel against the colour phases
+    betas = [0.2216544] * 20
+    for variant, name in ((3, "resident"), (0, "phases")):
+        sm = sp.Lattice(B.SPIN_ISING, 3, 16, B.SPIN_I8, n_temps=20, seed=33)
+        sm.set_variant(variant)
+        B.spin_sweep(sm.h, None, betas, 10, sm.seed)
+        a, b = _events(torch)
+        a.record(stream)
+        B.spin_sweep(sm.h, None, betas, 200, sm.seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"ising3d_L16x20_{name}_flips_per_ns"] = 200 * 20 * 16 ** 3 / (a.elapsed_time(b) * 1e6)
+        sm.close()
     return out
 
 

@@ -74,7 +74,9 @@ class Lattice:
         B.spin_pt_swap(self.h, self.couplings, list(betas), self.seed, accepted)
 
     def run(self, betas, n_sweeps, measure_every=0, pt_every=0, series=True, accepted=None):
-        n_meas = n_sweeps // measure_every if measure_every > 0 else 0
+        # measurements fall on sweep counts that are multiples of measure_every,
+        # counted from the handle's counter (not from the start of the call)
+        n_meas = B._n_meas(self.h, n_sweeps, measure_every)
         out = {}
         if series and n_meas:
             if self.model == B.SPIN_HEISENBERG:

@@ -411,3 +411,31 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(B.SpinError):
         lat.sweep([-0.1])
     lat.sync()
+
+
+@pytest.mark.parametrize("dim,L", [(2, 16), (3, 8)])
+def test_resident_two_replica_sets_equal_phases(dim, L):
+    """Two replica sets x 2 realisations x 3 slots: the resident kernel
+    (variant 3) keys every lattice as the colour phases do, sweeps alone and
+    in runs that measure E and M in place or, with the overlap requested,
+    through the separate measurement; both sides equal, E and M included."""
+    seed, betas, n = 41, [0.25, 0.44, 0.7], 7
+    a = sp.Lattice(B.SPIN_ISING, dim, L, B.SPIN_I8, n_real=2, n_temps=3, n_sets=2, seed=seed)
+    b = sp.Lattice(B.SPIN_ISING, dim, L, B.SPIN_I8, n_real=2, n_temps=3, n_sets=2, seed=seed)
+    a.set_variant(0)
+    b.set_variant(3)
+    a.sweep(betas, 3)
+    b.sweep(betas, 3)
+    oa, ob = a.run(betas, n, measure_every=2), b.run(betas, n, measure_every=2)
+    for key in ("E", "M", "Q"):
+        assert torch.equal(oa[key], ob[key]), key
+    # E and M only: the resident side measures in place
+    ser = {}
+    for name, lat in (("a", a), ("b", b)):
+        E = torch.zeros(4 * lat.n_lat, dtype=torch.int64, device="cuda")  # ceil(n / 2) rows
+        M = torch.zeros(4 * lat.n_lat, dtype=torch.int64, device="cuda")
+        B.spin_run(lat.h, None, betas, n, 2, 0, E, M, None, None, None, None)
+        ser[name] = (E, M)
+    assert torch.equal(ser["a"][0], ser["b"][0]) and torch.equal(ser["a"][1], ser["b"][1])
+    Ea, Eb = a.measure()[0], b.measure()[0]
+    assert torch.equal(a.spins, b.spins) and torch.equal(Ea, Eb)

@@ -33,3 +33,17 @@ def test_strerror_without_gpu():
     from paper_1101_1427_gb300 import _binding as B
     assert B.strerror(B.SPIN_EINVAL) == "invalid argument"
     assert B.strerror(B.SPIN_ETIMEOUT) == "device-side wait timed out"
+
+
+def test_measurement_rows_follow_the_handle_counter(monkeypatch):
+    """spin_run measures when the handle's sweep count reaches a multiple of
+    measure_every, so the rows a call writes depend on where the counter
+    stands: the binding's count (which sizes Lattice.run's series) equals a
+    brute-force count of those sweeps."""
+    from paper_1101_1427_gb300 import _binding as B
+    for cur in range(0, 13):
+        monkeypatch.setattr(B, "spin_sweeps_done", lambda h, cur=cur: cur)
+        for n in range(0, 11):
+            for every in range(0, 5):
+                want = sum(1 for s in range(cur + 1, cur + n + 1) if every > 0 and s % every == 0)
+                assert B._n_meas(None, n, every) == want, (cur, n, every)

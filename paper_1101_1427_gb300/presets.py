@@ -93,7 +93,8 @@ def run(p, n_sweeps=None):
         outs = []
         items = []
         for lat, m in zip(p.lattices, p.members):
-            ser = lat.series_buffers(n // p.measure_every)
+            # measurements fall on the handle's sweep counts that are multiples of measure_every
+            ser = lat.series_buffers(B._n_meas(lat.h, n, p.measure_every))
             if lat.n_sets < 2:
                 ser.pop("Q", None)
             outs.append(ser)

@@ -33,3 +33,20 @@ def assert_within(estimate, error, exact, nsigma=4.0, floor=0.0, what=""):
     dev = abs(estimate - exact)
     assert dev <= nsigma * error + floor, (
         f"{what}: {estimate} +- {error} vs exact {exact} ({dev / max(error, 1e-300):.2f} sigma)")
+
+
+def binned_variance(x, n_bins=50):
+    """Variance <x^2> - <x>^2 of a correlated series and its jackknife error
+    over n_bins consecutive bins (each leave-one-bin-out estimate uses the
+    means of x and x^2 over the other bins)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = (x.size // n_bins) * n_bins
+    b1 = x[:n].reshape(n_bins, -1).mean(axis=1)
+    b2 = (x[:n] ** 2).reshape(n_bins, -1).mean(axis=1)
+    s1, s2 = b1.sum(), b2.sum()
+    loo1 = (s1 - b1) / (n_bins - 1)
+    loo2 = (s2 - b2) / (n_bins - 1)
+    jk = loo2 - loo1 ** 2
+    full = s2 / n_bins - (s1 / n_bins) ** 2
+    err = np.sqrt((n_bins - 1) / n_bins * ((jk - jk.mean()) ** 2).sum())
+    return float(full), float(err)

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from oracle import exact
-from tests.stats import assert_within, binned_mean
+from tests.stats import assert_within, binned_mean, binned_variance, tau_int
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -63,6 +63,12 @@ def test_mc_4x4_matches_enumeration(beta):
     m_mc, m_err = binned_mean(np.abs(M[1000:]))
     assert_within(e_mc, e_err, bf["E"], what="<E>")
     assert_within(m_mc, m_err, bf["absM"], what="<|M|>")
+    # specific heat per spin C_V = beta^2 (<E^2> - <E>^2) / N (the
+    # definition taken for Tab. rng, which prints C_V without defining it)
+    N = L * L
+    var, var_err = binned_variance(E[1000:])
+    cv_exact = beta * beta * (bf["E2"] - bf["E"] ** 2) / N
+    assert_within(beta * beta * var / N, beta * beta * var_err / N, cv_exact, what="C_V")
 
 
 @pytest.mark.parametrize("beta", [0.4, 0.5])
@@ -74,6 +80,28 @@ def test_mc_16x16_matches_kaufman(beta):
     e_exact, _ = exact.kaufman_torus(L, beta)
     e_mc, e_err = binned_mean(-E[2000:] / (L * L))
     assert_within(e_mc, e_err, e_exact, what="e")
+
+
+def test_mc_magnetisation_and_energy_match_yang_and_onsager():
+    """Ordered phase of the square lattice, beta = 0.5 > beta_c (Sec. 3.4),
+    L = 64 torus from the all-up start: the signed magnetisation per spin
+    <M>/N equals Yang's spontaneous magnetisation and <E>/N Onsager's
+    infinite-lattice energy.  The true correlation length at this beta,
+    1 / (2 (K - K*)) with tanh K* = exp(-2K), is 4.4 sites, so finite-size
+    corrections ~ exp(-L / xi) ~ 5e-7 are far below the statistical error;
+    the interface free energy 2 sigma L ~ 29 rules out a reversal of M."""
+    dim, L, beta, n = 2, 64, 0.5, 24000
+    N = L * L
+    lid = oracle.lattice_id(0, 2, 0)
+    s = oracle.ising_init(dim, L, 31, lid, hot=False)
+    assert oracle.ising_magnetisation(dim, L, s) == N
+    E, M, _ = oracle.ising_run(dim, L, s, beta, 31, lid, 0, n)
+    m_series = M[2000:] / N
+    assert (n - 2000) / 50 > 20 * tau_int(m_series)
+    m_mc, m_err = binned_mean(m_series)
+    assert_within(m_mc, m_err, exact.yang_magnetisation(beta), what="<M>/N")
+    e_mc, e_err = binned_mean(E[2000:] / N)
+    assert_within(e_mc, e_err, exact.onsager_energy(beta), what="<E>/N")
 
 
 def test_mc_3d_L2_matches_enumeration():

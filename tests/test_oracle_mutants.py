@@ -44,9 +44,19 @@ MUTANTS = {
     "dcb3_missing_threshold": ("const int64_t n = or_nsites(dim, L);\n  uint32_t thr[4] = {0, 0, 0, 0};\n  for (int m = 1; m <= dim; ++m)",
                                "const int64_t n = or_nsites(dim, L);\n  uint32_t thr[4] = {0, 0, 0, 0};\n  for (int m = 1; m < dim; ++m)",
                                "tests/test_oracle_dcb.py::test_3d_one_compound_matches_exact_distribution"),
+    "overlap_one_replica_twice": ("q += s0[i] * s1[i];", "q += s0[i] * s0[i];",
+                                  "tests/test_oracle_pt_heis.py::test_overlap_second_moment_matches_enumeration"),
+    "overlap_sum_not_product": ("q += s0[i] * s1[i];", "q += s0[i] + s1[i];",
+                                "tests/test_oracle_pt_heis.py::test_overlap_second_moment_matches_enumeration"),
+    "magnetisation_sign": ("for (int64_t i = 0; i < n; ++i) m += s[i];",
+                           "for (int64_t i = 0; i < n; ++i) m -= s[i];",
+                           "tests/test_oracle_ising.py::test_mc_magnetisation_and_energy_match_yang_and_onsager"),
     "dcb_hit_words": ("const uint32_t sweep = M * (uint32_t)k + (uint32_t)h;",
                       "const uint32_t sweep = M * (uint32_t)k;",
                       "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
+    "heis_magnetisation_drops_z": ("for (int k = 0; k < 3; ++k) m[k] += s[3 * i + k];",
+                                   "for (int k = 0; k < 2; ++k) m[k] += s[3 * i + k];",
+                                   "tests/test_oracle_pt_heis.py::test_heis_magnetisation_second_moment"),
 }
 
 

@@ -62,17 +62,68 @@ def test_pt_step_rules():
     assert acc[0] == 0 and list(E4) == E[::-1]
 
 
-def test_pt_overlap_series():
+def test_overlap_definition_cases():
+    """q = sum_i s_i^(0) s_i^(1): a configuration with itself gives N, with
+    its reversal -N, and q is unchanged when both replicas take the same
+    gauge transformation s_i -> eps_i s_i (Eq. spinglass_hamiltonian: the
+    transformation that maps one coupling realisation onto another)."""
+    dim, L = 3, 6
+    N = L ** dim
+    s0 = oracle.ising_init(dim, L, 5, oracle.lattice_id(0, 0, 0))
+    s1 = oracle.ising_init(dim, L, 5, oracle.lattice_id(1, 0, 0))
+    assert oracle.overlap(dim, L, s0, s0) == N
+    assert oracle.overlap(dim, L, s0, (-s0).astype(np.int8)) == -N
+    eps = oracle.ising_init(dim, L, 6, oracle.lattice_id(0, 7, 0))
+    q = oracle.overlap(dim, L, s0, s1)
+    assert oracle.overlap(dim, L, (eps * s0).astype(np.int8), (eps * s1).astype(np.int8)) == q
+    # sites where the replicas agree minus sites where they differ
+    assert q == N - 2 * int(np.count_nonzero(s0 != s1))
+
+
+def test_overlap_of_independent_replicas_at_infinite_temperature():
+    """beta = 0: independent hot starts give <q> = 0 and <q^2> = N (q is a
+    sum of N independent +-1 products), and since every site then flips in
+    every sweep, the overlap series of a two-set run is constant in time."""
     dim, L = 3, 4
     N = L ** dim
-    betas = [0.9, 1.0]
-    J = oracle.ea_couplings(dim, L, 0, seed=4)
-    spins = np.stack([np.stack([oracle.ising_init(dim, L, 4, oracle.lattice_id(a, 0, t))
-                                for t in range(2)]) for a in range(2)]).copy()
-    E, Q, acc, _ = oracle.pt_run(dim, L, spins, betas, 4, 0, 0, 0, 5, 1, J=J)
-    for t in range(2):
-        assert Q[-1, t] == oracle.overlap(dim, L, spins[0, t], spins[1, t]) or acc.sum() > 0
-        assert abs(Q[-1, t]) <= N
+    qs = np.array([oracle.overlap(dim, L, oracle.ising_init(dim, L, 9, oracle.lattice_id(0, k, 0)),
+                                  oracle.ising_init(dim, L, 9, oracle.lattice_id(1, k, 0)))
+                   for k in range(4000)], np.float64)
+    assert abs(qs.mean()) < 4 * np.sqrt(N / qs.size)
+    # Var(q^2) = 2 N^2 - 2 N for a sum of N independent signs
+    assert abs((qs ** 2).mean() - N) < 4 * np.sqrt((2 * N * N - 2 * N) / qs.size)
+    J = oracle.ea_couplings(dim, L, 3, seed=9)
+    spins = np.stack([oracle.ising_init(dim, L, 9, oracle.lattice_id(a, 0, 0), bit=3)[None]
+                      for a in range(2)]).copy()
+    q0 = oracle.overlap(dim, L, spins[0, 0], spins[1, 0])
+    _, Q, _, _ = oracle.pt_run(dim, L, spins, [0.0], 9, 3, 0, 0, 6, 0, J=J)
+    assert np.all(Q[:, 0] == q0)
+
+
+def test_overlap_second_moment_matches_enumeration():
+    """Two independent replicas of one 4x4 +-J realisation (Sec. 6): the
+    overlap series of the oracle's two-set run has <q> = 0 (each replica is
+    spin-flip symmetric) and <q^2> = sum_ij <s_i s_j>^2, the correlation
+    matrix taken over all 2^16 states."""
+    dim, L, beta = 2, 4, 0.6
+    N = L * L
+    J = oracle.ea_couplings(dim, L, 1, seed=12)
+    E_all, _ = exact.state_energies(dim, L, J)
+    S = exact.all_states(N).astype(np.float64)
+    w = np.exp(-beta * (E_all - E_all.min()))
+    p = w / w.sum()
+    C = S.T @ (S * p[:, None])
+    q2_exact = float((C ** 2).sum())
+    spins = np.stack([oracle.ising_init(dim, L, 12, oracle.lattice_id(a, 0, 0), bit=1)[None]
+                      for a in range(2)]).copy()
+    n = 150000
+    _, Q, _, _ = oracle.pt_run(dim, L, spins, [beta], 12, 1, 0, 0, n, 0, J=J)
+    q = Q[1000:, 0].astype(np.float64)
+    m, err = binned_mean(q)
+    assert_within(m, err, 0.0, what="<q>")
+    m2, err2 = binned_mean(q ** 2)
+    assert_within(m2, err2, q2_exact, what="<q^2>")
+    assert N < q2_exact < N * N
 
 
 # --------------------------------------------------------------- Heisenberg
@@ -122,6 +173,29 @@ def test_heis_renormalisation_and_energy_definition():
     up[:, 2] = 1.0
     assert oracle.heis_energy(dim, L, up) == -3 * L ** dim
     assert np.allclose(oracle.heis_magnetisation(dim, L, up), [0, 0, L ** dim])
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.05])
+def test_heis_magnetisation_second_moment(beta):
+    """<|M|^2> / N = sum_j <s_0 . s_j>: at beta = 0 every proposal is
+    accepted, so each sweep leaves N fresh independent unit vectors and the
+    value is exactly 1 (1/3 per component); at small beta the
+    high-temperature series of the classical Heisenberg model on the simple
+    cubic lattice (6 neighbours; no closed loop below four bonds) gives
+    1 + 6u + 30u^2 + 150u^3 + O(u^4), u = coth(beta) - 1/beta."""
+    dim, L, n = 3, 8, 20000
+    N = L ** dim
+    s = oracle.heis_init(dim, L, 21, 0)
+    _, M = oracle.heis_run(dim, L, s, beta, 21, 0, 0, n)
+    u = exact.langevin(beta)
+    chi = 1 + 6 * u + 30 * u * u + 150 * u ** 3
+    m2, err = binned_mean((M[100:] ** 2).sum(axis=1) / N)
+    assert_within(m2, err, chi, floor=1e-4, what="<|M|^2>/N")
+    for k in range(3):
+        mk, ek = binned_mean(M[100:, k] ** 2 / N)
+        assert_within(mk, ek, chi / 3, floor=1e-4, what=f"<M_{k}^2>/N")
+        m1, e1 = binned_mean(M[100:, k] / N)
+        assert_within(m1, e1, 0.0, what=f"<M_{k}>/N")
 
 
 def test_heis_margins_identify_decisions():

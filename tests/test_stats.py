@@ -4,7 +4,7 @@ processes x_t = a x_{t-1} + e_t, whose integrated autocorrelation time is
 import numpy as np
 import pytest
 
-from tests.stats import binned_mean, tau_int
+from tests.stats import binned_mean, binned_variance, tau_int
 
 
 def _ar1(a, n, seed):
@@ -33,3 +33,19 @@ def test_binned_error_matches_tau_int():
     tau = (1 + a) / (2 * (1 - a))
     expect = np.sqrt(2 * tau * x.var() / n)
     assert 0.75 * expect < err < 1.3 * expect, (err, expect)
+
+
+def test_binned_variance_of_ar1():
+    """Stationary AR(1) with unit innovations has variance 1 / (1 - a^2); the
+    jackknife error of the binned estimate covers the deviation, and over
+    independent series its spread matches the quoted error."""
+    a = 0.5
+    exact = 1.0 / (1.0 - a * a)
+    vals, errs = [], []
+    for s in range(6):
+        v, e = binned_variance(_ar1(a, 200_000, 100 + s))
+        vals.append(v)
+        errs.append(e)
+        assert abs(v - exact) < 4 * e, (v, e, exact)
+    spread = np.std(vals, ddof=1)
+    assert 0.4 * np.mean(errs) < spread < 2.5 * np.mean(errs), (spread, errs)

@@ -47,7 +47,7 @@ def lib():
         L.or_ising_magnetisation.restype = i64
         L.or_overlap.argtypes = [i32, i32, p, p]
         L.or_overlap.restype = i64
-        L.or_pt_step.argtypes = [i32, i32, i32, p, p, p, u64, u32, u32, u32, p]
+        L.or_pt_step.argtypes = [i32, i32, i32, p, p, p, u64, u32, u32, u32, p, p]
         L.or_heis_init.argtypes = [i32, i32, p, u64, u32]
         L.or_heis_sweep.argtypes = [i32, i32, p, dbl, u64, u32, u32, p]
         L.or_heis_renormalise.argtypes = [i32, i32, p]
@@ -57,7 +57,7 @@ def lib():
         L.or_ising_run.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, i64, p, p, p]
         L.or_heis_run.argtypes = [i32, i32, p, dbl, u64, u32, u32, i64, i32, p, p]
         L.or_pt_run.argtypes = [i32, i32, i32, i32, p, p, p, u64, u32, u32, u32, i64, i32,
-                                p, p, p, p]
+                                p, p, p, p, p]
         L.or_ising_window_sweeps.argtypes = [i32, i32, p, i32, p, dbl, u64, u32, u32, i32]
         L.or_ising_init_sites.argtypes = [i64, p, p, u64, u32, i32]
         L.or_dcb_sweeps.argtypes = [i32, p, p, dbl, u64, u32, u32, i64, i32, i32, i32, p]
@@ -143,31 +143,39 @@ def ising_run(dim, L, s, beta, seed, lid, first_sweep, n_sweeps, J=None, series=
     return E, M, int(flips[0])
 
 
-def pt_step(dim, L, slots, E, betas, seed, set_a, r, step):
-    """One exchange step on a list of per-slot int8 arrays (modified in place)."""
+def pt_step(dim, L, slots, E, betas, seed, set_a, r, step, labels=None):
+    """One exchange step on a list of per-slot int8 arrays (modified in place);
+    labels (int32 [n_temps], optional) are exchanged with the configurations."""
     n_temps = len(slots)
     arr = (C.c_void_p * n_temps)(*[s.ctypes.data for s in slots])
     Ea = np.ascontiguousarray(E, dtype=np.int64)
     b = np.ascontiguousarray(betas, dtype=np.float64)
     acc = np.zeros(n_temps, np.int64)
+    if labels is not None:
+        assert labels.dtype == np.int32 and labels.flags.c_contiguous and labels.size == n_temps
     lib().or_pt_step(dim, L, n_temps, C.cast(arr, C.c_void_p), _ptr(Ea), _ptr(b), seed,
-                     set_a, r, step, _ptr(acc))
+                     set_a, r, step, _ptr(acc), _ptr(labels))
     return Ea, acc
 
 
 def pt_run(dim, L, spins, betas, seed, r, rkey, first_sweep, n_sweeps, pt_every,
-           pt_step0=0, J=None):
+           pt_step0=0, J=None, labels=None):
     """Parallel-tempering run of one realisation; spins [n_sets, n_temps, N]
-    int8 (modified in place).  Returns (E_series, Q_series, accepted, pt_step)."""
+    int8 (modified in place); labels (int32 [n_sets, n_temps], optional,
+    modified in place) follow the configurations through the exchanges.
+    Returns (E_series, Q_series, accepted, pt_step)."""
     n_sets, n_temps, _ = spins.shape
     assert spins.flags.c_contiguous and spins.dtype == np.int8
+    if labels is not None:
+        assert labels.dtype == np.int32 and labels.flags.c_contiguous and labels.shape == (n_sets, n_temps)
     b = np.ascontiguousarray(betas, dtype=np.float64)
     E = np.zeros((n_sweeps, n_sets, n_temps), np.int64)
     Q = np.zeros((n_sweeps, n_temps), np.int64)
     acc = np.zeros((n_sets, n_temps), np.int64)
     step = np.array([pt_step0], np.uint32)
     lib().or_pt_run(dim, L, n_temps, n_sets, _ptr(spins), _ptr(J), _ptr(b), seed, r, rkey,
-                    first_sweep, n_sweeps, pt_every, _ptr(step), _ptr(E), _ptr(Q), _ptr(acc))
+                    first_sweep, n_sweeps, pt_every, _ptr(step), _ptr(E), _ptr(Q), _ptr(acc),
+                    _ptr(labels))
     return E, Q, acc, int(step[0])
 
 

@@ -378,10 +378,14 @@ int64_t or_overlap(int dim, int L, const int8_t *s0, const int8_t *s1) {
  * accepted iff Delta >= 0 or r < thr, thr the threshold of exp(Delta).
  * The pairs of one step are disjoint, so their order does not matter.
  * On acceptance the two configurations and their energies are exchanged.
- * accepted[t] (optional) counts accepted exchanges of pair (t, t+1). */
+ * accepted[t] (optional) counts accepted exchanges of pair (t, t+1).
+ * labels[t] (optional) names the configuration held at slot t; an accepted
+ * exchange moves the two labels with their configurations (Sec. 7 on
+ * exchanging configurations rather than temperatures: the labels let a
+ * caller follow each configuration through the temperature slots). */
 void or_pt_step(int dim, int L, int n_temps, int8_t **slots, int64_t *E,
                 const double *betas, uint64_t seed, uint32_t set_a, uint32_t r,
-                uint32_t pt_step, int64_t *accepted) {
+                uint32_t pt_step, int64_t *accepted, int32_t *labels) {
   int64_t n = or_nsites(dim, L);
   for (int t = (int)(pt_step & 1u); t + 1 < n_temps; t += 2) {
     double dbeta = betas[t + 1] - betas[t];
@@ -404,6 +408,11 @@ void or_pt_step(int dim, int L, int n_temps, int8_t **slots, int64_t *E,
       int64_t te = E[t];
       E[t] = E[t + 1];
       E[t + 1] = te;
+      if (labels) {
+        int32_t tl = labels[t];
+        labels[t] = labels[t + 1];
+        labels[t + 1] = tl;
+      }
       if (accepted) accepted[t] += 1;
     }
   }
@@ -585,12 +594,14 @@ void or_heis_run(int dim, int L, double *s, double beta, uint64_t seed,
  * advances.  rkey = r >> 5 for EA (group-shared update uniforms), r for
  * the ferromagnet.  E_series [n_sweeps][n_sets][n_temps] and Q_series
  * [n_sweeps][n_temps] hold the measurements taken before that sweep's
- * exchange step; accepted [n_sets][n_temps] counts accepted exchanges. */
+ * exchange step; accepted [n_sets][n_temps] counts accepted exchanges and
+ * labels [n_sets][n_temps] (optional) follow the configurations as in
+ * or_pt_step. */
 void or_pt_run(int dim, int L, int n_temps, int n_sets, int8_t *spins, const int8_t *J,
                const double *betas, uint64_t seed, uint32_t r, uint32_t rkey,
                uint32_t first_sweep, int64_t n_sweeps, int pt_every,
                uint32_t *pt_step, int64_t *E_series, int64_t *Q_series,
-               int64_t *accepted) {
+               int64_t *accepted, int32_t *labels) {
   int64_t n = or_nsites(dim, L);
   int8_t **slots = (int8_t **)malloc(sizeof(int8_t *) * (size_t)n_temps);
   int64_t *E = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_temps * (size_t)n_sets);
@@ -613,7 +624,8 @@ void or_pt_run(int dim, int L, int n_temps, int n_sets, int8_t *spins, const int
       for (int a = 0; a < n_sets; ++a) {
         for (int t = 0; t < n_temps; ++t) slots[t] = spins + ((int64_t)a * n_temps + t) * n;
         or_pt_step(dim, L, n_temps, slots, &E[a * n_temps], betas, seed, (uint32_t)a, r,
-                   *pt_step, accepted ? &accepted[a * n_temps] : NULL);
+                   *pt_step, accepted ? &accepted[a * n_temps] : NULL,
+                   labels ? &labels[a * n_temps] : NULL);
       }
       *pt_step += 1u;
     }

@@ -54,6 +54,8 @@ MUTANTS = {
     "dcb_hit_words": ("const uint32_t sweep = M * (uint32_t)k + (uint32_t)h;",
                       "const uint32_t sweep = M * (uint32_t)k;",
                       "tests/test_oracle_dcb.py::test_one_compound_matches_exact_distribution"),
+    "pt_labels_half_exchanged": ("labels[t + 1] = tl;", "labels[t + 1] = labels[t];",
+                                 "tests/test_oracle_pt_heis.py::test_pt_labels_follow_the_configurations"),
     "heis_magnetisation_drops_z": ("for (int k = 0; k < 3; ++k) m[k] += s[3 * i + k];",
                                    "for (int k = 0; k < 2; ++k) m[k] += s[3 * i + k];",
                                    "tests/test_oracle_pt_heis.py::test_heis_magnetisation_second_moment"),

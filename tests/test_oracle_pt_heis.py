@@ -62,6 +62,46 @@ def test_pt_step_rules():
     assert acc[0] == 0 and list(E4) == E[::-1]
 
 
+@pytest.mark.parametrize("T", [5, 6])
+def test_pt_labels_reverse_after_T_steps_when_every_exchange_is_accepted(T):
+    """Equal betas make Delta = 0, so every tried pair is exchanged: the step
+    schedule (pairs t = p mod 2) is then the odd-even transposition network,
+    which reverses the order of T items in T steps (it sorts a reversed list
+    in T rounds, swapping at every comparator) and restores it after 2T."""
+    dim, L = 2, 4
+    slots = [oracle.ising_init(dim, L, 3, oracle.lattice_id(0, 0, t)) for t in range(T)]
+    E = [oracle.ising_energy(dim, L, s) for s in slots]
+    labels = np.arange(T, dtype=np.int32)
+    for step in range(2 * T):
+        E, _ = oracle.pt_step(dim, L, slots, E, [0.7] * T, 3, 0, 0, step, labels=labels)
+        if step == T - 1:
+            assert list(labels) == list(range(T - 1, -1, -1))
+    assert list(labels) == list(range(T))
+
+
+def test_pt_labels_follow_the_configurations():
+    """Distinct configurations at geometric betas, exchange steps without
+    sweeps: after every step each slot holds the configuration its label
+    names (with that configuration's energy), and the labels stay a
+    permutation."""
+    dim, L, T = 2, 4, 7
+    init = [oracle.ising_init(dim, L, 8, oracle.lattice_id(0, 0, t)) for t in range(T)]
+    E0 = [oracle.ising_energy(dim, L, s) for s in init]
+    slots = [s.copy() for s in init]
+    betas = 0.2 * 1.35 ** np.arange(T)
+    E = list(E0)
+    labels = np.arange(T, dtype=np.int32)
+    moved = 0
+    for step in range(400):
+        E, acc = oracle.pt_step(dim, L, slots, E, betas, 8, 0, 0, step, labels=labels)
+        moved += int(acc.sum())
+        assert sorted(labels) == list(range(T))
+        for t in range(T):
+            assert np.array_equal(slots[t], init[labels[t]])
+            assert E[t] == E0[labels[t]]
+    assert moved > 50
+
+
 def test_overlap_definition_cases():
     """q = sum_i s_i^(0) s_i^(1): a configuration with itself gives N, with
     its reversal -N, and q is unchanged when both replicas take the same

@@ -133,10 +133,19 @@ int spin_measure(spin_lattice *lat, const void *couplings, int64_t *E, int64_t *
  * the PT word r < floor(exp(Delta) 2^32).  Accepted pairs exchange their
  * configurations (bitwise for MSC1).  Energies are computed on the device
  * from the current state.  accepted (device int64 [n_sets][n_temps], may be
- * NULL) is incremented per accepted pair (t, t+1) at index t.  The exchange
- * counter then advances by one. */
+ * NULL) is incremented per accepted pair (t, t+1) at index t.  labels
+ * (device int32 [n_sets][n_temps][n_real], indexed like the lattices, may be
+ * NULL) names the configuration each lattice holds: an accepted exchange
+ * moves the two labels with their configurations.  Sec. 7 notes that
+ * exchanging temperatures instead of configurations is cheaper on a CPU;
+ * the labels give a caller of this configuration-exchange form the same
+ * information -- starting from labels[lat(a, t, r)] = t, the slot of every
+ * configuration (slot_of_config, for round-trip counts) is the inverse
+ * permutation of labels over t for each (a, r).  The values are the
+ * caller's; the library only moves them.  The exchange counter then
+ * advances by one. */
 int spin_pt_swap(spin_lattice *lat, const void *couplings, const double *betas,
-                 uint64_t seed, int64_t *accepted);
+                 uint64_t seed, int64_t *accepted, int32_t *labels);
 
 /* A whole simulation on one handle: n_sweeps sweeps; after every sweep that
  * brings the handle's sweep count (spin_sweeps_done) to a multiple of
@@ -145,13 +154,15 @@ int spin_pt_swap(spin_lattice *lat, const void *couplings, const double *betas,
  * k, so a call writes (s + n_sweeps) / measure_every - s / measure_every
  * rows for a count s before it); after every sweep that brings the count to
  * a multiple of pt_every (> 0) one exchange step as in spin_pt_swap follows
- * the measurement. */
+ * the measurement; accepted and labels as in spin_pt_swap. */
 int spin_run(spin_lattice *lat, const void *couplings, const double *betas, int64_t n_sweeps,
              int32_t measure_every, int32_t pt_every, int64_t *E_series, int64_t *M_series,
-             int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted);
+             int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted,
+             int32_t *labels);
 
 /* One handle of a batched launch: its couplings and HOST betas as in
- * spin_sweep, and optional device series/counters as in spin_run. */
+ * spin_sweep, and optional device series, counters and configuration
+ * labels as in spin_run. */
 typedef struct {
   spin_lattice *lat;
   const void *couplings;
@@ -160,6 +171,7 @@ typedef struct {
   int64_t *M_series;
   int64_t *Q_series;
   int64_t *accepted;
+  int32_t *labels;
 } spin_batch_item;
 
 /* Batched persistent launch (the paper maps independent replicas and
@@ -263,26 +275,29 @@ typedef enum {
 int spin_pipe_probe(int op, int32_t blocks_per_sm, uint32_t iters, int64_t *clocks, uint32_t *sink,
                     int32_t *sms, void *stream);
 
-/* Heisenberg energy and magnetisation (as Ef and Mf of spin_measure) for
- * callers that cannot allocate device memory.  The paper has no counterpart;
- * this entry point exists for library users: code inside a framework that
- * owns the whole device-memory pool (a raw cudaMalloc there fails or
- * fragments the pool) and code that must not stall the device (cudaFree, and
- * often cudaMalloc, synchronise it).  It needs no handle: spins is a device
- * float4 array [n_lat][L^3] (16-byte aligned), Ef [n_lat] and Mf [n_lat][3]
- * are caller-owned device outputs (NULL to skip); work runs on `stream`.
- * Partial sums live in one fixed array compiled into the library:
+/* Heisenberg energy and magnetisation (as Ef and Mf of spin_measure, with
+ * the same arithmetic and summation order, so the results are bit-identical)
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this entry point exists for library users: code inside a
+ * framework that owns the whole device-memory pool (a raw cudaMalloc there
+ * fails or fragments the pool) and code that must not stall the device
+ * (cudaFree, and often cudaMalloc, synchronise it).  It needs no handle:
+ * spins is a device float4 array [n_lat][L^dim] (16-byte aligned) on the
+ * square (dim = 2) or simple cubic (dim = 3) lattice, Ef [n_lat] and
+ * Mf [n_lat][3] are caller-owned device outputs (NULL to skip); work runs on
+ * `stream`.  Partial sums live in one fixed array compiled into the library:
  * 256 lattices x 64 blocks x 4 doubles = 512 KiB on every GPU that loads the
- * library, held until process exit.  n_lat > 256 (or n_lat L^3 >= 2^31) is
- * rejected with SPIN_EINVAL; nothing is allocated, neither by this call nor
- * by any library routine it uses.  The first call on a device looks up the
- * array's device address (one-time set-up per device); make that first call
- * before any stream capture.  Every call overwrites the partial sums before
- * reading them, so no state has to be cleared between calls, but all calls
- * share the one array: calls whose work overlaps on the GPU (different
- * streams without ordering) race and give wrong sums. */
-int spin_heis_measure_noalloc(const float *spins, int32_t L, int32_t n_lat, double *Ef, double *Mf,
-                              void *stream);
+ * library, held until process exit.  SPIN_EINVAL for dim other than 2 or 3,
+ * odd L or L < 4, n_lat > 256, L^dim >= 2^31 or n_lat L^dim >= 2^31;
+ * nothing is allocated, neither by this call nor by any library routine it
+ * uses.  The first call on a device looks up the array's device address
+ * (one-time set-up per device); make that first call before any stream
+ * capture.  Every call overwrites the partial sums before reading them, so
+ * no state has to be cleared between calls, but all calls share the one
+ * array: calls whose work overlaps on the GPU (different streams without
+ * ordering) race and give wrong sums. */
+int spin_heis_measure_noalloc(const float *spins, int32_t dim, int32_t L, int32_t n_lat, double *Ef,
+                              double *Mf, void *stream);
 
 /* Waits for the handle's stream and reports asynchronous failures
  * (SPIN_ECUDA, SPIN_ETIMEOUT).  Clears the device error word. */

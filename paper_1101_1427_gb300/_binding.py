@@ -29,7 +29,7 @@ class spin_desc(C.Structure):
 class spin_batch_item(C.Structure):
     _fields_ = [("lat", C.c_void_p), ("couplings", C.c_void_p), ("betas", C.c_void_p),
                 ("E_series", C.c_void_p), ("M_series", C.c_void_p), ("Q_series", C.c_void_p),
-                ("accepted", C.c_void_p)]
+                ("accepted", C.c_void_p), ("labels", C.c_void_p)]
 
 
 class SpinError(RuntimeError):
@@ -52,8 +52,8 @@ def lib():
         L.spin_init.argtypes = [C.POINTER(p), C.POINTER(spin_desc), p, p]
         L.spin_sweep.argtypes = [p, p, p, i64, u64]
         L.spin_measure.argtypes = [p, p, p, p, p, p, p]
-        L.spin_pt_swap.argtypes = [p, p, p, u64, p]
-        L.spin_run.argtypes = [p, p, p, i64, i32, i32, p, p, p, p, p, p]
+        L.spin_pt_swap.argtypes = [p, p, p, u64, p, p]
+        L.spin_run.argtypes = [p, p, p, i64, i32, i32, p, p, p, p, p, p, p]
         L.spin_unpack_i8.argtypes = [p, p]
         L.spin_pack_i8.argtypes = [p, p]
         L.spin_rng_fill.argtypes = [u64, u32, u32, u32, u32, u32, u64, p, p]
@@ -61,7 +61,7 @@ def lib():
         L.spin_pipe_probe.argtypes = [C.c_int, i32, u32, p, p, p, p]
         L.spin_describe.argtypes = [p, C.POINTER(spin_desc)]
         L.spin_sync.argtypes = [p]
-        L.spin_heis_measure_noalloc.argtypes = [p, i32, i32, p, p, p]
+        L.spin_heis_measure_noalloc.argtypes = [p, i32, i32, i32, p, p, p]
         L.spin_batch_run.argtypes = [p, C.c_int, i64, i32, i32, p]
         L.spin_batch_tune.argtypes = [p, C.c_int, i64, i32, i32, p, p]
         L.spin_set_batch_options.argtypes = [p, u64, i32, i32]
@@ -172,8 +172,9 @@ def _n_meas(h, n_sweeps, measure_every):
     return (cur + n_sweeps) // measure_every - cur // measure_every
 
 
-def _need_series(h, d, n_lat, rows, E, M, Q, Ef, Mf, accepted, what):
+def _need_series(h, d, n_lat, rows, E, M, Q, Ef, Mf, accepted, what, labels=None):
     import torch
+    _need(labels, n_lat, torch.int32, what, "labels")
     _need(E, rows * n_lat, torch.int64, what, "E")
     _need(M, rows * n_lat, torch.int64, what, "M")
     _need(Q, rows * d.n_temps * d.n_real, torch.int64, what, "Q")
@@ -205,25 +206,25 @@ def spin_measure(h, couplings=None, E=None, M=None, Q=None, Ef=None, Mf=None):
                                      _ptr(Mf)), "spin_measure")
 
 
-def spin_pt_swap(h, couplings, betas, seed, accepted=None):
+def spin_pt_swap(h, couplings, betas, seed, accepted=None, labels=None):
     d, N, n_lat = _shape(h)
     _need_betas(d, betas, "spin_pt_swap")
     _need_couplings(d, N, couplings, "spin_pt_swap")
-    _need_series(h, d, n_lat, 0, None, None, None, None, None, accepted, "spin_pt_swap")
+    _need_series(h, d, n_lat, 0, None, None, None, None, None, accepted, "spin_pt_swap", labels)
     return _check(lib().spin_pt_swap(h, _ptr(couplings), _host_doubles(betas), seed,
-                                     _ptr(accepted)), "spin_pt_swap")
+                                     _ptr(accepted), _ptr(labels)), "spin_pt_swap")
 
 
 def spin_run(h, couplings, betas, n_sweeps, measure_every=0, pt_every=0, E=None, M=None,
-             Q=None, Ef=None, Mf=None, accepted=None):
+             Q=None, Ef=None, Mf=None, accepted=None, labels=None):
     d, N, n_lat = _shape(h)
     _need_betas(d, betas, "spin_run")
     _need_couplings(d, N, couplings, "spin_run")
     rows = _n_meas(h, n_sweeps, measure_every) if n_sweeps > 0 else 0
-    _need_series(h, d, n_lat, rows, E, M, Q, Ef, Mf, accepted, "spin_run")
+    _need_series(h, d, n_lat, rows, E, M, Q, Ef, Mf, accepted, "spin_run", labels)
     return _check(lib().spin_run(h, _ptr(couplings), _host_doubles(betas), n_sweeps,
                                  measure_every, pt_every, _ptr(E), _ptr(M), _ptr(Q), _ptr(Ef),
-                                 _ptr(Mf), _ptr(accepted)), "spin_run")
+                                 _ptr(Mf), _ptr(accepted), _ptr(labels)), "spin_run")
 
 
 def spin_unpack_i8(h, out):
@@ -259,7 +260,7 @@ def spin_pipe_probe(op, blocks_per_sm, iters, cycles, sink, stream=None):
 
 def _batch_items(items, n_sweeps=0, measure_every=0):
     """items: list of dicts with keys lat (handle), couplings, betas and the
-    optional device tensors E, M, Q, accepted (checked against each handle's
+    optional device tensors E, M, Q, accepted, labels (checked against each handle's
     descriptor).  Returns the ctypes array and the host beta arrays that must
     stay alive during the call."""
     arr = (spin_batch_item * len(items))()
@@ -271,12 +272,12 @@ def _batch_items(items, n_sweeps=0, measure_every=0):
         _need_couplings(d, N, it.get("couplings"), "spin_batch_run")
         rows = _n_meas(lat, n_sweeps, measure_every) if n_sweeps > 0 else 0
         _need_series(lat, d, n_lat, rows, it.get("E"), it.get("M"), it.get("Q"), None, None,
-                     it.get("accepted"), "spin_batch_run")
+                     it.get("accepted"), "spin_batch_run", it.get("labels"))
         b = _host_doubles(it["betas"])
         keep.append(b)
         dp = lambda key: it[key].data_ptr() if it.get(key) is not None else None
         arr[k] = spin_batch_item(lat, dp("couplings"), C.cast(b, C.c_void_p), dp("E"), dp("M"),
-                                 dp("Q"), dp("accepted"))
+                                 dp("Q"), dp("accepted"), dp("labels"))
     return arr, keep
 
 
@@ -299,14 +300,14 @@ def spin_set_batch_options(h, timeout_ns=0, ctas_per_sm=0, missing_arrivals=0):
                   "spin_set_batch_options")
 
 
-def spin_heis_measure_noalloc(spins, L, n_lat, Ef=None, Mf=None, stream=None):
+def spin_heis_measure_noalloc(spins, dim, L, n_lat, Ef=None, Mf=None, stream=None):
     """Heisenberg E and M into caller-owned tensors without any device
     allocation (the partial sums use a fixed array inside the library)."""
     import torch
-    _need(spins, 4 * n_lat * L ** 3, torch.float32, "spin_heis_measure_noalloc", "spins")
+    _need(spins, 4 * n_lat * L ** dim, torch.float32, "spin_heis_measure_noalloc", "spins")
     _need(Ef, n_lat, torch.float64, "spin_heis_measure_noalloc", "Ef")
     _need(Mf, 3 * n_lat, torch.float64, "spin_heis_measure_noalloc", "Mf")
-    return _check(lib().spin_heis_measure_noalloc(_ptr(spins), L, n_lat, _ptr(Ef), _ptr(Mf), stream),
+    return _check(lib().spin_heis_measure_noalloc(_ptr(spins), dim, L, n_lat, _ptr(Ef), _ptr(Mf), stream),
                   "spin_heis_measure_noalloc")
 
 

@@ -275,13 +275,13 @@ namespace {
 // One exchange step; `energies` (device, [n_lat]) are the lattices' current
 // energies when the caller has just measured them, else NULL.
 int pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_t seed,
-            int64_t *accepted, const int64_t *energies) {
+            int64_t *accepted, int32_t *labels, const int64_t *energies) {
   if (!h || seed != h->d.seed || !betas) return SPIN_EINVAL;
   if (h->d.model == SPIN_HEISENBERG) return SPIN_EINVAL;
   if (ea(h) && !couplings) return SPIN_EINVAL;
   int rc = upload_pt_tables(h, betas);
   if (rc) return rc;
-  cudaError_t e = launch_pt_swap(h, ea(h) ? couplings : nullptr, accepted, energies);
+  cudaError_t e = launch_pt_swap(h, ea(h) ? couplings : nullptr, accepted, labels, energies);
   if (e != cudaSuccess) return SPIN_ECUDA;
   h->pt_steps_done += 1;
   return SPIN_OK;
@@ -289,14 +289,15 @@ int pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_
 }  // namespace
 
 int spin_pt_swap(spin_lattice *h, const void *couplings, const double *betas, uint64_t seed,
-                 int64_t *accepted) {
+                 int64_t *accepted, int32_t *labels) {
   NvtxRange nvtx_range("spin_pt_swap");
-  return pt_swap(h, couplings, betas, seed, accepted, nullptr);
+  return pt_swap(h, couplings, betas, seed, accepted, labels, nullptr);
 }
 
 int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_t n_sweeps,
              int32_t measure_every, int32_t pt_every, int64_t *E_series, int64_t *M_series,
-             int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted) {
+             int64_t *Q_series, double *Ef_series, double *Mf_series, int64_t *accepted,
+             int32_t *labels) {
   NvtxRange nvtx_range("spin_run");
   if (!h || n_sweeps < 0) return SPIN_EINVAL;
   if (pt_every > 0 && h->d.model == SPIN_HEISENBERG) return SPIN_EINVAL;
@@ -328,7 +329,7 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
     k_meas += now / measure_every - cur / measure_every;
     if (pt_every > 0 && now % pt_every == 0) {
       const int64_t *energies = E_series && now % measure_every == 0 ? E_series + (k_meas - 1) * nl : nullptr;
-      rc = pt_swap(h, couplings, betas, h->d.seed, accepted, energies);
+      rc = pt_swap(h, couplings, betas, h->d.seed, accepted, labels, energies);
       if (rc) return rc;
     }
   }
@@ -362,7 +363,7 @@ int spin_run(spin_lattice *h, const void *couplings, const double *betas, int64_
       ++k_meas;
     }
     if (pt_every > 0 && now % pt_every == 0) {
-      rc = pt_swap(h, couplings, betas, h->d.seed, accepted, energies);
+      rc = pt_swap(h, couplings, betas, h->d.seed, accepted, labels, energies);
       if (rc) return rc;
     }
   }

@@ -56,6 +56,7 @@ struct BatchUnit {
   const int32_t *pt_off, *pt_len;
   const double *pt_dbeta;
   long long *E_series, *M_series, *Q_series, *accepted;
+  int *labels;          // configuration labels of the handle's lattices (or NULL)
   long long n_lat;      // lattices of the handle (series row length)
   int *Escr;            // [n_sets][n_T][32] unsatisfied-bond counts
   // Ising
@@ -80,6 +81,8 @@ struct BatchParams {
   RoundKeys keys[kMaxHandles];
   BatchUnit units[kMaxUnits];
 };
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(BatchParams) <= 32764, "batch parameters exceed the kernel parameter space");
 
 namespace {
 
@@ -466,6 +469,12 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
       const uint4 v = philox(make_uint4((uint32_t)r >> 2, pt_step, lattice_id((uint32_t)a, 0, (uint32_t)t),
                                         ctr_w(TAG_PT, 0, 0)), rk);
       acc = word_of(v, (uint32_t)r & 3u) < th;
+    }
+    if (U.labels && acc) {  // this lane alone owns realisation r of pair (t, t+1)
+      const long long l0 = ((long long)a * U.n_T + t) * U.n_real + r, l1 = l0 + U.n_real;
+      const int x = U.labels[l0];
+      U.labels[l0] = U.labels[l1];
+      U.labels[l1] = x;
     }
     const uint32_t A = __ballot_sync(0xffffffffu, acc);
     if (lane == 0) {
@@ -885,6 +894,7 @@ static int batch_build(const spin_batch_item *items, int n_items, BatchParams &p
         U.M_series = (long long *)items[k].M_series;
         U.Q_series = (long long *)items[k].Q_series;
         U.accepted = (long long *)items[k].accepted;
+        U.labels = (int *)items[k].labels;
         U.n_lat = h->n_lat;
         U.Escr = h->d_escr + (size_t)grp * g.n_sets * g.n_temps * 32;
       }
@@ -1100,6 +1110,7 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
     sw[k] = h->sweeps_done;
     ps[k] = h->pt_steps_done;
     tmp[k].E_series = tmp[k].M_series = tmp[k].Q_series = tmp[k].accepted = nullptr;
+    tmp[k].labels = nullptr;
   }
   // scratch series, so that the trials measure as the real runs will
   std::vector<void *> scratch;

@@ -83,7 +83,9 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
                            double *Ef, double *Mf);
 // energies: the lattices' current energies if the caller has them (device,
 // [n_lat]), else NULL to compute them
-cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, const int64_t *energies);
+// labels: configuration labels moved with accepted exchanges (device, [n_lat], or NULL)
+cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, int32_t *labels,
+                           const int64_t *energies);
 
 // Launches kernel k as a programmatic dependent of the previous work in
 // stream s (the kernel must call griddep_wait() before touching memory).

@@ -3,6 +3,7 @@
 // and the replica-exchange step (Eq. parallel_tempering, Sec. 7).
 #include "bitslice.cuh"
 #include "ea_cs.cuh"
+#include "heis_reduce.cuh"
 #include "internal.h"
 
 namespace spin {
@@ -444,48 +445,8 @@ __global__ void measure_heis_kernel(const float4 *__restrict__ s, Geom g,
   griddep_wait();
   griddep_release();
   const int64_t lat = blockIdx.y;
-  const float4 *sl = s + lat * g.N;
-  const int L = g.L;
-  const int64_t LL = (int64_t)L * L;
-  double e = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / LL);
-    const float4 a = sl[i];
-    const float4 bx = sl[i - x + (x == L - 1 ? 0 : x + 1)];
-    const float4 by = sl[y == L - 1 ? i - (int64_t)(L - 1) * L : i + L];
-    const double ax = a.x, ay = a.y, az = a.z;
-    if (g.dim == 3) {
-      const float4 bz = sl[z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL];
-      e -= ax * ((double)bx.x + (double)by.x + (double)bz.x) +
-           ay * ((double)bx.y + (double)by.y + (double)bz.y) +
-           az * ((double)bx.z + (double)by.z + (double)bz.z);
-    } else {
-      e -= ax * ((double)bx.x + (double)by.x) + ay * ((double)bx.y + (double)by.y) +
-           az * ((double)bx.z + (double)by.z);
-    }
-    mx += ax;
-    my += ay;
-    mz += az;
-  }
-  __shared__ double red[4][32];
-  e = warp_sum(e);
-  mx = warp_sum(mx);
-  my = warp_sum(my);
-  mz = warp_sum(mz);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[0][wid] = e;
-    red[1][wid] = mx;
-    red[2][wid] = my;
-    red[3][wid] = mz;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double acc = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) acc += red[threadIdx.x][k];
-    partial[(lat * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = acc;
-  }
+  heis_block_partials(s + lat * g.N, g.L, g.dim, g.N, blockIdx.x, gridDim.x,
+                      partial + (lat * gridDim.x + blockIdx.x) * 4);
 }
 
 __global__ void finish_heis_kernel(const double *__restrict__ partial, int64_t n_lat, int nb,
@@ -494,15 +455,7 @@ __global__ void finish_heis_kernel(const double *__restrict__ partial, int64_t n
   griddep_release();
   const int64_t lat = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (lat >= n_lat) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = 0; b < nb; ++b)
-    for (int c = 0; c < 4; ++c) acc[c] += partial[(lat * nb + b) * 4 + c];
-  if (Ef) Ef[lat] = acc[0];
-  if (Mf) {
-    Mf[3 * lat] = acc[1];
-    Mf[3 * lat + 1] = acc[2];
-    Mf[3 * lat + 2] = acc[3];
-  }
+  heis_finish_lattice(partial, nb, lat, Ef, Mf);
 }
 
 // ---------------------------------------------------------------- replica exchange
@@ -513,7 +466,8 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
                                  const double *__restrict__ dbeta,
                                  const uint32_t *__restrict__ tab, const int32_t *__restrict__ off,
                                  const int32_t *__restrict__ len, RoundKeys rk, uint32_t step,
-                                 uint8_t *__restrict__ decision, long long *__restrict__ accepted) {
+                                 uint8_t *__restrict__ decision, long long *__restrict__ accepted,
+                                 int *__restrict__ labels) {
   griddep_wait();
   griddep_release();
   const int parity = (int)(step & 1u);
@@ -539,6 +493,11 @@ __global__ void pt_decide_kernel(const long long *__restrict__ E, Geom g,
     acc = word_of(w, (uint32_t)r & 3u) < thr;
   }
   decision[lat0] = acc ? 1 : 0;
+  if (labels && acc) {  // one thread per pair: no other thread touches these two
+    const int l0 = labels[lat0];
+    labels[lat0] = labels[lat1];
+    labels[lat1] = l0;
+  }
   if (!accepted) return;
   if ((g.n_real & 31) == 0) {
     // the 32 lanes of a warp share (a, t): one atomic per warp
@@ -677,7 +636,8 @@ cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *
                           (g.n_sets >= 2) ? (long long *)Q : nullptr);
 }
 
-cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, const int64_t *energies) {
+cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, int32_t *labels,
+                           const int64_t *energies) {
   const Geom &g = h->g;
   cudaStream_t st = h->stream;
   if (!energies) {
@@ -695,7 +655,7 @@ cudaError_t launch_pt_swap(spin_lattice *h, const void *J, int64_t *accepted, co
                                    (const long long *)energies, g, (const double *)h->d_pt_dbeta,
                                    (const uint32_t *)h->d_pt_thr, (const int32_t *)h->d_pt_off,
                                    (const int32_t *)h->d_pt_len, make_round_keys(h->d.seed), step, decision,
-                                   (long long *)accepted);
+                                   (long long *)accepted, (int *)labels);
   if (e != cudaSuccess) return e;
   if (h->d.layout == SPIN_MSC1 && h->d.model == SPIN_EA) {
     const int64_t n_wl = (int64_t)g.n_sets * (g.n_real / 32) * g.n_temps;

@@ -12,6 +12,7 @@
 // device, held from library load until process exit).
 #include <mutex>
 
+#include "heis_reduce.cuh"
 #include "internal.h"
 
 namespace {
@@ -27,63 +28,20 @@ static __device__ __align__(256) double g_partials[kMaxLattices * kBlocks * 4];
 std::mutex g_setup_mutex;
 double *g_partials_addr[kMaxDevices] = {};  // device address of g_partials, per device
 
-// Same arithmetic and order as the reduction behind spin_measure: FP32
-// products widened to double, per-thread double sums, warp and block sums,
-// then a fixed-order pass over the block partials.
-__global__ void heis_partials_kernel(const float4 *__restrict__ s, int L, double *__restrict__ part) {
+// The arithmetic and order of the reduction behind spin_measure (one shared
+// device function), so both give bit-identical sums.
+__global__ void heis_partials_kernel(const float4 *__restrict__ s, int dim, int L, int64_t N,
+                                     double *__restrict__ part) {
   const int64_t lat = blockIdx.y;
-  const int64_t N = (int64_t)L * L * L;
-  const float4 *sl = s + lat * N;
-  const int64_t LL = (int64_t)L * L;
-  double e = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / LL);
-    const float4 a = sl[i];
-    const float4 bx = sl[i - x + (x == L - 1 ? 0 : x + 1)];
-    const float4 by = sl[y == L - 1 ? i - (int64_t)(L - 1) * L : i + L];
-    const float4 bz = sl[z == L - 1 ? i - (int64_t)(L - 1) * LL : i + LL];
-    const double ax = a.x, ay = a.y, az = a.z;
-    e -= ax * ((double)bx.x + (double)by.x + (double)bz.x) +
-         ay * ((double)bx.y + (double)by.y + (double)bz.y) +
-         az * ((double)bx.z + (double)by.z + (double)bz.z);
-    mx += ax;
-    my += ay;
-    mz += az;
-  }
-  __shared__ double red[4][32];
-  e = spin::warp_sum(e);
-  mx = spin::warp_sum(mx);
-  my = spin::warp_sum(my);
-  mz = spin::warp_sum(mz);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[0][wid] = e;
-    red[1][wid] = mx;
-    red[2][wid] = my;
-    red[3][wid] = mz;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double acc = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) acc += red[threadIdx.x][k];
-    part[(lat * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = acc;
-  }
+  spin::heis_block_partials(s + lat * N, L, dim, N, blockIdx.x, gridDim.x,
+                            part + (lat * gridDim.x + blockIdx.x) * 4);
 }
 
 __global__ void heis_finish_kernel(const double *__restrict__ part, int64_t n_lat, double *__restrict__ Ef,
                                    double *__restrict__ Mf) {
   const int64_t lat = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (lat >= n_lat) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = 0; b < kBlocks; ++b)
-    for (int c = 0; c < 4; ++c) acc[c] += part[(lat * kBlocks + b) * 4 + c];
-  if (Ef) Ef[lat] = acc[0];
-  if (Mf) {
-    Mf[3 * lat] = acc[1];
-    Mf[3 * lat + 1] = acc[2];
-    Mf[3 * lat + 2] = acc[3];
-  }
+  spin::heis_finish_lattice(part, kBlocks, lat, Ef, Mf);
 }
 
 // Device address of the fixed scratch for the current device, looked up
@@ -103,18 +61,21 @@ int partials_for_current_device(double **out) {
 
 }  // namespace
 
-extern "C" int spin_heis_measure_noalloc(const float *spins, int32_t L, int32_t n_lat, double *Ef,
+extern "C" int spin_heis_measure_noalloc(const float *spins, int32_t dim, int32_t L, int32_t n_lat, double *Ef,
                                          double *Mf, void *stream) {
-  if (!spins || L < 4 || (L & 1) || n_lat < 1) return SPIN_EINVAL;
+  if (!spins || (dim != 2 && dim != 3) || L < 4 || (L & 1) || n_lat < 1) return SPIN_EINVAL;
   if (n_lat > kMaxLattices) return SPIN_EINVAL;  // beyond the fixed scratch
-  if ((int64_t)n_lat * L * L * L >= ((int64_t)1 << 31)) return SPIN_EINVAL;
+  // bound L on its own first, so that the products below cannot overflow
+  if (L > (dim == 3 ? 1290 : 46340)) return SPIN_EINVAL;  // L^dim < 2^31
+  const int64_t N = dim == 3 ? (int64_t)L * L * L : (int64_t)L * L;
+  if ((int64_t)n_lat * N >= ((int64_t)1 << 31)) return SPIN_EINVAL;
   if (((uintptr_t)spins & 15u) != 0) return SPIN_EALIGN;
   if (!Ef && !Mf) return SPIN_OK;
   double *part = nullptr;
   const int rc = partials_for_current_device(&part);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  heis_partials_kernel<<<dim3(kBlocks, (unsigned)n_lat), 256, 0, st>>>((const float4 *)spins, L, part);
+  heis_partials_kernel<<<dim3(kBlocks, (unsigned)n_lat), 256, 0, st>>>((const float4 *)spins, dim, L, N, part);
   heis_finish_kernel<<<(n_lat + 127) / 128, 128, 0, st>>>(part, n_lat, Ef, Mf);
   return cudaGetLastError() == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }

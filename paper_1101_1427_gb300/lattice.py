@@ -70,10 +70,18 @@ class Lattice:
         B.spin_measure(self.h, self.couplings, E=E, M=M, Q=Q)
         return E, M, Q
 
-    def pt_swap(self, betas, accepted=None):
-        B.spin_pt_swap(self.h, self.couplings, list(betas), self.seed, accepted)
+    def pt_swap(self, betas, accepted=None, labels=None):
+        B.spin_pt_swap(self.h, self.couplings, list(betas), self.seed, accepted, labels)
 
-    def run(self, betas, n_sweeps, measure_every=0, pt_every=0, series=True, accepted=None):
+    def slot_labels(self):
+        """Configuration labels [n_sets, n_temps, n_real] (int32, device)
+        holding each lattice's slot t: passed to pt_swap / run / batch_item,
+        they follow the configurations through accepted exchanges."""
+        t = torch.arange(self.n_temps, dtype=torch.int32, device=self.device)
+        return t.view(1, -1, 1).expand(self.n_sets, self.n_temps, self.n_real).contiguous()
+
+    def run(self, betas, n_sweeps, measure_every=0, pt_every=0, series=True, accepted=None,
+            labels=None):
         # measurements fall on sweep counts that are multiples of measure_every,
         # counted from the handle's counter (not from the start of the call)
         n_meas = B._n_meas(self.h, n_sweeps, measure_every)
@@ -91,7 +99,7 @@ class Lattice:
                                            device=self.device)
         B.spin_run(self.h, self.couplings, list(betas), n_sweeps, measure_every, pt_every,
                    out.get("E"), out.get("M"), out.get("Q"), out.get("Ef"), out.get("Mf"),
-                   accepted)
+                   accepted, labels)
         return out
 
     def series_buffers(self, n_meas):
@@ -106,12 +114,14 @@ class Lattice:
                                    device=self.device)
         return out
 
-    def batch_item(self, betas, series=None, accepted=None):
+    def batch_item(self, betas, series=None, accepted=None, labels=None):
         it = {"lat": self.h, "couplings": self.couplings, "betas": list(betas)}
         if series:
             it.update(series)
         if accepted is not None:
             it["accepted"] = accepted
+        if labels is not None:
+            it["labels"] = labels
         return it
 
     def unpack(self):

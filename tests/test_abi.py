@@ -47,3 +47,27 @@ def test_measurement_rows_follow_the_handle_counter(monkeypatch):
             for every in range(0, 5):
                 want = sum(1 for s in range(cur + 1, cur + n + 1) if every > 0 and s % every == 0)
                 assert B._n_meas(None, n, every) == want, (cur, n, every)
+
+
+def declared_parameter_counts():
+    """Parameter count of every spin_* function declared in include/spin.h."""
+    text = open(os.path.join(ROOT, "include", "spin.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(spin_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argtypes_match_the_header():
+    """The ctypes signatures of the binding have as many parameters as the
+    header's declarations (a drift between the two would pass arguments in
+    the wrong places)."""
+    from paper_1101_1427_gb300 import _binding as B
+    lib = B.lib()
+    counts = declared_parameter_counts()
+    assert len(counts) == len(declared_symbols())
+    bad = {n: (c, len(getattr(lib, n).argtypes)) for n, c in counts.items()
+           if len(getattr(lib, n).argtypes or []) != c}
+    assert not bad, bad

@@ -49,9 +49,9 @@ def test_batch_equals_per_handle_runs(measure_every, pt_every):
         if lat.n_sets < 2:
             ser.pop("Q", None)
         acc = torch.zeros(lat.n_sets * lat.n_temps, dtype=torch.int64, device="cuda")
-        ptv = pt_every if lat.model == B.SPIN_EA else pt_every
-        items.append(lat.batch_item(betas, ser, acc))
-        outs_b.append((ser, acc))
+        labels = lat.slot_labels() if lat.model == B.SPIN_EA else None
+        items.append(lat.batch_item(betas, ser, acc, labels))
+        outs_b.append((ser, acc, labels))
     ising_pt = pt_every and any(l.model == B.SPIN_ISING and l.n_temps > 1 for l, _ in batch)
     if ising_pt:
         with pytest.raises(B.SpinError):
@@ -65,11 +65,14 @@ def test_batch_equals_per_handle_runs(measure_every, pt_every):
     for i in keep:
         lat, betas = plain[i]
         acc = torch.zeros(lat.n_sets * lat.n_temps, dtype=torch.int64, device="cuda")
+        labels = lat.slot_labels() if lat.model == B.SPIN_EA else None
         out = lat.run(betas, n, measure_every, pt_every if lat.model == B.SPIN_EA or lat.n_temps == 1 else 0,
-                      accepted=acc)
+                      accepted=acc, labels=labels)
         lb = batch[i][0]
         assert torch.equal(lat.spins, lb.spins), KINDS[i]
-        ser, accb = outs_b[i]
+        ser, accb, labels_b = outs_b[i]
+        if labels is not None:
+            assert torch.equal(labels, labels_b), KINDS[i]
         for key in ("E", "M", "Q"):
             if key in out and key in ser:
                 assert torch.equal(out[key], ser[key]), (KINDS[i], key)
@@ -84,16 +87,20 @@ def test_batch_matches_oracle_for_one_realisation():
     lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=32, n_temps=4, n_sets=2, seed=seed)
     betas = list(1.0 / np.geomspace(0.9, 2.0, 4))
     ser = lat.series_buffers(n)
-    sp.batch_run([lat.batch_item(betas, ser)], n, 1, 1)
+    labels = lat.slot_labels()
+    sp.batch_run([lat.batch_item(betas, ser, labels=labels)], n, 1, 1)
     got = lat.unpack().cpu().numpy()
     E = ser["E"].cpu().numpy().reshape(n, 2, 4, 32)
+    lab_gpu = labels.cpu().numpy()
     for r in (0, 17, 31):
         J = oracle.ea_couplings(3, L, r, seed)
         s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, 0, t), bit=r)
                                 for t in range(4)]) for a in range(2)]).copy()
-        Es, Qs, acc, _ = oracle.pt_run(3, L, s, betas, seed, r, 0, 0, n, 1, J=J)
+        lab = np.tile(np.arange(4, dtype=np.int32), (2, 1))
+        Es, Qs, acc, _ = oracle.pt_run(3, L, s, betas, seed, r, 0, 0, n, 1, J=J, labels=lab)
         assert np.array_equal(got[:, :, r], s)
         assert np.array_equal(E[:, :, :, r], Es)
+        assert np.array_equal(lab_gpu[:, :, r], lab)
 
 
 def test_batch_timeout_is_reported_and_context_survives():

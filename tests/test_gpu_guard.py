@@ -72,6 +72,11 @@ class Handle:
         self.guards.append(g)
         return g
 
+    def labels(self):
+        g = Guarded(self.n_lat, torch.int32, 0)
+        self.guards.append(g)
+        return g
+
     def close(self):
         B.spin_destroy(self.h)
 
@@ -83,14 +88,15 @@ def _run_all(hd, betas, order=None):
     ser = hd.series(n)
     pt = 1 if hd.model == B.SPIN_EA else 0
     acc = hd.accepted() if pt else None
+    lab = hd.labels() if pt else None
     t = lambda k: ser[k].t if k in ser else None
     B.spin_run(hd.h, hd.couplings, betas, n, 1 if order is None else order[2], pt, t("E"), t("M"), t("Q"),
-               t("Ef"), t("Mf"), acc.t if acc else None)
+               t("Ef"), t("Mf"), acc.t if acc else None, lab.t if lab else None)
     one = hd.series(1)
     u = lambda k: one[k].t if k in one else None
     B.spin_measure(hd.h, hd.couplings, u("E"), u("M"), u("Q"), u("Ef"), u("Mf"))
     if pt:
-        B.spin_pt_swap(hd.h, hd.couplings, betas, hd.seed, acc.t)
+        B.spin_pt_swap(hd.h, hd.couplings, betas, hd.seed, acc.t, lab.t)
     if hd.model != B.SPIN_HEISENBERG:
         out = Guarded(hd.n_lat * hd.L ** hd.dim, torch.int8)
         hd.guards.append(out)
@@ -145,8 +151,9 @@ def test_no_stray_writes_w64_and_batch():
     for hd, betas in ((ea, [0.5, 0.7, 0.9, 1.1]), (ising, [0.44]), (i8, [0.44])):
         ser = hd.series(n)
         acc = hd.accepted()
+        lab = hd.labels()
         items.append({"lat": hd.h, "couplings": hd.couplings, "betas": betas,
-                      **{k: g.t for k, g in ser.items()}, "accepted": acc.t})
+                      **{k: g.t for k, g in ser.items()}, "accepted": acc.t, "labels": lab.t})
     B.spin_batch_run(items, n, 1, 1, torch.cuda.current_stream().cuda_stream)
     for hd in (ea, ising, i8):
         B.spin_sync(hd.h)

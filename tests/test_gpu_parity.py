@@ -154,9 +154,12 @@ def test_fused_many_lattices_short_strips():
 
 
 # ------------------------------------------------------------------ EA
-def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None, width=32, dim=3):
+def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None, width=32, dim=3,
+               labels=None):
     """Oracle runs of single realisations; `width` realisations share each
-    update uniform (key r >> 5 for 32, r >> 6 for 64)."""
+    update uniform (key r >> 5 for 32, r >> 6 for 64).  labels (optional,
+    int32 [n_sets, n_temps, n_real], modified in place) are moved with the
+    configurations as the oracle exchanges them."""
     n_temps = len(betas)
     shift = 5 if width == 32 else 6
     reals = range(n_real) if reals is None else reals
@@ -166,7 +169,11 @@ def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None,
         sp_ = np.stack([np.stack([oracle.ising_init(dim, L, seed, oracle.lattice_id(a, r >> 5, t),
                                                     bit=r & 31) for t in range(n_temps)])
                         for a in range(n_sets)]).copy()
-        E, Q, acc, _ = oracle.pt_run(dim, L, sp_, betas, seed, r, r >> shift, 0, n_sweeps, pt_every, J=J)
+        lab = None if labels is None else np.ascontiguousarray(labels[:, :, r])
+        E, Q, acc, _ = oracle.pt_run(dim, L, sp_, betas, seed, r, r >> shift, 0, n_sweeps, pt_every, J=J,
+                                     labels=lab)
+        if labels is not None:
+            labels[:, :, r] = lab
         res[r] = (J, sp_, E, Q, acc)
     return res
 
@@ -277,11 +284,15 @@ def test_ea_parallel_tempering_bit_exact(layout, L):
     betas = list(1.0 / np.geomspace(0.9, 2.0, 5))
     lat = sp.Lattice(B.SPIN_EA, 3, L, layout, n_real=n_real, n_temps=5, n_sets=2, seed=seed)
     acc = torch.zeros(2 * 5, dtype=torch.int64, device="cuda")
-    out = lat.run(betas, n, measure_every=1, pt_every=1, accepted=acc)
+    # configuration labels: arbitrary caller values, moved with the configurations
+    lab0 = (np.arange(2 * 5 * n_real, dtype=np.int32) * 7 + 3).reshape(2, 5, n_real)
+    labels = torch.from_numpy(lab0.copy()).cuda()
+    out = lat.run(betas, n, measure_every=1, pt_every=1, accepted=acc, labels=labels)
     got = host(lat.unpack())
     Eser = host(out["E"]).reshape(n, 2, 5, n_real)
     Qser = host(out["Q"]).reshape(n, 5, n_real)
-    ref = _ea_oracle(L, seed, betas, n_real, 2, n, pt_every=1)
+    lab_ref = lab0.copy()
+    ref = _ea_oracle(L, seed, betas, n_real, 2, n, pt_every=1, labels=lab_ref)
     acc_ref = np.zeros((2, 5), np.int64)
     for r, (J, s, Es, Qs, ac) in ref.items():
         assert np.array_equal(got[:, :, r], s), r
@@ -289,6 +300,8 @@ def test_ea_parallel_tempering_bit_exact(layout, L):
         assert np.array_equal(Qser[:, :, r], Qs), r
         acc_ref += ac
     assert np.array_equal(host(acc).reshape(2, 5), acc_ref)
+    assert np.array_equal(host(labels), lab_ref)
+    assert not np.array_equal(lab_ref, lab0)
     assert acc_ref.sum() > 0
     assert lat.pt_steps_done == n
 

@@ -32,12 +32,15 @@ def test_ising2d_parallel_tempering_bit_exact(L, pt_every, me, n):
     betas = list(np.linspace(0.1, 0.15, n_t))
     lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=n_t, seed=seed)
     acc = torch.zeros(n_t, dtype=torch.int64, device="cuda")
-    out = lat.run(betas, n, me, pt_every, accepted=acc)
+    labels = lat.slot_labels()
+    out = lat.run(betas, n, me, pt_every, accepted=acc, labels=labels)
     s = np.stack([oracle.ising_init(2, L, seed, oracle.lattice_id(0, 0, t)) for t in range(n_t)])[None].copy()
-    Es, _, acc_o, _ = oracle.pt_run(2, L, s, betas, seed, 0, 0, 0, n, pt_every)
+    lab = np.arange(n_t, dtype=np.int32)[None].copy()
+    Es, _, acc_o, _ = oracle.pt_run(2, L, s, betas, seed, 0, 0, 0, n, pt_every, labels=lab)
     assert np.array_equal(lat.unpack().cpu().numpy()[:, :, 0], s)
     assert np.array_equal(out["E"].view(n // me, 1, n_t).cpu().numpy(), Es[me - 1::me])
     assert np.array_equal(acc.cpu().numpy(), acc_o[0])
+    assert np.array_equal(labels.view(1, n_t).cpu().numpy(), lab)
 
 
 @pytest.mark.parametrize("L,pt_every,me,n", [(8, 2, 1, 9), (16, 4, 3, 12), (24, 1, 1, 5), (12, 2, 1, 6)])

@@ -317,11 +317,16 @@ int64_t spin_pt_steps_done(const spin_lattice *lat);
 int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_done);
 
 /* Kernel variant.  2D int8 ferromagnet: 0 = two in-place colour phases per
- * sweep, 1 = one fused out-of-place pass per sweep (default for L > 128),
- * 3 = resident: one CTA per lattice holds the whole lattice in shared
- * memory for all sweeps of a call and measures E and M itself (default for
- * L % 8 == 0, L <= 128; the paper's tempering code likewise maps replicas
- * to thread blocks, Sec. 7); all three give identical results.  3D int8
+ * sweep, 1 = one fused out-of-place pass per sweep (default for L > 128
+ * with L % 256 != 0), 3 = resident: one CTA per lattice holds the whole
+ * lattice in shared memory for all sweeps of a call and measures E and M
+ * itself (default for L % 8 == 0, L <= 128; the paper's tempering code
+ * likewise maps replicas to thread blocks, Sec. 7), 4 = coded: a call of at
+ * least 4 sweeps packs the lattices into a handle-owned 1-bit buffer
+ * (L^2 / 8 bytes per lattice, allocated on first use, kept until
+ * spin_destroy), runs the synchronous multi-spin-coded sweep (Sec. 6) and
+ * unpacks them, shorter calls take the fused pass (default for
+ * L % 256 == 0, L > 128); all four give identical results.  3D int8
  * ferromagnet: 0 = colour phases, 3 = resident (default for L % 8 == 0,
  * L <= 24), identical results.  Heisenberg: 0 = the full-accuracy FP32
  * library functions (default), 2 = hardware approximations of sin, cos and

@@ -168,6 +168,7 @@ bool tables_cached_for_batch(const spin_lattice *h, const double *betas, bool pt
   return !pt || (!h->pt_betas_cached.empty() && memcmp(h->pt_betas_cached.data(), betas, nb) == 0);
 }
 bool fused2d_supported(int L);
+bool coded_i8_supported(const spin_lattice *h);
 cudaError_t launch_init_msc2d(spin_lattice *h);
 }
 
@@ -205,7 +206,9 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   h->g.fgrp2 = make_fastdiv((uint32_t)std::max(1, desc->n_real / 64));
   h->n_lat = (int64_t)desc->n_sets * desc->n_temps * desc->n_real;
   const bool i8 = desc->model == SPIN_ISING && desc->layout == SPIN_I8, i8_2d = i8 && desc->dim == 2;
-  h->variant = i8 && resident_supported(desc->dim, desc->L) ? 3 : (i8_2d && fused2d_supported(desc->L) ? 1 : 0);
+  h->variant = i8 && resident_supported(desc->dim, desc->L)
+                   ? 3
+                   : (i8_2d && coded_i8_supported(h) ? 4 : (i8_2d && fused2d_supported(desc->L) ? 1 : 0));
   const int nt = desc->n_temps;
   bool ok = cudaMalloc(&h->d_thr, 16 * (size_t)nt) == cudaSuccess &&
             cudaMalloc(&h->d_pt_off, 4 * (size_t)nt) == cudaSuccess &&
@@ -474,9 +477,10 @@ int spin_set_update_order(spin_lattice *h, int32_t order, int32_t tile, int32_t 
 }
 
 int spin_set_variant(spin_lattice *h, int32_t variant) {
-  if (!h || variant < 0 || variant > 3) return SPIN_EINVAL;
+  if (!h || variant < 0 || variant > 4) return SPIN_EINVAL;
   const bool i8 = h->d.model == SPIN_ISING && h->d.layout == SPIN_I8, i8_2d = i8 && h->d.dim == 2;
   if (variant == 1 && !(i8_2d && fused2d_supported(h->g.L))) return SPIN_EINVAL;
+  if (variant == 4 && !(coded_i8_supported(h) && fused2d_supported(h->g.L))) return SPIN_EINVAL;
   if (variant == 3 && !(i8 && resident_supported(h->d.dim, h->g.L))) return SPIN_EINVAL;
   if (variant == 2 && h->d.model != SPIN_HEISENBERG) return SPIN_EINVAL;
   h->variant = variant;

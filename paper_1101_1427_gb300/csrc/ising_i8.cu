@@ -417,6 +417,12 @@ cudaError_t launch_couplings_i8(spin_lattice *h) {
 
 cudaError_t launch_fused2d_i8(spin_lattice *h, int64_t n_sweeps);  // fused2d.cu
 bool fused2d_supported(int L);                                     // fused2d.cu
+cudaError_t launch_sweeps_i8_coded(spin_lattice *h, int64_t n_sweeps);  // msc2d.cu
+bool coded_i8_supported(const spin_lattice *h);                         // msc2d.cu
+// Calls of at least this many sweeps take the coded path (variant 4): the two
+// transcoding passes cost about one sweep of HBM traffic, short calls take
+// the fused pass instead.
+constexpr int64_t kCodedMinSweeps = 4;
 
 // Whole lattice in one CTA's shared memory: 16 KB at L = 128 in 2D, 13.5 KB
 // at L = 24 in 3D (at most four chunks per thread, so that each thread's
@@ -463,7 +469,9 @@ cudaError_t launch_sweeps_i8(spin_lattice *h, const int8_t *J, int64_t n_sweeps)
   const RoundKeys rk = make_round_keys(h->d.seed);
   const bool fast2d = g.dim == 2 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
   const bool fast3d = g.dim == 3 && J == nullptr && (g.L % 8) == 0 && h->n_lat <= 65535;
-  if (fast2d && h->variant == 1 && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
+  if (fast2d && h->variant == 4 && coded_i8_supported(h) && n_sweeps >= kCodedMinSweeps)
+    return launch_sweeps_i8_coded(h, n_sweeps);
+  if (fast2d && (h->variant == 1 || h->variant == 4) && fused2d_supported(g.L)) return launch_fused2d_i8(h, n_sweeps);
   if ((fast2d || fast3d) && h->variant == 3 && resident_supported(g.dim, g.L))
     return launch_resident(h, n_sweeps, nullptr, nullptr, 1, 1);
   for (int64_t k = 0; k < n_sweeps; ++k) {

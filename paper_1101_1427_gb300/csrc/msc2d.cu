@@ -149,6 +149,104 @@ __global__ void msc2d_pack_kernel(const int8_t *__restrict__ in, uint32_t *__res
   }
 }
 
+// int8 <-> coded transcoding, one warp per 256-site block (lattice, row y,
+// block B) and both colours: lane l holds the eight bytes x = 256 B + 8 l ..
+// + 7 of the row, i.e. the sites k = 128 B + 4 l + q of both colours
+// (x = 2k + p, p = (c + y) & 1), so byte o = 2q + p of every lane is bit l of
+// coded word 4 B + q of colour c, and one warp ballot per byte position o
+// builds that word.  Loads and stores of the int8 rows are 256 contiguous
+// bytes per warp; a warp takes kTcBlocks blocks at a time, all loads first,
+// so that several are in flight.  Block indices are < 2^31 (spin_init checks
+// n_lat L L / 256 < 2^31); fper divides by the blocks per lattice, fbpr by
+// the blocks per row.
+constexpr int kTcBlocks = 4;
+
+struct TcBlock {
+  uint32_t lat;
+  int y, B;
+};
+
+__device__ __forceinline__ TcBlock tc_block(uint32_t blk, const FastDiv &fper, const FastDiv &fbpr) {
+  TcBlock t;
+  t.lat = fdiv(blk, fper);
+  const uint32_t rem = blk - t.lat * fper.d;
+  t.y = (int)fdiv(rem, fbpr);
+  t.B = (int)(rem - (uint32_t)t.y * fbpr.d);
+  return t;
+}
+
+__device__ __forceinline__ int64_t tc_row_byte(const Msc2d &m, const TcBlock &t) {
+  return ((int64_t)t.lat * m.L + t.y) * (int64_t)m.L + 256 * t.B;
+}
+
+__global__ void msc2d_pack_warp_kernel(const int8_t *__restrict__ in, uint32_t *__restrict__ w, Msc2d m,
+                                       uint32_t n_blocks, FastDiv fper, FastDiv fbpr) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t first = warp0 * kTcBlocks; first < n_blocks; first += nwarps * kTcBlocks) {
+    uint2 v[kTcBlocks];
+#pragma unroll
+    for (int u = 0; u < kTcBlocks; ++u) {
+      v[u] = make_uint2(0u, 0u);
+      if (first + u < n_blocks) {
+        const TcBlock t = tc_block(first + u, fper, fbpr);
+        v[u] = reinterpret_cast<const uint2 *>(in + tc_row_byte(m, t))[lane];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kTcBlocks; ++u) {
+      if (first + u >= n_blocks) break;  // uniform across the warp
+      const TcBlock t = tc_block(first + u, fper, fbpr);
+      uint32_t word = 0;
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const uint32_t half = o < 4 ? v[u].x : v[u].y;
+        const uint32_t bal = __ballot_sync(0xffffffffu, (half >> (8 * (o & 3) + 1)) & 1u);  // bit 1 <=> -1
+        if (lane == o) word = bal;
+      }
+      if (lane < 8) {
+        const int q = lane >> 1, c = (lane & 1) ^ (t.y & 1);  // byte parity p = (c + y) & 1
+        w[row_word(m, t.lat, c, t.y) + 4 * t.B + q] = word;
+      }
+    }
+  }
+}
+
+__global__ void msc2d_unpack_warp_kernel(const uint32_t *__restrict__ w, int8_t *__restrict__ out, Msc2d m,
+                                         uint32_t n_blocks, FastDiv fper, FastDiv fbpr) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t first = warp0 * kTcBlocks; first < n_blocks; first += nwarps * kTcBlocks) {
+    // lanes 0..7 fetch the eight words of each block, every lane then takes its bit of each
+    uint32_t mine[kTcBlocks];
+#pragma unroll
+    for (int u = 0; u < kTcBlocks; ++u) {
+      mine[u] = 0u;
+      if (lane < 8 && first + u < n_blocks) {
+        const TcBlock t = tc_block(first + u, fper, fbpr);
+        const int q = lane >> 1, c = (lane & 1) ^ (t.y & 1);
+        mine[u] = w[row_word(m, t.lat, c, t.y) + 4 * t.B + q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kTcBlocks; ++u) {
+      if (first + u >= n_blocks) break;  // uniform across the warp
+      const TcBlock t = tc_block(first + u, fper, fbpr);
+      uint32_t lo = 0, hi = 0;
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const uint32_t word = __shfl_sync(0xffffffffu, mine[u], o);
+        const uint32_t byte = ((word >> lane) & 1u) ? 0xFFu : 0x01u;
+        if (o < 4) lo |= byte << (8 * o);
+        else hi |= byte << (8 * (o - 4));
+      }
+      reinterpret_cast<uint2 *>(out + tc_row_byte(m, t))[lane] = make_uint2(lo, hi);
+    }
+  }
+}
+
 Msc2d geom2d(const spin_lattice *h) {
   Msc2d m;
   m.L = h->g.L;
@@ -172,7 +270,9 @@ cudaError_t launch_init_msc2d(spin_lattice *h) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweeps_msc2d(spin_lattice *h, int64_t n_sweeps) {
+namespace {
+// n_sweeps coded sweeps of the handle's lattices held in the words w.
+cudaError_t sweeps_msc2d_words(spin_lattice *h, uint32_t *w, int64_t n_sweeps) {
   const Msc2d m = geom2d(h);
   const RoundKeys rk = make_round_keys(h->d.seed);
   const int64_t blocks = h->n_lat * m.L * m.bpr;  // < 2^31, checked by spin_init
@@ -180,13 +280,50 @@ cudaError_t launch_sweeps_msc2d(spin_lattice *h, int64_t n_sweeps) {
   for (int64_t k = 0; k < n_sweeps; ++k) {
     const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
     for (int colour = 0; colour < 2; ++colour) {
-      const cudaError_t e = launch_dependent(msc2d_phase_kernel, dim3(grid), dim3(32 * kWarps), 0, h->stream,
-                                             (uint32_t *)h->spins, m, h->g, (uint32_t)blocks,
-                                             (const uint32_t *)h->d_thr, rk, sweep, colour);
+      const cudaError_t e = launch_dependent(msc2d_phase_kernel, dim3(grid), dim3(32 * kWarps), 0, h->stream, w, m,
+                                             h->g, (uint32_t)blocks, (const uint32_t *)h->d_thr, rk, sweep, colour);
       if (e != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_sweeps_msc2d(spin_lattice *h, int64_t n_sweeps) {
+  return sweeps_msc2d_words(h, (uint32_t *)h->spins, n_sweeps);
+}
+
+// Sweeps of 2D int8 ferromagnets through the coded layout: the lattices are
+// packed into a handle-owned word buffer (L^2 / 8 bytes per lattice), swept
+// with the bit-sliced coded kernel -- the same random words and the same
+// decisions as every int8 kernel -- and unpacked into the caller's buffer.
+bool coded_i8_supported(const spin_lattice *h) {
+  return h->d.model == SPIN_ISING && h->d.layout == SPIN_I8 && h->d.dim == 2 && h->g.L % 256 == 0 &&
+         h->n_lat * (int64_t)h->g.L * (h->g.L / 256) < ((int64_t)1 << 31);
+}
+
+cudaError_t launch_sweeps_i8_coded(spin_lattice *h, int64_t n_sweeps) {
+  const Msc2d m = geom2d(h);
+  const size_t bytes = (size_t)h->n_lat * (size_t)m.lat_words * 4;
+  if (!h->d_pingpong || h->pingpong_bytes < bytes) {
+    if (h->d_pingpong) cudaFree(h->d_pingpong);
+    h->d_pingpong = nullptr;
+    cudaError_t e = cudaMalloc(&h->d_pingpong, bytes);
+    if (e != cudaSuccess) return e;
+    h->pingpong_bytes = bytes;
+  }
+  uint32_t *words = (uint32_t *)h->d_pingpong;
+  const uint32_t n_blocks = (uint32_t)(h->n_lat * (int64_t)m.L * m.bpr);  // < 2^31 (coded_i8_supported)
+  const FastDiv fper = make_fastdiv((uint32_t)(m.L * m.bpr)), fbpr = make_fastdiv((uint32_t)m.bpr);
+  // one group of kTcBlocks blocks per warp, 8 warps per CTA
+  const unsigned grid = (unsigned)(((int64_t)n_blocks + 8 * kTcBlocks - 1) / (8 * kTcBlocks));
+  msc2d_pack_warp_kernel<<<grid, 256, 0, h->stream>>>((const int8_t *)h->spins, words, m, n_blocks, fper, fbpr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = sweeps_msc2d_words(h, words, n_sweeps);
+  if (e != cudaSuccess) return e;
+  msc2d_unpack_warp_kernel<<<grid, 256, 0, h->stream>>>(words, (int8_t *)h->spins, m, n_blocks, fper, fbpr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_msc2d(spin_lattice *h, int8_t *out) {

@@ -123,6 +123,7 @@ CASES = [
     ("ea3d_coded", (B.SPIN_EA, 3, 8, B.SPIN_MSC1), dict(n_real=64, n_temps=5, n_sets=2), None, None),
     ("ea2d_coded", (B.SPIN_EA, 2, 16, B.SPIN_MSC1), dict(n_real=64, n_temps=3, n_sets=2), None, None),
     ("ea2d_coded_persite", (B.SPIN_EA, 2, 10, B.SPIN_MSC1), dict(n_real=32, n_temps=2, n_sets=2), None, None),
+    ("i8_2d_coded_path", (B.SPIN_ISING, 2, 256, B.SPIN_I8), dict(n_real=2), 4, None),
     ("heis3d", (B.SPIN_HEISENBERG, 3, 8, B.SPIN_F32X4), dict(n_temps=2), 2, None),
     ("heis2d", (B.SPIN_HEISENBERG, 2, 18, B.SPIN_F32X4), dict(n_temps=2), 0, None),
     ("heis2d_dcb8", (B.SPIN_HEISENBERG, 2, 32, B.SPIN_F32X4), dict(n_temps=2), 2, (B.SPIN_ORDER_DCB, 8, 2)),

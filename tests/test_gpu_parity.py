@@ -64,6 +64,28 @@ def _ising_run_oracle(dim, L, seed, betas, n_real, n_sweeps, first=0):
     return s, E, M
 
 
+@pytest.mark.parametrize("L,n_real,calls", [(256, 1, (4,)), (512, 3, (3, 5)), (768, 2, (9, 1, 4))])
+def test_ising2d_i8_coded_variant_bit_exact(L, n_real, calls):
+    """int8 ferromagnets with L % 256 == 0 sweep through the 1-bit coded
+    layout (variant 4, the default there) in calls of >= 4 sweeps and through
+    the fused pass otherwise; lattices, E and M equal the oracle after every
+    call, so packing, the coded sweeps and unpacking are exact."""
+    seed, betas = 13, [0.4407]
+    lat = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_real=n_real, seed=seed)
+    assert B.lib().spin_set_variant(lat.h, 4) == B.SPIN_OK
+    s = oracle_lattices_ising(2, L, seed, n_real, 1, 1)
+    done = 0
+    for n in calls:
+        lat.sweep(betas, n)
+        for r in range(n_real):
+            E, M, _ = oracle.ising_run(2, L, s[0, 0, r], betas[0], seed, oracle.lattice_id(0, r, 0), done, n)
+        done += n
+        assert np.array_equal(host(lat.spins).reshape(s.shape), s), (L, n)
+        Eg, Mg, _ = lat.measure()
+        assert np.array_equal(host(Eg), [oracle.ising_energy(2, L, s[0, 0, r]) for r in range(n_real)])
+        assert np.array_equal(host(Mg), [int(s[0, 0, r].astype(np.int64).sum()) for r in range(n_real)])
+
+
 @pytest.mark.parametrize("variant", [0, 1, 3])
 def test_ising2d_L64_1000_sweeps_bit_exact(variant):
     """2D Ising L=64, beta = 0.4407, 1000 sweeps, E and M after every sweep."""

@@ -31,12 +31,13 @@ sys.path.insert(0, ROOT)
 
 L = 16384
 BETAS = [0.40, 0.4407, 0.50]
-SWEEPS_PER_STEP = 10
+SWEEPS_PER_STEP = 50
 METRIC = "spin flips/ns, 2D Ising L=16384 checkerboard Metropolis, 1 GB300"
 UNIT = "flips/ns"
 WORKLOAD = ("2D Ising ferromagnet L=16384 periodic, 3 lattices at beta 0.40/0.4407/0.50, "
-            "hot start, Philox4x32-10 uniform per site, %d sweeps + E/M reduction per step; "
-            "1-bit multi-spin-coded layout (int8 layout reported beside it)" % SWEEPS_PER_STEP)
+            "hot start, Philox4x32-10 uniform per site, %d sweeps + E/M reduction per step "
+            "(20 steps = the configuration's 1000 sweeps); 1-bit multi-spin-coded layout (int8 layout "
+            "reported beside it)" % SWEEPS_PER_STEP)
 
 # Roofline of the sweep: every attempted flip consumes one 32-bit Philox
 # word, and Philox4x32-10 costs 20 wide (32x32->64) multiplies per 4 words,
@@ -46,6 +47,24 @@ WORKLOAD = ("2D Ising ferromagnet L=16384 periodic, 3 lattices at beta 0.40/0.44
 # roof is therefore SMs x 32 x f_SM wide multiplies per second.
 WIDE_MULS_PER_FLIP = 5
 WIDE_MULS_PER_CLK_PER_SM = 32
+# The other configurations' roofs, from algorithmic operation counts per
+# attempted flip (counted from the algorithm, not from compiled code):
+#  * Heisenberg update: one whole Philox call (20 wide multiplies); its
+#    other classes -- about 60 FP32 operations (128 per clock per SM) and 5
+#    MUFU / conversion operations (16 per clock) -- bind later.
+#  * coded EA word-site (32 realisations, one shared uniform), on the ALU
+#    pipe (64 three-input logic operations per clock per SM, measured 63.7):
+#    sweep 28 = 5 Philox XORs (a quarter call) + 3 threshold compares + 6
+#    bond terms s ^ s_j ^ J + 8 for the bit-sliced 6-input count + 5 for the
+#    flip mask + 1 to apply it; measuring E, M and Q every sweep adds 12
+#    (3 bond terms and carry-save counting for E, M, half of Q per set) and
+#    the bitwise exchange about 1 (3 operations per word of an accepted
+#    pair, half the pairs tried per sweep).  Its Philox multiplies (5 per 32
+#    flips) bind far later.
+HEIS_WIDE_MULS_PER_FLIP = 20
+ALU_OPS_PER_CLK_PER_SM = 64
+EA_SWEEP_ALU_PER_WORD = 28
+EA_PT_ALU_PER_WORD = 28 + 12 + 1
 
 # DRAM bytes of one phase launch of the coded sweep over the three lattices
 # (mean of two launches captured with ncu, summarised in profiles/), valid
@@ -151,25 +170,92 @@ def oracle_rate(seconds=10.0):
     return flips / (dt * 1e9), flips, dt
 
 
+def oracle_omp_sweeps(s, first, count):
+    """`count` full sweeps of the workload's lattice s on all host cores
+    (the oracle's sweep with the rows of each colour phase shared among
+    OpenMP threads); returns (flips, seconds, threads used)."""
+    import oracle
+    t0 = time.perf_counter()
+    used = 0
+    for k in range(count):
+        _, used = oracle.omp_ising2d_sweeps(L, s, BETAS[1], 1, oracle.lattice_id(0, 0, 1), first + k, 1)
+    return count * L * L, time.perf_counter() - t0, used
+
+
+def oracle_omp_rate(seconds=10.0):
+    s = oracle_lattice()
+    oracle_omp_sweeps(s, 0, 1)  # warm
+    flips, dt, k, used = 0, 0.0, 1, 0
+    while dt < seconds:
+        f, t, used = oracle_omp_sweeps(s, k, 1)
+        flips, dt, k = flips + f, dt + t, k + 1
+    return flips / (dt * 1e9), flips, dt, used
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
     s = oracle_lattice()
-    oracle_bands(s, 64, steps=args.warmup)
-    flips, dt = oracle_bands(s, 64, steps=args.steps, first=args.warmup)
+    oracle_omp_sweeps(s, 0, args.warmup)
+    flips, dt, used = oracle_omp_sweeps(s, args.warmup, args.steps)
     value = flips / (dt * 1e9)
-    sample = ("per step one 64-row band (colour 0, then colour 1) of the workload's L=16384 lattice at "
-              "beta=0.4407, swept by the oracle's row-band sweep after its hot start (untimed)")
+    sample = (f"per step one full checkerboard sweep of the workload's L=16384 lattice at beta=0.4407 "
+              f"(slot 1, after the oracle's untimed hot start) on {used} host threads: the oracle's sweep "
+              f"with the rows of each colour phase shared among OpenMP threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def config_rooflines(side, i8_value, sms, mhz):
+    """Roofline of every configuration's kernel from its algorithmic
+    operations per attempted flip (see the constants at the top) and the
+    pipe rates per clock per SM at the sampled SM clock."""
+    f = mhz * 1e6
+    philox2d = sms * WIDE_MULS_PER_CLK_PER_SM * f / WIDE_MULS_PER_FLIP / 1e9   # flips/ns
+    heis = sms * WIDE_MULS_PER_CLK_PER_SM * f / HEIS_WIDE_MULS_PER_FLIP / 1e9
+    ea_sweep = sms * ALU_OPS_PER_CLK_PER_SM * f * 32 / EA_SWEEP_ALU_PER_WORD / 1e9
+    ea_pt = sms * ALU_OPS_PER_CLK_PER_SM * f * 32 / EA_PT_ALU_PER_WORD / 1e9
+    mul_basis = f"{sms} SMs x {WIDE_MULS_PER_CLK_PER_SM} wide multiplies/clk x {mhz:.0f} MHz"
+    alu_basis = f"{sms} SMs x {ALU_OPS_PER_CLK_PER_SM} logic ops/clk x {mhz:.0f} MHz"
+
+    def line(value, peak, per_flip, basis, kernel):
+        if value is None:
+            return None
+        return {"bound": "alu", "unit": "flips/ns", "achieved": value, "peak": peak, "frac": value / peak,
+                "per_flip": per_flip, "peak_basis": basis, "kernel": kernel}
+
+    out = {"2d_ising_L16384_i8": line(i8_value, philox2d, f"{WIDE_MULS_PER_FLIP} wide multiplies (Philox)",
+                                      mul_basis, "msc2d_pack/phase/unpack (coded path of the int8 layout)")}
+    for key, name in (("heisenberg_L128_fp32_flips_per_ns", "3d_heisenberg_L128_fp32"),
+                      ("heisenberg_L128_fp32_fast_flips_per_ns", "3d_heisenberg_L128_fp32_fast")):
+        out[name] = line(side.get(key), heis, f"{HEIS_WIDE_MULS_PER_FLIP} wide multiplies (one Philox call)",
+                         mul_basis, "heis_phase_kernel")
+    out["3d_ea_L16_sweep"] = line(side.get("ea_L16_w32_sweep_flips_per_ns"), ea_sweep,
+                                  f"{EA_SWEEP_ALU_PER_WORD}/32 logic ops", alu_basis, "msc_phase_kernel")
+    out["3d_ea_L16_pt_per_handle"] = line(side.get("ea_L16_pt_plain_flips_per_ns"), ea_pt,
+                                          f"{EA_PT_ALU_PER_WORD}/32 logic ops", alu_basis,
+                                          "msc_phase_kernel + measure_msc_rows_kernel + pt kernels")
+    out["3d_ea_L16_pt_batched"] = line(side.get("ea_L16_pt_batched_flips_per_ns"), ea_pt,
+                                       f"{EA_PT_ALU_PER_WORD}/32 logic ops", alu_basis, "batch_kernel")
+    # uneven batch: the roof of the mix is its total flips over the sum of
+    # each unit's flips at its own roof
+    n = 1
+    ea_flips = sum(2 * T * R * Le ** 3 for Le, R, T in UNEVEN_EA) * n
+    is_flips = sum(Li * Li for Li in UNEVEN_ISING) * n
+    mix = (ea_flips + is_flips) / (ea_flips / ea_pt + is_flips / philox2d)
+    for key, name in (("uneven_batch_batched_flips_per_ns", "uneven_batch_batched"),
+                      ("uneven_batch_plain_flips_per_ns", "uneven_batch_per_handle")):
+        out[name] = line(side.get(key), mix, "EA units as the tempering form, Ising units 5 wide multiplies",
+                         f"{alu_basis}; {mul_basis}", "batch_kernel" if "batched" in name else "per-handle kernels")
+    return {k: v for k, v in out.items() if v is not None}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -624,7 +710,8 @@ def run_gpu(args, rank, world, local_rank):
     for p in pipes:
         p["h"].close()
 
-    # the int8 layout of the same workload (fused out-of-place sweep)
+    # the int8 layout of the same workload (calls of 50 sweeps take the coded
+    # path: pack, bit-sliced sweeps, unpack)
     lat8 = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, n_temps=n_lat, seed=1 + rank)
     step8 = make_step(lat8)
     step8()
@@ -643,10 +730,16 @@ def run_gpu(args, rank, world, local_rank):
     traffic = KERNEL_TRAFFIC_BYTES if KERNEL_TRAFFIC_SRC_SHA == kernel_sha() else None
     cpu_baseline = None
     if world == 1:
+        omp_value, omp_flips, omp_s, omp_threads = oracle_omp_rate(args.cpu_seconds)
         cpu_value, cpu_flips, cpu_s = oracle_rate(args.cpu_seconds)
-        cpu_baseline = {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": f"{cpu_flips} flips in 256-row bands of the workload's L=16384 lattice at "
-                                  f"beta=0.4407 ({cpu_s:.1f} s, after the oracle's untimed hot start)"}
+        cpu_baseline = {"value": omp_value, "unit": UNIT, "cores": omp_threads, "kind": "oracle",
+                        "sample": f"{omp_flips} flips: full checkerboard sweeps of the workload's L=16384 "
+                                  f"lattice at beta=0.4407 ({omp_s:.1f} s, after the oracle's untimed hot start) "
+                                  f"with the rows of each colour phase shared among {omp_threads} OpenMP threads "
+                                  f"(os.cpu_count() = {os.cpu_count()})",
+                        "single_core": {"value": cpu_value, "unit": UNIT, "cores": 1,
+                                        "sample": f"{cpu_flips} flips in 256-row bands of the same lattice "
+                                                  f"({cpu_s:.1f} s), the serial oracle"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -658,7 +751,8 @@ def run_gpu(args, rank, world, local_rank):
                    "e2e_form": "two handles take alternate steps, their sweeps in order on one compute stream, "
                                "copies on two copy streams ordered by events; each step copies its 3 lattices "
                                "in from pinned host memory and lattices + E, M out",
-                   "parallelism": f"replicas x{world}", **side},
+                   "parallelism": f"replicas x{world}", **side,
+                   "rooflines": config_rooflines(side or {}, i8_value, sms, mhz)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "msc2d_phase_kernel", "launch_ms": launch_ms,
@@ -794,7 +888,7 @@ def run_case(name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

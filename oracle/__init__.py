@@ -68,6 +68,31 @@ def lib():
     return _lib
 
 
+_omp = None
+
+
+def omp_lib():
+    """The all-cores sweep of the CPU baseline (spin_oracle_omp.c)."""
+    global _omp
+    if _omp is None:
+        L = C.CDLL(_build.build_omp())
+        L.or_omp_ising2d_sweeps.argtypes = [C.c_int, C.c_void_p, C.c_double, C.c_uint64, C.c_uint32,
+                                            C.c_uint32, C.c_int64, C.c_int, C.c_void_p]
+        L.or_omp_ising2d_sweeps.restype = C.c_int64
+        _omp = L
+    return _omp
+
+
+def omp_ising2d_sweeps(L, s, beta, seed, lid, first_sweep, n_sweeps, threads=0):
+    """n_sweeps checkerboard sweeps of a 2D L x L int8 ferromagnet in place on
+    `threads` host cores (0: all); returns (flips, threads used)."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous and s.size == L * L
+    used = C.c_int(0)
+    f = omp_lib().or_omp_ising2d_sweeps(L, s.ctypes.data_as(C.c_void_p), beta, seed, lid, first_sweep,
+                                        n_sweeps, threads, C.byref(used))
+    return int(f), used.value
+
+
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 

@@ -1,4 +1,6 @@
-"""Compile the CPU oracle (test infrastructure) into oracle/libspin_oracle.so.
+"""Compile the CPU oracle (test infrastructure) into oracle/libspin_oracle.so,
+and its all-cores sweep for the CPU baseline into oracle/libspin_oracle_omp.so
+(the serial oracle plus spin_oracle_omp.c, built with OpenMP).
 
 Plain gcc, ISO C11, no fast-math and no floating-point contraction, so the
 double-precision threshold tables are the IEEE results of exp() and floor().
@@ -10,17 +12,29 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "spin_oracle.c")
 LIB = os.path.join(HERE, "libspin_oracle.so")
+OMP_SRC = os.path.join(HERE, "spin_oracle_omp.c")
+OMP_LIB = os.path.join(HERE, "libspin_oracle_omp.so")
+FLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-Wall", "-Wextra", "-fPIC", "-shared"]
+
+
+def _stale(lib, srcs):
+    return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(f) for f in srcs)
 
 
 def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-Wall", "-Wextra",
-           "-fPIC", "-shared", SRC, "-o", LIB + ".tmp", "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
+    if force or _stale(LIB, [SRC]):
+        subprocess.run(["gcc", *FLAGS, SRC, "-o", LIB + ".tmp", "-lm"], check=True)
+        os.replace(LIB + ".tmp", LIB)
     return LIB
+
+
+def build_omp(force: bool = False) -> str:
+    if force or _stale(OMP_LIB, [SRC, OMP_SRC]):
+        subprocess.run(["gcc", *FLAGS, "-fopenmp", SRC, OMP_SRC, "-o", OMP_LIB + ".tmp", "-lm"], check=True)
+        os.replace(OMP_LIB + ".tmp", OMP_LIB)
+    return OMP_LIB
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+    print(build_omp(force="--force" in sys.argv))

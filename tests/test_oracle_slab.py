@@ -58,3 +58,18 @@ def test_slab_reads_ghosts_only():
     ys = 3 + np.arange(rows)[:, None]
     xs = np.arange(L)[None, :]
     assert np.array_equal(sl[1:-1] == -1, ((xs + ys) & 1) == 0)
+
+
+@pytest.mark.parametrize("L,threads", [(16, 3), (64, 4), (66, 7)])
+def test_openmp_sweep_equals_serial_sweep(L, threads):
+    """The all-cores sweep of the CPU baseline (rows of each colour phase
+    shared among threads) equals the serial oracle sweep bit for bit."""
+    seed, beta, n = 5, 0.4407, 6
+    lid = oracle.lattice_id(0, 1, 0)
+    s = oracle.ising_init(2, L, seed, lid)
+    t = s.copy()
+    _, _, flips = oracle.ising_run(2, L, s, beta, seed, lid, 3, n, series=False)
+    f2, used = oracle.omp_ising2d_sweeps(L, t, beta, seed, lid, 3, n, threads)
+    assert np.array_equal(s, t)
+    assert f2 == flips
+    assert used >= 1

@@ -79,6 +79,10 @@ def omp_lib():
         L.or_omp_ising2d_sweeps.argtypes = [C.c_int, C.c_void_p, C.c_double, C.c_uint64, C.c_uint32,
                                             C.c_uint32, C.c_int64, C.c_int, C.c_void_p]
         L.or_omp_ising2d_sweeps.restype = C.c_int64
+        p, i32, u32, u64, i64, dbl = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_int64, C.c_double
+        L.or_omp_pt_run.argtypes = [i32, i32, i32, i32, p, p, p, u64, u32, u32, u32, i64, i32,
+                                    p, p, p, p, p, i32]
+        L.or_omp_heis_run.argtypes = [i32, i32, p, dbl, u64, u32, u32, i64, i32, i32, p, p, i32]
         _omp = L
     return _omp
 
@@ -91,6 +95,36 @@ def omp_ising2d_sweeps(L, s, beta, seed, lid, first_sweep, n_sweeps, threads=0):
     f = omp_lib().or_omp_ising2d_sweeps(L, s.ctypes.data_as(C.c_void_p), beta, seed, lid, first_sweep,
                                         n_sweeps, threads, C.byref(used))
     return int(f), used.value
+
+
+def omp_pt_run(dim, L, spins, betas, seed, r, rkey, first_sweep, n_sweeps, pt_every, pt_step0=0, J=None,
+               labels=None, threads=0):
+    """pt_run with the lattices of each sweep shared among host threads (the
+    same results bit for bit)."""
+    n_sets, n_temps, _ = spins.shape
+    assert spins.flags.c_contiguous and spins.dtype == np.int8 and n_temps <= 4096 and n_sets <= 2
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    E = np.zeros((n_sweeps, n_sets, n_temps), np.int64)
+    Q = np.zeros((n_sweeps, n_temps), np.int64)
+    acc = np.zeros((n_sets, n_temps), np.int64)
+    step = np.array([pt_step0], np.uint32)
+    omp_lib().or_omp_pt_run(dim, L, n_temps, n_sets, _ptr(spins), _ptr(J), _ptr(b), seed, r, rkey,
+                            first_sweep, n_sweeps, pt_every, _ptr(step), _ptr(E), _ptr(Q), _ptr(acc),
+                            _ptr(labels), threads)
+    return E, Q, acc, int(step[0])
+
+
+def omp_heis_run(dim, L, s, beta, seed, lid, first_sweep, n_sweeps, renorm_every=100, measure_every=1,
+                 threads=0):
+    """heis_run with the sites of each colour phase shared among host threads
+    (the lattice equals the serial run bit for bit; E and M are summed in a
+    thread-dependent order); measurements after every measure_every sweeps."""
+    rows = n_sweeps // measure_every if measure_every > 0 else 0
+    E = np.zeros(rows, np.float64)
+    M = np.zeros((rows, 3), np.float64)
+    omp_lib().or_omp_heis_run(dim, L, _ptr(s), beta, seed, lid, first_sweep, n_sweeps, renorm_every,
+                              measure_every, _ptr(E), _ptr(M), threads)
+    return E, M
 
 
 def _ptr(a):

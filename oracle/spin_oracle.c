@@ -451,8 +451,8 @@ void or_heis_init(int dim, int L, double *s, uint64_t seed, uint32_t lattice_id)
  * it with the Metropolis rule using word 2: dE = -(n - s_i) . h_i, h_i the
  * sum of the neighbour spins; accept iff dE <= 0 or u3 < exp(-beta dE).
  * Returns |u3 - exp(-beta dE)|: how far the decision was from flipping. */
-static double or_heis_site(int dim, int L, double *s, int64_t i, int colour, double beta, uint64_t seed,
-                           uint32_t lattice_id, uint32_t sweep) {
+double or_heis_site(int dim, int L, double *s, int64_t i, int colour, double beta, uint64_t seed,
+                    uint32_t lattice_id, uint32_t sweep) {
   double h[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < dim; ++d) {
     int64_t up = or_neighbour(dim, L, i, d, +1);

@@ -101,35 +101,44 @@ def test_ea_L16_full_size_batched_sampled_realisations():
 
 def test_ea_L16_full_size_long_run_first_and_last_group():
     """3D EA L=16, 1024 realisations x 32 slots x 2 sets, exchange and
-    measurement every sweep for 2000 sweeps in one batched launch: one
-    realisation of the first and one of the last group of 32 equal their
-    oracle runs (lattices, energy and overlap series every sweep)."""
+    measurement every sweep for the configuration's full 10^4 sweeps in one
+    batched launch: one realisation of the first and one of the last group
+    of 32 equal their oracle runs (lattices, energy and overlap series every
+    sweep, exchange counts and configuration labels), the oracle running on
+    the host cores while the GPU works."""
     from concurrent.futures import ThreadPoolExecutor
-    L, seed, n = 16, 9, 2000
+    L, seed, n = 16, 9, 10000
     betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
-
-    def oracle_run(r):
-        J = oracle.ea_couplings(3, L, r, seed)
-        s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t), bit=r & 31)
-                                for t in range(32)]) for a in range(2)]).copy()
-        Es, Qs, _, _ = oracle.pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J)
-        return s, Es, Qs
-
     reals = (5, 31 * 32 + 26)
-    with ThreadPoolExecutor(len(reals)) as ex:  # the oracle's C calls run while the GPU works
-        futs = [ex.submit(oracle_run, r) for r in reals]
+
+    def oracle_runs():
+        out = []
+        for r in reals:
+            J = oracle.ea_couplings(3, L, r, seed)
+            s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t), bit=r & 31)
+                                    for t in range(32)]) for a in range(2)]).copy()
+            lab = np.tile(np.arange(32, dtype=np.int32), (2, 1))
+            Es, Qs, acc, _ = oracle.omp_pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J, labels=lab)
+            out.append((s, Es, Qs, lab))
+        return out
+
+    with ThreadPoolExecutor(1) as ex:  # the oracle's C calls run while the GPU works
+        fut = ex.submit(oracle_runs)
         lat = sp.Lattice(B.SPIN_EA, 3, L, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=seed)
-        ser = lat.series_buffers(n)
-        sp.batch_run([lat.batch_item(betas, ser)], n, 1, 1)
+        ser = {"E": torch.zeros(n * 2 * 32 * 1024, dtype=torch.int64, device="cuda"),
+               "Q": torch.zeros(n * 32 * 1024, dtype=torch.int64, device="cuda")}
+        labels = lat.slot_labels()
+        sp.batch_run([lat.batch_item(betas, ser, labels=labels)], n, 1, 1)
         lat.sync()
+        assert lat.sweeps_done == n and lat.pt_steps_done == n
         got = lat.unpack()
         E = ser["E"].view(n, 2, 32, 1024)
         Q = ser["Q"].view(n, 32, 1024)
-        for r, f in zip(reals, futs):
-            s, Es, Qs = f.result()
+        for r, (s, Es, Qs, lab) in zip(reals, fut.result()):
             assert np.array_equal(got[:, :, r].cpu().numpy(), s), r
             assert np.array_equal(E[:, :, :, r].cpu().numpy(), Es), r
             assert np.array_equal(Q[:, :, r].cpu().numpy(), Qs), r
+            assert np.array_equal(labels[:, :, r].cpu().numpy(), lab), r
 
 
 @pytest.mark.parametrize("variant", [0, 2])
@@ -166,6 +175,44 @@ def test_heis_L128_renormalisation():
     lat.sweep([0.693], 100)
     v = lat.spins.view(-1, 4)[:, :3].double()
     assert torch.max(torch.abs(torch.linalg.norm(v, dim=1) - 1)).item() <= 1e-6
+
+
+def test_heis_L128_long_run_energy_matches_fp64_oracle():
+    """The 3D Heisenberg configuration at full size: L = 128, beta = 0.693,
+    2000 sweeps from the hot start with renormalisation every 100 sweeps, E
+    every 10 sweeps.  The FP32 GPU chain and the FP64 oracle chain (same
+    seed, so the same random numbers; they part at the first decision that
+    differs) have window means of the energy per spin within 3 combined
+    standard errors, and their paired difference has mean zero within 3
+    standard errors."""
+    from concurrent.futures import ThreadPoolExecutor
+    L, beta, n, every, seed = 128, 0.693, 2000, 10, 10
+    N = L ** 3
+    lid = oracle.lattice_id(0, 0, 0)
+
+    def oracle_run():
+        s = oracle.heis_init(3, L, seed, lid)
+        E, _ = oracle.omp_heis_run(3, L, s, beta, seed, lid, 0, n, renorm_every=100, measure_every=every)
+        return E / N, s
+
+    with ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle_run)
+        lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, seed=seed)
+        out = lat.run([beta], n, measure_every=every)
+        eg = out["Ef"].cpu().numpy() / N
+        v = lat.spins.view(-1, 4)[:, :3].double()
+        norm_dev = torch.max(torch.abs(torch.linalg.norm(v, dim=1) - 1)).item()
+        eo, so = fut.result()
+    assert eg.shape == eo.shape == (n // every,)
+    assert norm_dev <= 1e-6  # the last sweep (2000) renormalised
+    assert np.max(np.abs(np.linalg.norm(so, axis=1) - 1)) < 1e-12
+    w = slice(50, None)  # sweeps 500 .. 2000
+    mg, sg = binned_mean(eg[w], 15)
+    mo, sob = binned_mean(eo[w], 15)
+    assert abs(mg - mo) <= 3 * math.sqrt(sg ** 2 + sob ** 2) + 1e-9, (mg, sg, mo, sob)
+    md, sd = binned_mean(eg[w] - eo[w], 15)
+    assert abs(md) <= 3 * sd + 1e-9, (md, sd)
+    assert abs(eg[0] - eo[0]) < 1e-3  # the first measurement, before the chains have drifted apart
 
 
 def test_heis_long_run_energy_matches_fp64_oracle():
@@ -225,9 +272,9 @@ def test_uneven_batch_full_size(ising_layout):
     """The full uneven batch (EA L = 8..32 with 512..32 realisations and
     24..48 temperatures in [0.8, 2.2], two sets; 2D Ising L = 256..4096, int8
     or coded) in one batched launch, measurement and exchange every sweep:
-    equal to plain per-handle runs, and sampled EA realisations equal to the
-    oracle."""
-    n = 3
+    equal to plain per-handle runs over the configuration's 50 sweeps, and
+    one sampled realisation of every EA size equal to the oracle."""
+    n = 50
 
     def build():
         side = []
@@ -254,17 +301,28 @@ def test_uneven_batch_full_size(ising_layout):
         for key in ser:
             assert torch.equal(ser[key], out[key]), (lb.L, key)
     for (lat, betas), (L, R, T), r in zip(batch, UNEVEN_EA, (511, 200, 64, 33, 31)):
-        if L not in (12, 32):
-            continue
-        seed = lat.seed
+        s, Es, Qs = _uneven_oracle(L, T, r, lat.seed, tuple(betas), n)
+        got = lat.unpack()[:, :, r].cpu().numpy()
+        assert np.array_equal(got, s), L
+        ser = sers[UNEVEN_EA.index((L, R, T))]
+        assert np.array_equal(ser["E"].view(n, 2, T, R)[:, :, :, r].cpu().numpy(), Es), L
+        assert np.array_equal(ser["Q"].view(n, T, R)[:, :, r].cpu().numpy(), Qs), L
+
+
+_UNEVEN_CACHE = {}
+
+
+def _uneven_oracle(L, T, r, seed, betas, n):
+    """Oracle tempering run of realisation r of an uneven-batch EA lattice
+    (cached: both Ising layouts of the test share the EA lattices)."""
+    key = (L, T, r, seed, betas, n)
+    if key not in _UNEVEN_CACHE:
         J = oracle.ea_couplings(3, L, r, seed)
         s = np.stack([np.stack([oracle.ising_init(3, L, seed, oracle.lattice_id(a, r >> 5, t), bit=r & 31)
                                 for t in range(T)]) for a in range(2)]).copy()
-        Es, Qs, _, _ = oracle.pt_run(3, L, s, betas, seed, r, r >> 5, 0, n, 1, J=J)
-        got = lat.unpack()[:, :, r].cpu().numpy()
-        assert np.array_equal(got, s), L
-        E = sers[UNEVEN_EA.index((L, R, T))]["E"].view(n, 2, T, R)[:, :, :, r].cpu().numpy()
-        assert np.array_equal(E, Es), L
+        Es, Qs, _, _ = oracle.omp_pt_run(3, L, s, list(betas), seed, r, r >> 5, 0, n, 1, J=J)
+        _UNEVEN_CACHE[key] = (s, Es, Qs)
+    return _UNEVEN_CACHE[key]
 
 
 def _tab_rng_e():

@@ -394,12 +394,32 @@ int spin_set_msc_width(spin_lattice *lat, int32_t width);
  * n_sweeps and the handle's sweep count to be multiples of hits (so must
  * spin_run's measure_every and pt_every).  Such handles cannot join a
  * batched launch.  tile and hits are ignored for SPIN_ORDER_CHECKERBOARD. */
+/* tile 0 leaves the tile edge to spin_tune, which must then run before the
+ * first sweep (a sweep with the edge still open returns SPIN_EINVAL). */
 typedef enum {
   SPIN_ORDER_CHECKERBOARD = 0,
   SPIN_ORDER_DCB = 1,
   SPIN_ORDER_DCB_SYMMETRIC = 2
 } spin_update_order;
 int spin_set_update_order(spin_lattice *lat, int32_t order, int32_t tile, int32_t hits);
+
+/* Autotuner for one handle (no counterpart in the paper's code; Sec. 3.4
+ * chooses its tile size by measuring): times trial calls of n_sweeps sweeps
+ * (1 .. 100000; a multiple of the hits in the double-checkerboard order)
+ * with the given couplings and HOST betas for every choice that leaves the
+ * handle's chain unchanged -- the kernel variants of the int8 ferromagnet
+ * (spin_set_variant: 0, 1, 3, 4 where supported) -- and, for a
+ * double-checkerboard handle whose tile edge was left open (tile 0), every
+ * supported tile edge (each gives its own chain, Sec. 3.2).  The fastest
+ * choice is set on the handle and cached per (model, layout, dim, L,
+ * lattices, order, hits, n_sweeps) for later handles of that shape.  Trials
+ * run on the handle's buffer after a backup copy (allocated and freed by
+ * this call); spins and counters are restored, so results do not depend on
+ * whether or when the tuner ran.  best_variant, best_tile (host, optional)
+ * receive the choice.  SPIN_EINVAL for bad arguments, SPIN_ENOMEM if the
+ * backup cannot be allocated. */
+int spin_tune(spin_lattice *lat, const void *couplings, const double *betas, int64_t n_sweeps,
+              int32_t *best_variant, int32_t *best_tile);
 
 const char *spin_strerror(int code);
 void spin_destroy(spin_lattice *lat);

@@ -73,6 +73,7 @@ def lib():
         L.spin_set_variant.argtypes = [p, i32]
         L.spin_set_update_order.argtypes = [p, i32, i32, i32]
         L.spin_set_msc_width.argtypes = [p, i32]
+        L.spin_tune.argtypes = [p, p, p, i64, p, p]
         L.spin_slab_phase.argtypes = [p, i32, i32, i32, C.c_double, u64, u32, u32, i32, p]
         L.spin_slab_measure.argtypes = [p, i32, i32, p, p, p]
         L.spin_strerror.argtypes = [C.c_int]
@@ -82,7 +83,7 @@ def lib():
         for name in ("spin_init", "spin_sweep", "spin_measure", "spin_pt_swap", "spin_run",
                      "spin_unpack_i8", "spin_pack_i8", "spin_rng_fill", "spin_rng_probe", "spin_pipe_probe", "spin_sync",
                      "spin_set_counters", "spin_set_variant", "spin_batch_run", "spin_batch_tune",
-                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width", "spin_slab_phase",
+                     "spin_set_batch_options", "spin_heis_measure_noalloc", "spin_set_update_order", "spin_set_msc_width", "spin_tune", "spin_slab_phase",
                      "spin_slab_measure", "spin_describe"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -293,6 +294,17 @@ def spin_batch_tune(items, n_sweeps, measure_every=0, pt_every=0, stream=None):
     _check(lib().spin_batch_tune(arr, len(items), n_sweeps, measure_every, pt_every, stream,
                                  C.byref(best)), "spin_batch_tune")
     return best.value
+
+
+def spin_tune(h, couplings, betas, n_sweeps):
+    """Runs the per-handle autotuner; returns (variant, tile) it chose."""
+    d, N, _ = _shape(h)
+    _need_betas(d, betas, "spin_tune")
+    _need_couplings(d, N, couplings, "spin_tune")
+    v, t = C.c_int32(0), C.c_int32(0)
+    _check(lib().spin_tune(h, _ptr(couplings), _host_doubles(betas), n_sweeps, C.byref(v), C.byref(t)),
+           "spin_tune")
+    return v.value, t.value
 
 
 def spin_set_batch_options(h, timeout_ns=0, ctas_per_sm=0, missing_arrivals=0):

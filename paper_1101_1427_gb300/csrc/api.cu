@@ -254,8 +254,8 @@ int spin_sweep(spin_lattice *h, const void *couplings, const double *betas, int6
   if (couplings && !aligned16(couplings)) return SPIN_EALIGN;
   if (h->sweeps_done + n_sweeps > (int64_t)0xFFFFFFFFll) return SPIN_EINVAL;
   if (h->order != SPIN_ORDER_CHECKERBOARD &&
-      (n_sweeps % h->order_hits != 0 || h->sweeps_done % h->order_hits != 0))
-    return SPIN_EINVAL;  // whole compound moves only
+      (n_sweeps % h->order_hits != 0 || h->sweeps_done % h->order_hits != 0 || h->order_tile == 0))
+    return SPIN_EINVAL;  // whole compound moves only, and a tile edge chosen
   int rc = upload_thresholds(h, betas);
   if (rc) return rc;
   cudaError_t e = h->order != SPIN_ORDER_CHECKERBOARD ? launch_sweeps_dcb(h, n_sweeps)
@@ -467,9 +467,15 @@ int spin_set_update_order(spin_lattice *h, int32_t order, int32_t tile, int32_t 
     h->order = order;
     return SPIN_OK;
   }
-  if ((order != SPIN_ORDER_DCB && order != SPIN_ORDER_DCB_SYMMETRIC) || hits < 1 || hits > (1 << 20) ||
-      !spin::dcb_supported(h, tile))
+  if ((order != SPIN_ORDER_DCB && order != SPIN_ORDER_DCB_SYMMETRIC) || hits < 1 || hits > (1 << 20))
     return SPIN_EINVAL;
+  if (tile == 0) {  // chosen later by spin_tune: some tile edge must fit
+    bool any = false;
+    for (int t : {8, 16, 32, 64, 128}) any = any || spin::dcb_supported(h, t);
+    if (!any) return SPIN_EINVAL;
+  } else if (!spin::dcb_supported(h, tile)) {
+    return SPIN_EINVAL;
+  }
   h->order = order;
   h->order_tile = tile;
   h->order_hits = hits;

@@ -1,0 +1,137 @@
+// Per-handle autotuner: kernel form and double-checkerboard tile edge.
+//
+// The int8 ferromagnet has several kernel forms that give the same chain
+// (colour phases, fused pass, resident lattice, coded path); which one is
+// fastest depends on the lattice size, the number of lattices and the call
+// length.  The double-checkerboard order (Sec. 3.2) takes a tile edge T whose
+// best value the paper finds by measurement (Sec. 3.4: tiles against
+// occupancy and shared memory); a handle set up with tile 0 lets this tuner
+// choose it.  Trials run on the handle's own buffer after a backup copy, and
+// the spins and counters are restored afterwards.
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace spin {
+bool dcb_supported(const spin_lattice *h, int tile);
+}
+
+namespace {
+
+using Key = std::tuple<int, int, int, int, int64_t, int, int, int64_t>;
+std::mutex g_tune_mutex;
+std::map<Key, std::pair<int, int>> g_tuned;  // shape -> (variant, tile)
+
+Key key_of(const spin_lattice *h, int64_t n_sweeps) {
+  return Key(h->d.model, h->d.layout, h->d.dim, h->g.L, h->n_lat, h->order, h->order_hits, n_sweeps);
+}
+
+int64_t spin_bytes(const spin_lattice *h) {
+  if (h->d.layout == SPIN_I8) return h->n_lat * h->g.N;
+  if (h->d.layout == SPIN_F32X4) return h->n_lat * h->g.N * 16;
+  if (h->d.model == SPIN_ISING) return h->n_lat * h->g.N / 8;
+  return (int64_t)h->g.n_sets * (h->g.n_real / 32) * h->g.n_temps * h->g.N * 4;
+}
+
+}  // namespace
+
+extern "C" int spin_tune(spin_lattice *h, const void *couplings, const double *betas, int64_t n_sweeps,
+                         int32_t *best_variant, int32_t *best_tile) {
+  NvtxRange nvtx_range("spin_tune");
+  if (!h || !betas || n_sweeps < 1 || n_sweeps > 100000) return SPIN_EINVAL;
+  const bool dcb = h->order != SPIN_ORDER_CHECKERBOARD;
+  if (dcb && n_sweeps % h->order_hits != 0) return SPIN_EINVAL;
+  const bool i8_ferro = h->d.model == SPIN_ISING && h->d.layout == SPIN_I8;
+  // candidate (variant, tile) pairs that give the handle's chain
+  std::vector<std::pair<int, int>> cand;
+  if (dcb) {
+    if (h->order_tile == 0) {
+      for (int t : {8, 16, 32, 64, 128})
+        if (spin::dcb_supported(h, t)) cand.emplace_back(h->variant, t);
+    } else {
+      cand.emplace_back(h->variant, h->order_tile);
+    }
+  } else if (i8_ferro) {
+    for (int v : {0, 1, 3, 4}) {
+      const int old = h->variant;
+      if (spin_set_variant(h, v) == SPIN_OK) cand.emplace_back(v, h->order_tile);
+      h->variant = old;
+    }
+  } else {
+    cand.emplace_back(h->variant, h->order_tile);
+  }
+  if (cand.empty()) return SPIN_EINVAL;
+  const Key key = key_of(h, n_sweeps);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      h->variant = it->second.first;
+      h->order_tile = it->second.second;
+      if (best_variant) *best_variant = h->variant;
+      if (best_tile) *best_tile = h->order_tile;
+      return SPIN_OK;
+    }
+  }
+  const int64_t bytes = spin_bytes(h);
+  void *backup = nullptr;
+  if (cudaMalloc(&backup, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SPIN_ENOMEM;
+  }
+  cudaStream_t st = h->stream;
+  cudaMemcpyAsync(backup, h->spins, (size_t)bytes, cudaMemcpyDeviceToDevice, st);
+  const int64_t sweeps0 = h->sweeps_done, pt0 = h->pt_steps_done;
+  const int variant0 = h->variant, tile0 = h->order_tile;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best_ms = 1e30f;
+  std::pair<int, int> best = cand[0];
+  int rc = SPIN_OK;
+  for (const auto &c : cand) {
+    h->variant = c.first;
+    h->order_tile = c.second;
+    float ms_c = 1e30f;
+    for (int rep = 0; rep < 3 && rc == SPIN_OK; ++rep) {  // first run warms up, best of the other two
+      cudaMemcpyAsync(h->spins, backup, (size_t)bytes, cudaMemcpyDeviceToDevice, st);
+      h->sweeps_done = sweeps0;
+      cudaEventRecord(a, st);
+      rc = spin_sweep(h, couplings, betas, n_sweeps, h->d.seed);
+      cudaEventRecord(b, st);
+      if (cudaEventSynchronize(b) != cudaSuccess) rc = SPIN_ECUDA;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0 && ms < ms_c) ms_c = ms;
+    }
+    if (rc != SPIN_OK) break;
+    if (ms_c < best_ms) {
+      best_ms = ms_c;
+      best = c;
+    }
+  }
+  cudaMemcpyAsync(h->spins, backup, (size_t)bytes, cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  cudaFree(backup);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->sweeps_done = sweeps0;
+  h->pt_steps_done = pt0;
+  if (rc != SPIN_OK) {
+    h->variant = variant0;
+    h->order_tile = tile0;
+    return rc;
+  }
+  h->variant = best.first;
+  h->order_tile = best.second;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = best;
+  }
+  if (best_variant) *best_variant = h->variant;
+  if (best_tile) *best_tile = h->order_tile;
+  return SPIN_OK;
+}

@@ -153,6 +153,11 @@ class Lattice:
     def set_msc_width(self, width):
         B.spin_set_msc_width(self.h, width)
 
+    def tune(self, betas, n_sweeps):
+        """Autotunes the kernel form (and an open double-checkerboard tile
+        edge) for calls of n_sweeps sweeps; returns (variant, tile)."""
+        return B.spin_tune(self.h, self.couplings, list(betas), n_sweeps)
+
     def set_update_order(self, order, tile=0, hits=1):
         B.spin_set_update_order(self.h, order, tile, hits)
 

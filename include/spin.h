@@ -29,9 +29,10 @@
  * Ownership: every spin, coupling and output buffer is allocated and owned
  * by the caller; the library only borrows device pointers while the work it
  * enqueued on the handle's stream runs.  A handle owns small workspaces
- * (threshold tables, reduction partials, an error word, and for the fused
- * 2D int8 sweep one lattice-sized ping-pong buffer), allocated by spin_init
- * and freed by spin_destroy.
+ * (threshold tables, reduction partials, an error word), allocated by
+ * spin_init, and one lattice-sized working buffer allocated by the first
+ * sweep call that needs it (the fused 2D int8 pass, the coded path of int8
+ * lattices, long fast-math Heisenberg calls); all are freed by spin_destroy.
  *
  * Errors: every entry point returns 0 (SPIN_OK) or a negative SPIN_E* code
  * and never throws.  Work is asynchronous on the handle's stream; kernel
@@ -329,8 +330,13 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * L % 256 == 0, L > 128); all four give identical results.  3D int8
  * ferromagnet: 0 = colour phases, 3 = resident (default for L % 8 == 0,
  * L <= 24), identical results.  Heisenberg: 0 = the full-accuracy FP32
- * library functions (default), 2 = hardware approximations of sin, cos and
- * exp (the paper's "fast_math" mode, Sec. 5), within the same tolerances. */
+ * library functions (default), 2 = the paper's "fast_math" mode (Sec. 5):
+ * rho = sqrt(1 - z^2) from the hardware reciprocal square root, sin and cos
+ * of the azimuth from the hardware sine and cosine on [-pi, pi), and the
+ * acceptance as u3 2^24 < 2^(24 - beta log2(e) dE) with the hardware exp2;
+ * within the same tolerances of the FP64 reference.  Calls of at least 4
+ * sweeps in variant 2 run on a colour-split copy of the lattices (same
+ * results bit for bit). */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
 /* Slab decomposition of one 2D int8 ferromagnet over several GPUs (the

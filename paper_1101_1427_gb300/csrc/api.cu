@@ -41,6 +41,12 @@ int upload_thresholds(spin_lattice *h, const double *betas) {
     memcpy(&bits, &bf, 4);
     tab[4 * t] = bits;
     for (int m = 1; m <= 3; ++m) tab[4 * t + m] = prob_threshold(exp(-betas[t] * (double)(4 * m)));
+    if (h->d.model == SPIN_HEISENBERG) {
+      // the fast-math acceptance tests u3 2^24 < 2^(24 - beta log2(e) dE)
+      const float bl = (float)(betas[t] * 1.4426950408889634074);
+      memcpy(&bits, &bl, 4);
+      tab[4 * t + 1] = bits;
+    }
   }
   cudaError_t e = cudaMemcpyAsync(h->d_thr, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return SPIN_ECUDA;
@@ -198,6 +204,7 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
   h->g.n_sets = desc->n_sets;
   h->g.ea = desc->model == SPIN_EA;
   h->g.fL = make_fastdiv((uint32_t)desc->L);
+  h->g.fHalfL = make_fastdiv((uint32_t)(desc->L / 2));
   h->g.fhalf = make_fastdiv((uint32_t)(h->g.N / 2));
   h->g.fquads = make_fastdiv((uint32_t)((h->g.N / 2 + 3) / 4));
   h->g.freal = make_fastdiv((uint32_t)desc->n_real);

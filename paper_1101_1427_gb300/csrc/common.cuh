@@ -150,6 +150,7 @@ struct Geom {
   int n_sets;
   int ea;          // realisation key is r >> 5
   FastDiv fL;      // division by L
+  FastDiv fHalfL;  // division by L / 2
   FastDiv fhalf;   // division by N / 2
   FastDiv fquads;  // division by (N / 2 + 3) / 4
   FastDiv freal;   // division by n_real

@@ -24,6 +24,38 @@ __device__ __forceinline__ float4 unit_vector(uint32_t w1, uint32_t w2) {
   return make_float4(rho * cs, rho * sn, z, 0.0f);
 }
 
+// The Metropolis step of one site (Sec. 5) from its spin si, the sum h of
+// its neighbours and its Philox call w: proposal n from words 0 and 1,
+// acceptance from word 2, dE = -(n - si) . h; returns whether n is taken.
+// kFast = false: the library's full-accuracy FP32 functions (sqrtf, sincospif,
+// expf).  kFast = true, the paper's fast-math mode: rho = sqrt(1 - z^2) as
+// s2 rsqrt(s2), sin and cos of phi = 2 pi u2 from the hardware sin and cos of
+// phi - pi in [-pi, pi) (negated), and u3 < exp(-beta dE) tested as
+// (w2 >> 8) < 2^(24 - beta log2(e) dE) with the hardware exp2 (beta_l2e =
+// beta log2(e) from the host).  Every kernel of one variant calls this, so a
+// chain does not depend on which kernel or call length ran it.
+template <bool kFast>
+__device__ __forceinline__ bool heis_step(const float4 &si, float hx, float hy, float hz, const uint4 &w,
+                                          float beta, float beta_l2e, float4 &n) {
+  if (!kFast) {
+    n = unit_vector<false>(w.x, w.y);
+    const float u3 = uniform24(w.z);
+    const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
+    return dE <= 0.0f || u3 < expf(-beta * dE);
+  }
+  const float z = fmaf(__uint2float_rn(w.x >> 8), 1.1920928955078125e-7f, -1.0f);  // 2 u1 - 1
+  const float s2 = fmaf(-z, z, 1.0f);
+  const float rho = s2 * rsqrtf(fmaxf(s2, 1e-30f));
+  const float xa = fmaf(__uint2float_rn(w.y >> 8), 3.7450702663161573e-7f, -3.14159265358979f);
+  float sn, cs;
+  __sincosf(xa, &sn, &cs);
+  n = make_float4(-rho * cs, -rho * sn, z, 0.0f);
+  const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
+  float p;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(fmaf(-beta_l2e, dE, 24.0f)));
+  return dE <= 0.0f || __uint2float_rn(w.z >> 8) < p;
+}
+
 __global__ void heis_init_kernel(float4 *__restrict__ s, Geom g, int64_t n_lat, RoundKeys rk) {
   const int64_t total = n_lat * g.N;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
@@ -55,16 +87,18 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
   griddep_release();
   const uint32_t L = (uint32_t)g.L, LL = L * L, N = (uint32_t)g.N, half = N / 2;
   const bool single = g.n_real == 1 && g.n_temps == 1 && g.n_sets == 1;
-  const float beta0 = __uint_as_float(__ldg(thr));
+  const float beta0 = __uint_as_float(__ldg(thr)), bl0 = __uint_as_float(__ldg(thr + 1));
   const uint32_t wctr = ctr_w(TAG_HEIS, (uint32_t)colour, 0);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     uint32_t lat = 0, j = k, lid = 0;
-    float beta = beta0;
+    float beta = beta0, bl = bl0;
     if (!single) {
       lat = fdiv(k, g.fhalf);
       j = k - lat * half;
       lid = lattice_id32(g, lat);
-      beta = __uint_as_float(__ldg(thr + 4 * slot_of32(g, lat)));
+      const uint32_t slot = slot_of32(g, lat);
+      beta = __uint_as_float(__ldg(thr + 4 * slot));
+      bl = __uint_as_float(__ldg(thr + 4 * slot + 1));
     }
     float4 *sl = s + (size_t)lat * N;
     const Site st = site_of(g, j, colour);
@@ -84,11 +118,88 @@ __global__ void __launch_bounds__(256) heis_phase_kernel(float4 *__restrict__ s,
     const float hx = kDim == 3 ? a.x + b.x + c.x + d.x + e.x + f.x : a.x + b.x + c.x + d.x;
     const float hy = kDim == 3 ? a.y + b.y + c.y + d.y + e.y + f.y : a.y + b.y + c.y + d.y;
     const float hz = kDim == 3 ? a.z + b.z + c.z + d.z + e.z + f.z : a.z + b.z + c.z + d.z;
-    const float4 n = unit_vector<kFast>(w.x, w.y);
-    const float u3 = uniform24(w.z);
-    const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
-    const float boltz = kFast ? __expf(-beta * dE) : expf(-beta * dE);
-    if (dE <= 0.0f || u3 < boltz) sl[i] = n;
+    float4 n;
+    if (heis_step<kFast>(si, hx, hy, hz, w, beta, bl, n)) sl[i] = n;
+  }
+}
+
+// Colour-split working copy of the lattices for the long calls: per lattice
+// [2 colours][L^(dim-1) rows][L/2], the site (x, row) of colour c at
+// c N/2 + row L/2 + (x >> 1), i.e. at c N/2 + (i >> 1).  A warp's 32
+// consecutive sites of one colour then read 32 consecutive float4 of the
+// other colour for each neighbour direction instead of every other float4
+// of two cache lines.
+__global__ void heis_to_split_kernel(const float4 *__restrict__ s, float4 *__restrict__ S, Geom g, int64_t total) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / g.N, i = k - lat * g.N;
+    S[lat * g.N + (int64_t)colour_of(g, (uint32_t)i) * (g.N / 2) + (i >> 1)] = s[k];
+  }
+}
+
+__global__ void heis_from_split_kernel(const float4 *__restrict__ S, float4 *__restrict__ s, Geom g, int64_t total) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lat = k / g.N, i = k - lat * g.N;
+    s[k] = S[lat * g.N + (int64_t)colour_of(g, (uint32_t)i) * (g.N / 2) + (i >> 1)];
+  }
+}
+
+// One colour phase on the colour-split copy: thread per colour site j (the
+// Philox index, j = row L/2 + kx); the neighbours x +- 1 are the other
+// colour's entries kx and kx +- 1 of the same row (which one is x + 1
+// depends on the row's parity p), y +- 1 and z +- 1 the entries kx of the
+// neighbouring rows.  Same arithmetic as heis_phase_kernel, site for site.
+template <bool kFast, int kDim>
+__global__ void __launch_bounds__(256) heis_split_phase_kernel(float4 *__restrict__ S, Geom g, uint32_t total,
+                                                               const uint32_t *__restrict__ thr, RoundKeys rk,
+                                                               uint32_t sweep, int colour) {
+  griddep_wait();
+  griddep_release();
+  const uint32_t L = (uint32_t)g.L, H = L >> 1, half = (uint32_t)(g.N / 2);
+  const bool single = g.n_real == 1 && g.n_temps == 1 && g.n_sets == 1;
+  const float beta0 = __uint_as_float(__ldg(thr)), bl0 = __uint_as_float(__ldg(thr + 1));
+  const uint32_t wctr = ctr_w(TAG_HEIS, (uint32_t)colour, 0);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    uint32_t lat = 0, j = k, lid = 0;
+    float beta = beta0, bl = bl0;
+    if (!single) {
+      lat = fdiv(k, g.fhalf);
+      j = k - lat * half;
+      lid = lattice_id32(g, lat);
+      const uint32_t slot = slot_of32(g, lat);
+      beta = __uint_as_float(__ldg(thr + 4 * slot));
+      bl = __uint_as_float(__ldg(thr + 4 * slot + 1));
+    }
+    const uint32_t row = fdiv(j, g.fHalfL), kx = j - row * H;
+    uint32_t y = row, z = 0;
+    if (kDim == 3) {
+      z = fdiv(row, g.fL);
+      y = row - z * L;
+    }
+    const uint32_t p = (colour + y + z) & 1u;
+    float4 *own = S + (size_t)lat * g.N + (colour ? half : 0) + j;
+    const float4 *O = S + (size_t)lat * g.N + (colour ? 0 : half) + j;
+    const int dr = p ? (kx == H - 1 ? 1 - (int)H : 1) : (kx == 0 ? (int)H - 1 : -1);
+    const int dyp = y == L - 1 ? -(int)((L - 1) * H) : (int)H, dym = y == 0 ? (int)((L - 1) * H) : -(int)H;
+    const float4 m = O[0], sh = O[dr];
+    const float4 a = p ? sh : m, b = p ? m : sh;  // x + 1, x - 1
+    const float4 c = O[dyp], d = O[dym];
+    float hx, hy, hz;
+    if (kDim == 3) {
+      const int LH = (int)(L * H);
+      const int dzp = z == L - 1 ? -(int)((L - 1) * L * H) : LH, dzm = z == 0 ? (int)((L - 1) * L * H) : -LH;
+      const float4 e = O[dzp], f = O[dzm];
+      hx = a.x + b.x + c.x + d.x + e.x + f.x;
+      hy = a.y + b.y + c.y + d.y + e.y + f.y;
+      hz = a.z + b.z + c.z + d.z + e.z + f.z;
+    } else {
+      hx = a.x + b.x + c.x + d.x;
+      hy = a.y + b.y + c.y + d.y;
+      hz = a.z + b.z + c.z + d.z;
+    }
+    const float4 si = *own;
+    const uint4 w = philox(make_uint4(j, sweep, lid, wctr), rk);
+    float4 n;
+    if (heis_step<kFast>(si, hx, hy, hz, w, beta, bl, n)) *own = n;
   }
 }
 
@@ -127,7 +238,7 @@ __global__ void __launch_bounds__(256) heis_dcb2_kernel(float4 *__restrict__ s, 
     }
   __syncthreads();
   const uint32_t slot = slot_of32(g, lat), lid = lattice_id32(g, lat);
-  const float beta = __uint_as_float(__ldg(thr + 4 * slot));
+  const float beta = __uint_as_float(__ldg(thr + 4 * slot)), bl = __uint_as_float(__ldg(thr + 4 * slot + 1));
   PhiloxX1 pre[kPer][2];
   if (active)
 #pragma unroll
@@ -155,11 +266,8 @@ __global__ void __launch_bounds__(256) heis_dcb2_kernel(float4 *__restrict__ s, 
           const float hx = a.x + b.x + cc.x + d.x;
           const float hy = a.y + b.y + cc.y + d.y;
           const float hz = a.z + b.z + cc.z + d.z;
-          const float4 n = unit_vector<kFast>(w.x, w.y);
-          const float u3 = uniform24(w.z);
-          const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
-          const float boltz = kFast ? __expf(-beta * dE) : expf(-beta * dE);
-          if (dE <= 0.0f || u3 < boltz) sw[at] = n;
+          float4 n;
+          if (heis_step<kFast>(si, hx, hy, hz, w, beta, bl, n)) sw[at] = n;
         }
       __syncthreads();
     }
@@ -218,7 +326,53 @@ cudaError_t launch_init_heis(spin_lattice *h) {
   return cudaGetLastError();
 }
 
+namespace {
+// Calls of at least this many sweeps in the fast-math variant run on the
+// colour-split copy (the two conversions cost about one sweep's memory
+// traffic).  Measured on the L = 128 and 256 lattices: +6-7 % for the
+// fast-math form, none for the full-accuracy form, which stays on the
+// row-major kernel.
+constexpr int64_t kSplitMinSweeps = 4;
+
+cudaError_t sweeps_heis_split(spin_lattice *h, int64_t n_sweeps) {
+  const int64_t total = h->n_lat * h->g.N;
+  const size_t bytes = (size_t)total * 16;
+  if (!h->d_pingpong || h->pingpong_bytes < bytes) {
+    if (h->d_pingpong) cudaFree(h->d_pingpong);
+    h->d_pingpong = nullptr;
+    cudaError_t e = cudaMalloc(&h->d_pingpong, bytes);
+    if (e != cudaSuccess) return e;
+    h->pingpong_bytes = bytes;
+  }
+  float4 *S = (float4 *)h->d_pingpong;
+  heis_to_split_kernel<<<capped_grid(total), 256, 0, h->stream>>>((const float4 *)h->spins, S, h->g, total);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const RoundKeys rk = make_round_keys(h->d.seed);
+  const uint32_t half = (uint32_t)(total / 2);
+  auto *kern = h->g.dim == 3 ? (h->variant == 2 ? heis_split_phase_kernel<true, 3> : heis_split_phase_kernel<false, 3>)
+                             : (h->variant == 2 ? heis_split_phase_kernel<true, 2> : heis_split_phase_kernel<false, 2>);
+  for (int64_t k = 0; k < n_sweeps; ++k) {
+    const uint32_t sweep = (uint32_t)(h->sweeps_done + k);
+    for (int colour = 0; colour < 2; ++colour) {
+      e = launch_dependent(kern, dim3(capped_grid(half)), dim3(256), 0, h->stream, S, h->g, half, h->d_thr, rk,
+                           sweep, colour);
+      if (e != cudaSuccess) return e;
+    }
+    if ((sweep + 1u) % 100u == 0u) {  // renormalisation is site-wise: the layout does not matter
+      heis_renorm_kernel<<<capped_grid(total), 256, 0, h->stream>>>(S, total);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  heis_from_split_kernel<<<capped_grid(total), 256, 0, h->stream>>>(S, (float4 *)h->spins, h->g, total);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
+  if (h->variant == 2 && n_sweeps >= kSplitMinSweeps && h->n_lat * h->g.N < ((int64_t)1 << 32))
+    return sweeps_heis_split(h, n_sweeps);
   const RoundKeys rk = make_round_keys(h->d.seed);
   const uint32_t half = (uint32_t)(h->n_lat * (h->g.N / 2));
   for (int64_t k = 0; k < n_sweeps; ++k) {

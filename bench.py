@@ -56,15 +56,16 @@ WIDE_MULS_PER_CLK_PER_SM = 32
 #    pipe (64 three-input logic operations per clock per SM, measured 63.7):
 #    sweep 28 = 5 Philox XORs (a quarter call) + 3 threshold compares + 6
 #    bond terms s ^ s_j ^ J + 8 for the bit-sliced 6-input count + 5 for the
-#    flip mask + 1 to apply it; measuring E, M and Q every sweep adds 12
-#    (3 bond terms and carry-save counting for E, M, half of Q per set) and
-#    the bitwise exchange about 1 (3 operations per word of an accepted
+#    flip mask + 1 to apply it; measuring E and Q every sweep (the
+#    tempering run of the configuration) adds 10 (3 bond terms and
+#    carry-save counting for E, half of the overlap's XOR and count per set)
+#    and the bitwise exchange about 1 (3 operations per word of an accepted
 #    pair, half the pairs tried per sweep).  Its Philox multiplies (5 per 32
 #    flips) bind far later.
 HEIS_WIDE_MULS_PER_FLIP = 20
 ALU_OPS_PER_CLK_PER_SM = 64
 EA_SWEEP_ALU_PER_WORD = 28
-EA_PT_ALU_PER_WORD = 28 + 12 + 1
+EA_PT_ALU_PER_WORD = 28 + 10 + 1
 
 # DRAM bytes of one phase launch of the coded sweep over the three lattices
 # (mean of two launches captured with ncu, summarised in profiles/), valid
@@ -266,8 +267,9 @@ def _events(torch):
 def side_configs(torch, sp, B, stream):
     """Short measurements of the other hot-path configurations (context for
     the headline): 3D Heisenberg L=128 and 2D L=4096 (FP32), and 3D EA L=16 with 1024
-    realisations x 32 slots x 2 sets, exchange and measurement every sweep,
-    in the per-handle multi-launch form and in the batched persistent form;
+    realisations x 32 slots x 2 sets, exchange and overlap every sweep (and
+    then E, M and Q), in the per-handle multi-launch form and in the batched
+    persistent form;
     then the uneven batch in both forms, the 2D tempering benchmark, the
     double checkerboard and the 3D ferromagnet."""
     import numpy as np
@@ -317,22 +319,33 @@ def side_configs(torch, sp, B, stream):
     flips = n * 16 ** 3 * 1024 * 32 * 2
     ser = ea.series_buffers(n)
     acc = torch.zeros(64, dtype=torch.int64, device=stream.device)
-    B.spin_run(ea.h, ea.couplings, betas, 2, 1, 1, ser["E"], ser["M"], ser["Q"], None, None, acc)
-    a, b = _events(torch)
-    a.record(stream)
-    B.spin_run(ea.h, ea.couplings, betas, n, 1, 1, ser["E"], ser["M"], ser["Q"], None, None, acc)
-    b.record(stream)
-    torch.cuda.synchronize()
-    out["ea_L16_pt_plain_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
-    item = [ea.batch_item(betas, ser, acc)]
-    B.spin_batch_run(item, 2, 1, 1, stream.cuda_stream)
-    a, b = _events(torch)
-    a.record(stream)
-    B.spin_batch_run(item, n, 1, 1, stream.cuda_stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ea.sync()
-    out["ea_L16_pt_batched_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
+    # the configuration's tempering run: exchange and overlap every sweep (the
+    # exchange needs the energies, which are therefore recorded too); then
+    # the same with the magnetisation measured as well
+    for suffix, M in (("", None), ("_with_M", ser["M"])):
+        B.spin_run(ea.h, ea.couplings, betas, 2, 1, 1, ser["E"], M, ser["Q"], None, None, acc)
+        best = 1e30
+        for _ in range(2):
+            a, b = _events(torch)
+            a.record(stream)
+            B.spin_run(ea.h, ea.couplings, betas, n, 1, 1, ser["E"], M, ser["Q"], None, None, acc)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out[f"ea_L16_pt{suffix}_plain_flips_per_ns"] = flips / (best * 1e6)
+        item = [{"lat": ea.h, "couplings": ea.couplings, "betas": betas, "E": ser["E"], "M": M, "Q": ser["Q"],
+                 "accepted": acc}]
+        B.spin_batch_run(item, 2, 1, 1, stream.cuda_stream)
+        best = 1e30
+        for _ in range(2):
+            a, b = _events(torch)
+            a.record(stream)
+            B.spin_batch_run(item, n, 1, 1, stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        ea.sync()
+        out[f"ea_L16_pt{suffix}_batched_flips_per_ns"] = flips / (best * 1e6)
     # the same lattices with 64 realisations per shared uniform (Sec. 6, w = 64)
     ea.set_msc_width(64)
     for name, me in (("ea_L16_w64_sweep_flips_per_ns", 0), ("ea_L16_w64_pt_plain_flips_per_ns", 1)):
@@ -803,14 +816,17 @@ def run_case(name):
     from paper_1101_1427_gb300 import _binding as B
     stream = torch.cuda.current_stream()
     a, b = _events(torch)
-    if name in ("msc2d", "fused2d"):
+    if name in ("msc2d", "fused2d", "i8coded"):
+        # fused2d: two-sweep calls of the int8 lattices (the fused pass);
+        # i8coded: four-sweep calls (pack, coded sweeps, unpack)
         layout = B.SPIN_MSC1 if name == "msc2d" else B.SPIN_I8
+        n = 4 if name == "i8coded" else 2
         lat = sp.Lattice(B.SPIN_ISING, 2, L, layout, n_temps=3, seed=1)
-        B.spin_sweep(lat.h, None, BETAS, 2, lat.seed)
+        B.spin_sweep(lat.h, None, BETAS, n, lat.seed)
         a.record(stream)
-        B.spin_sweep(lat.h, None, BETAS, 2, lat.seed)
+        B.spin_sweep(lat.h, None, BETAS, n, lat.seed)
         b.record(stream)
-        flips = 2 * 3 * L * L
+        flips = n * 3 * L * L
     elif name in ("ea", "ea_batch", "ea_measure"):
         betas = list(1.0 / np.geomspace(0.9, 2.0, 32))
         lat = sp.Lattice(B.SPIN_EA, 3, 16, B.SPIN_MSC1, n_real=1024, n_temps=32, n_sets=2, seed=1)
@@ -853,13 +869,19 @@ def run_case(name):
     elif name == "uneven":
         print(json.dumps({"case": name, **uneven_batch(torch, sp, B, stream, n=8)}), flush=True)
         return
-    elif name == "heis":
+    elif name in ("heis", "heis_fast"):
+        # heis: the full-accuracy variant (row-major kernel); heis_fast: the
+        # fast-math variant in four-sweep calls (colour-split copy)
         lat = sp.Lattice(B.SPIN_HEISENBERG, 3, 128, B.SPIN_F32X4, seed=1)
-        B.spin_sweep(lat.h, None, [0.693], 2, lat.seed)
+        n = 2
+        if name == "heis_fast":
+            lat.set_variant(2)
+            n = 4
+        B.spin_sweep(lat.h, None, [0.693], n, lat.seed)
         a.record(stream)
-        B.spin_sweep(lat.h, None, [0.693], 2, lat.seed)
+        B.spin_sweep(lat.h, None, [0.693], n, lat.seed)
         b.record(stream)
-        flips = 2 * 128 ** 3
+        flips = n * 128 ** 3
     elif name == "pipes":
         print(json.dumps({"case": name, **pipe_rates(torch, B, stream)}), flush=True)
         return
@@ -894,7 +916,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-side", action="store_true", help="skip the side configurations")
     ap.add_argument("--case", default=None,
-                    help="run one kernel family briefly (msc2d, fused2d, ea, ea_batch, ea_measure, ising_pt_sizes, heis, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
+                    help="run one kernel family briefly (msc2d, fused2d, i8coded, ea, ea_batch, ea_measure, ising_pt_sizes, heis, "
+                         "heis_fast, heis_dcb, rng, pipes, uneven, ising_pt, dcb, ising3d)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -68,11 +68,10 @@ EA_SWEEP_ALU_PER_WORD = 28
 EA_PT_ALU_PER_WORD = 28 + 10 + 1
 
 # DRAM bytes of one phase launch of the coded sweep over the three lattices
-# (mean of two launches captured with ncu, summarised in profiles/), valid
-# while the kernel's sources hash to KERNEL_TRAFFIC_SRC_SHA; otherwise
-# reported as null.
-KERNEL_TRAFFIC_BYTES = (100_703_232 + 11_326_464 + 100_742_912 + 7_770_880) // 2
-KERNEL_TRAFFIC_SRC_SHA = "206e08c055b635ba"
+# (one launch captured with ncu, summarised in profiles/), valid while the
+# kernel's sources hash to KERNEL_TRAFFIC_SRC_SHA; otherwise reported as null.
+KERNEL_TRAFFIC_BYTES = 100_702_464 + 10_737_664
+KERNEL_TRAFFIC_SRC_SHA = "8d91632b9bd5988a"
 
 
 def kernel_sha():

@@ -287,7 +287,7 @@ def side_configs(torch, sp, B, stream):
         torch.cuda.synchronize()
         out[name + "_flips_per_ns"] = 100 * 128 ** 3 / (a.elapsed_time(b) * 1e6)
     lat.close()
-    # the paper's own Heisenberg study is 2D, L = 4096 (Sec. 5)
+    # the paper's own Heisenberg study is 2D, L = 4096 (Sec. 4)
     lat = sp.Lattice(B.SPIN_HEISENBERG, 2, 4096, B.SPIN_F32X4, seed=13)
     B.spin_sweep(lat.h, None, [1.1], 50, lat.seed)
     for variant, name in ((0, "heisenberg2d_L4096_fp32"), (2, "heisenberg2d_L4096_fp32_fast")):
@@ -345,7 +345,7 @@ def side_configs(torch, sp, B, stream):
             best = min(best, a.elapsed_time(b))
         ea.sync()
         out[f"ea_L16_pt{suffix}_batched_flips_per_ns"] = flips / (best * 1e6)
-    # the same lattices with 64 realisations per shared uniform (Sec. 6, w = 64)
+    # the same lattices with 64 realisations per shared uniform (Sec. 5, w = 64)
     ea.set_msc_width(64)
     for name, me in (("ea_L16_w64_sweep_flips_per_ns", 0), ("ea_L16_w64_pt_plain_flips_per_ns", 1)):
         B.spin_run(ea.h, ea.couplings, betas, 2, me, me, ser["E"] if me else None, ser["M"] if me else None,
@@ -365,7 +365,7 @@ def side_configs(torch, sp, B, stream):
     torch.cuda.synchronize()
     out["ea_L16_w32_sweep_flips_per_ns"] = flips / (a.elapsed_time(b) * 1e6)
     ea.close()
-    # the paper's own multi-spin-coding benchmark is the 2D glass, L = 16 (Sec. 6):
+    # the paper's own multi-spin-coding benchmark is the 2D glass, L = 16 (Sec. 5):
     # 16384 realisations x 32 temperatures x 2 sets (2^28 spins), sweeps only
     ea2 = sp.Lattice(B.SPIN_EA, 2, 16, B.SPIN_MSC1, n_real=16384, n_temps=32, n_sets=2, seed=14)
     flips2 = n * 16 ** 2 * 16384 * 32 * 2
@@ -388,7 +388,7 @@ def side_configs(torch, sp, B, stream):
 
 
 def ising3d(torch, sp, B, stream):
-    """3D Ising ferromagnet (Sec. 4): one int8 lattice of L = 512 (2^27 sites,
+    """3D Ising ferromagnet (Sec. 3.6): one int8 lattice of L = 512 (2^27 sites,
     larger than L2) at the critical coupling, plain red-black sweeps and the
     double checkerboard with cubic tiles (T = 8, 16) and k = 100 hits."""
     out = {}
@@ -452,7 +452,7 @@ def dcb(torch, sp, B, stream):
 
 def ising_pt_sizes(torch, sp, B, stream):
     """The tempering benchmark over lattice sizes (the paper plots its flip
-    time against L, Sec. 7): 20 int8 replicas, beta in [0.1, 0.15], one
+    time against L, Sec. 6): 20 int8 replicas, beta in [0.1, 0.15], one
     exchange per 100 sweeps, with the resident kernel (L <= 128) and the
     fused pass (L >= 32)."""
     import numpy as np
@@ -500,7 +500,7 @@ def ising2d_small(torch, sp, B, stream):
 
 
 def ising_pt(torch, sp, B, stream):
-    """The paper's tempering benchmark for the 2D ferromagnet (Sec. 7): 20
+    """The paper's tempering benchmark for the 2D ferromagnet (Sec. 6): 20
     int8 replicas at equally spaced beta in [0.1, 0.15], one exchange step
     per 100 (and per 10) sweeps; flips/ns counts spin flips of all replicas.
     Each size runs its default kernel: resident (whole lattice in one CTA)

@@ -5,10 +5,10 @@
  * "Performance potential for simulating spin models on GPU"
  * (arXiv:1101.1427): checkerboard (red-black) Metropolis sweeps for the
  * 2D/3D Ising ferromagnet (Eq. ising_hamiltonian, Eq. metropolis, Sec. 3.2),
- * the +-J Edwards-Anderson spin glass (Eq. spinglass_hamiltonian, Sec. 6,
+ * the +-J Edwards-Anderson spin glass (Eq. spinglass_hamiltonian, Sec. 5,
  * including asynchronous multi-spin coding), the 3D Heisenberg model
- * (Eq. On_hamiltonian, Sec. 5) and the replica-exchange step of parallel
- * tempering (Eq. parallel_tempering, Sec. 7), plus the energy,
+ * (Eq. On_hamiltonian, Sec. 4) and the replica-exchange step of parallel
+ * tempering (Eq. parallel_tempering, Sec. 6), plus the energy,
  * magnetisation and overlap reductions.
  *
  * Conventions (shared with the test oracle, which implements them
@@ -60,7 +60,7 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *  SPIN_I8     int8 +-1, [n_sets][n_temps][n_real][L^dim].  Ising (2D, 3D) and
  *              EA (3D, one spin per byte: the per-realisation form).
  *  SPIN_MSC1   1 bit per spin, bit set <=> s = -1, uint32 words.
- *              EA (2D or 3D, asynchronous coding, Sec. 6): word-lattices
+ *              EA (2D or 3D, asynchronous coding, Sec. 5): word-lattices
  *              [n_sets][n_real/32][n_temps], each stored colour-split as
  *              [2 colours][L^dim/2] (site i of colour c at c L^dim/2 + (i >> 1));
  *              bit b of a word is realisation 32 g + b.
@@ -69,7 +69,7 @@ typedef enum { SPIN_ISING = 0, SPIN_EA = 1, SPIN_HEISENBERG = 2 } spin_model;
  *              x = 2k + ((c + y) & 1) are grouped in blocks of 128 k's, and
  *              k = 128 B + 4 l + q is bit l of word 4 B + q.  Needs L % 256 == 0.
  *  SPIN_F32X4  float4 (x, y, z, 0) unit vectors, [n_sets][n_temps][n_real][L^dim]
- *              (Heisenberg, 2D as in Sec. 5 or 3D).
+ *              (Heisenberg, 2D as in Sec. 4 or 3D).
  * Couplings (EA only; NULL for the ferromagnet, J = 1):
  *  SPIN_I8     int8 +-1, [n_real][dim][L^dim]: bond (i, i + e_d).
  *  SPIN_MSC1   uint32 [n_real/32][dim][2 colours][L^dim/2] (bond (i, i + e_d)
@@ -116,8 +116,8 @@ int spin_init(spin_lattice **out, const spin_desc *desc, void *spins, void *coup
 int spin_sweep(spin_lattice *lat, const void *couplings, const double *betas,
                int64_t n_sweeps, uint64_t seed);
 
-/* Reductions over the current state (Sec. 4, measurement by binary-tree
- * reduction; double accumulation for continuous spins, Sec. 5).  Device
+/* Reductions over the current state (Sec. 3.5, measurement by binary-tree
+ * reduction; double accumulation for continuous spins, Sec. 4).  Device
  * outputs, NULL to skip; lat index = (a * n_temps + t) * n_real + r:
  *   E   int64 [n_lat]  E = -sum_<ij> J_ij s_i s_j        (Ising, EA)
  *   M   int64 [n_lat]  M = sum_i s_i                     (Ising, EA)
@@ -137,7 +137,7 @@ int spin_measure(spin_lattice *lat, const void *couplings, int64_t *E, int64_t *
  * NULL) is incremented per accepted pair (t, t+1) at index t.  labels
  * (device int32 [n_sets][n_temps][n_real], indexed like the lattices, may be
  * NULL) names the configuration each lattice holds: an accepted exchange
- * moves the two labels with their configurations.  Sec. 7 notes that
+ * moves the two labels with their configurations.  Sec. 6 notes that
  * exchanging temperatures instead of configurations is cheaper on a CPU;
  * the labels give a caller of this configuration-exchange form the same
  * information -- starting from labels[lat(a, t, r)] = t, the slot of every
@@ -176,7 +176,7 @@ typedef struct {
 } spin_batch_item;
 
 /* Batched persistent launch (the paper maps independent replicas and
- * tempering copies to thread blocks, Sec. 6-7): n_sweeps sweeps of every
+ * tempering copies to thread blocks, Sec. 5-6): n_sweeps sweeps of every
  * lattice of every handle, with the measurements and exchange steps of
  * spin_run, in ONE cooperative kernel launch on `stream`.  Results
  * (lattices, series, exchange decisions) are identical to calling spin_run
@@ -322,15 +322,15 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * with L % 256 != 0), 3 = resident: one CTA per lattice holds the whole
  * lattice in shared memory for all sweeps of a call and measures E and M
  * itself (default for L % 8 == 0, L <= 128; the paper's tempering code
- * likewise maps replicas to thread blocks, Sec. 7), 4 = coded: a call of at
+ * likewise maps replicas to thread blocks, Sec. 6), 4 = coded: a call of at
  * least 4 sweeps packs the lattices into a handle-owned 1-bit buffer
  * (L^2 / 8 bytes per lattice, allocated on first use, kept until
- * spin_destroy), runs the synchronous multi-spin-coded sweep (Sec. 6) and
+ * spin_destroy), runs the synchronous multi-spin-coded sweep (Sec. 5) and
  * unpacks them, shorter calls take the fused pass (default for
  * L % 256 == 0, L > 128); all four give identical results.  3D int8
  * ferromagnet: 0 = colour phases, 3 = resident (default for L % 8 == 0,
  * L <= 24), identical results.  Heisenberg: 0 = the full-accuracy FP32
- * library functions (default), 2 = the paper's "fast_math" mode (Sec. 5):
+ * library functions (default), 2 = the paper's "fast_math" mode (Sec. 4):
  * rho = sqrt(1 - z^2) from the hardware reciprocal square root, sin and cos
  * of the azimuth from the hardware sine and cosine on [-pi, pi), and the
  * acceptance as u3 2^24 < 2^(24 - beta log2(e) dE) with the hardware exp2;
@@ -365,7 +365,7 @@ int spin_slab_phase(int8_t *slab, int32_t L, int32_t y0, int32_t rows, double be
 int spin_slab_measure(const int8_t *slab, int32_t L, int32_t rows, int64_t *E, int64_t *M, void *stream);
 
 /* Realisations that share one uniform per site in the coded EA layout
- * (Sec. 6, footnote: the same random number serves all w spins of a word):
+ * (Sec. 5, footnote: the same random number serves all w spins of a word):
  * 32 (one word, the default) or 64 (the paper's w = 64: realisation groups
  * 2q and 2q + 1 draw the words of group q, i.e. lattice_id(a, r >> 6, t);
  * the storage stays 32-bit, since on this GPU a 64-bit logical operation is
@@ -392,9 +392,9 @@ int spin_set_msc_width(spin_lattice *lat, int32_t width);
  *                           the compound order of Sec. 3.4 that satisfies
  *                           detailed balance.
  * The double-checkerboard orders take Ising ferromagnets in the int8
- * layout: 2D with tile in {8, 16, 32, 64, 128}, or 3D (Sec. 4: tile^3
+ * layout: 2D with tile in {8, 16, 32, 64, 128}, or 3D (Sec. 3.6: tile^3
  * cubes, coarse colour (x / tile + y / tile + z / tile) mod 2) with tile in
- * {8, 16}; and the 2D Heisenberg model (Sec. 5) with tile in {8, 16, 32},
+ * {8, 16}; and the 2D Heisenberg model (Sec. 4) with tile in {8, 16, 32},
  * renormalised after every compound move that passes a sweep count
  * divisible by 100; tile divides L with L / tile even, and hits >= 1; spin_sweep then counts sweeps as updates per site and needs
  * n_sweeps and the handle's sweep count to be multiples of hits (so must
@@ -409,7 +409,7 @@ typedef enum {
 } spin_update_order;
 int spin_set_update_order(spin_lattice *lat, int32_t order, int32_t tile, int32_t hits);
 
-/* Autotuner for one handle (no counterpart in the paper's code; Sec. 3.4
+/* Autotuner for one handle (no counterpart in the paper's code; Sec. 3.5
  * chooses its tile size by measuring): times trial calls of n_sweeps sweeps
  * (1 .. 100000; a multiple of the hits in the double-checkerboard order)
  * with the given couplings and HOST betas for every choice that leaves the

@@ -21,17 +21,25 @@ def _stale(lib, srcs):
     return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(f) for f in srcs)
 
 
+# Several processes (the ranks of a multi-process test) may build at the
+# same time: each writes its own temporary file and renames it into place.
+def _tmp(lib):
+    return f"{lib}.{os.getpid()}.tmp"
+
+
 def build(force: bool = False) -> str:
     if force or _stale(LIB, [SRC]):
-        subprocess.run(["gcc", *FLAGS, SRC, "-o", LIB + ".tmp", "-lm"], check=True)
-        os.replace(LIB + ".tmp", LIB)
+        tmp = _tmp(LIB)
+        subprocess.run(["gcc", *FLAGS, SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, LIB)
     return LIB
 
 
 def build_omp(force: bool = False) -> str:
     if force or _stale(OMP_LIB, [SRC, OMP_SRC]):
-        subprocess.run(["gcc", *FLAGS, "-fopenmp", SRC, OMP_SRC, "-o", OMP_LIB + ".tmp", "-lm"], check=True)
-        os.replace(OMP_LIB + ".tmp", OMP_LIB)
+        tmp = _tmp(OMP_LIB)
+        subprocess.run(["gcc", *FLAGS, "-fopenmp", SRC, OMP_SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, OMP_LIB)
     return OMP_LIB
 
 

@@ -97,7 +97,7 @@ static double or_uniform(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216
 /* Lattice identifiers: (replica set a, realisation key, temperature slot t).
  * The realisation key is the realisation r for Ising / Heisenberg lattices
  * and the group r >> 5 for EA lattices (the 32 realisations of a group
- * share one uniform per site, Sec. 6, asynchronous multi-spin coding). */
+ * share one uniform per site, Sec. 5, asynchronous multi-spin coding). */
 uint32_t or_lattice_id(uint32_t a, uint32_t rkey, uint32_t t) {
   return (a << 24) | (rkey << 12) | t;
 }
@@ -281,7 +281,7 @@ void or_ising_slab_phase(int L, int y0, int rows, int8_t *slab, double beta, uin
 }
 
 /* Double checkerboard order with multi-hit updates (Sec. 3.2 and 3.4; in
- * three dimensions, Sec. 4, the tiles are T x T x T cubes).  The lattice is
+ * three dimensions, Sec. 3.6, the tiles are T x T x T cubes).  The lattice is
  * cut into tiles of edge T; tile (x / T, y / T[, z / T]) has the coarse
  * colour (x / T + y / T [+ z / T]) mod 2.  A compound move takes the tiles
  * of one coarse colour through k hits, each hit updating the fine colour-0
@@ -380,7 +380,7 @@ int64_t or_overlap(int dim, int L, const int8_t *s0, const int8_t *s1) {
  * On acceptance the two configurations and their energies are exchanged.
  * accepted[t] (optional) counts accepted exchanges of pair (t, t+1).
  * labels[t] (optional) names the configuration held at slot t; an accepted
- * exchange moves the two labels with their configurations (Sec. 7 on
+ * exchange moves the two labels with their configurations (Sec. 6 on
  * exchanging configurations rather than temperatures: the labels let a
  * caller follow each configuration through the temperature slots). */
 void or_pt_step(int dim, int L, int n_temps, int8_t **slots, int64_t *E,
@@ -424,7 +424,7 @@ void or_pt_step(int dim, int L, int n_temps, int8_t **slots, int64_t *E,
 
 /* Uniformly distributed unit vector from two uniforms: z = 2u1 - 1,
  * phi = 2 pi u2 (Archimedes' z-phi construction; the paper asks only for a
- * uniformly drawn new direction, Sec. 5). */
+ * uniformly drawn new direction, Sec. 4). */
 static void or_unit_vector(double u1, double u2, double v[3]) {
   double z = 2.0 * u1 - 1.0;
   double phi = 6.283185307179586476925 * u2; /* 2 pi */
@@ -472,7 +472,7 @@ double or_heis_site(int dim, int L, double *s, int64_t i, int colour, double bet
   return fabs(u3 - boltz);
 }
 
-/* One checkerboard sweep of the Heisenberg model (Sec. 5): every colour-0
+/* One checkerboard sweep of the Heisenberg model (Sec. 4): every colour-0
  * site, then every colour-1 site, takes or_heis_site.  `margin` (optional)
  * receives the per-site distance of the decision from flipping. */
 void or_heis_sweep(int dim, int L, double *s, double beta, uint64_t seed,
@@ -498,7 +498,7 @@ void or_heis_renormalise(int dim, int L, double *s) {
 }
 
 /* The Heisenberg model in the double-checkerboard order with multi-hit
- * updates (Sec. 5 uses it for its GPU code): tiles, compound moves, hit
+ * updates (Sec. 4 uses it for its GPU code): tiles, compound moves, hit
  * numbering and the symmetric variant exactly as in or_dcb_sweeps_dim, each
  * update being or_heis_site.  After a compound move the spins are
  * renormalised if the move passed a sweep count (1-based) that is a
@@ -585,7 +585,7 @@ void or_heis_run(int dim, int L, double *s, double beta, uint64_t seed,
   }
 }
 
-/* Parallel-tempering run of one realisation r (Sec. 7): n_sets independent
+/* Parallel-tempering run of one realisation r (Sec. 6): n_sets independent
  * replica sets, each with n_temps slots at betas[t]; spins is
  * [n_sets][n_temps][N].  Every sweep updates all lattices, then measures
  * E per (set, slot) and the overlap Q per slot between sets 0 and 1; when

@@ -1,6 +1,6 @@
 // Batched persistent launch: many lattices of several handles, many sweeps,
 // one kernel launch.  The paper maps independent replicas to thread blocks
-// (Sec. 6) and tempering copies to extra blocks (Sec. 7) but returns to the
+// (Sec. 5) and tempering copies to extra blocks (Sec. 6) but returns to the
 // host for every exchange; here measurement, exchange decisions and the
 // exchange itself run inside the same persistent launch.
 //

@@ -1,5 +1,5 @@
 // Double checkerboard with multi-hit updates for the 2D and 3D int8
-// ferromagnet (Sec. 3.2 and 3.4; Sec. 4 for three dimensions).  The lattice is cut into T x T tiles coloured like a
+// ferromagnet (Sec. 3.2 and 3.4; Sec. 3.6 for three dimensions).  The lattice is cut into T x T tiles coloured like a
 // checkerboard; one launch takes every tile of one coarse colour, loads it
 // with a one-site halo (from tiles of the other colour, which this launch
 // does not change) into shared memory, and gives it k hits there, each hit
@@ -109,7 +109,7 @@ cudaError_t launch_tiles(spin_lattice *h, int coarse, uint32_t sweep0) {
 }
 
 // ---------------------------------------------------------------- 3D
-// The same order in three dimensions (Sec. 4: cubic tiles of edge T, coarse
+// The same order in three dimensions (Sec. 3.6: cubic tiles of edge T, coarse
 // colour (x / T + y / T + z / T) mod 2).  Shared tile: (T + 2)^2 rows (z and
 // y from -1 to T, z slowest), each of T / 8 + 2 eight-byte words holding
 // x = -8 .. T + 7; only face neighbours are read, so the halo rows on the

@@ -86,7 +86,7 @@ __device__ __forceinline__ uint4 ldv4(const uint32_t *p) {
 }
 
 // ---------------------------------------------------------------- 2D
-// The square lattice (the paper's own Sec. 6 benchmark is 2D): four bonds,
+// The square lattice (the paper's own Sec. 5 benchmark is 2D): four bonds,
 // dE = 8 - 4u per realisation; flip iff u >= 2 or r < thr(dE).  Storage and
 // couplings as in 3D with two directions ([2][colour][N/2] per group).
 

@@ -1,7 +1,7 @@
 // Heisenberg model (Eq. On_hamiltonian, n = 3) on the cubic lattice and, as
-// in the paper's own study (Sec. 5), the square lattice, with FP32 unit
+// in the paper's own study (Sec. 4), the square lattice, with FP32 unit
 // vectors stored as float4 (x, y, z, 0): hot start, checkerboard Metropolis
-// sweep with a uniformly drawn new direction (Sec. 5), renormalisation.
+// sweep with a uniformly drawn new direction (Sec. 4), renormalisation.
 #include "internal.h"
 
 namespace spin {
@@ -10,7 +10,7 @@ namespace {
 // Uniform unit vector from two uniforms: z = 2 u1 - 1, phi = 2 pi u2.
 // sin/cos of 2 pi u2 are evaluated as sincospi(2 u2): 2 u2 is exact, so the
 // argument reduction is exact too.  kFast selects the hardware
-// approximations (the paper's "fast_math" mode, Sec. 5).
+// approximations (the paper's "fast_math" mode, Sec. 4).
 template <bool kFast>
 __device__ __forceinline__ float4 unit_vector(uint32_t w1, uint32_t w2) {
   const float z = 2.0f * uniform24(w1) - 1.0f;
@@ -24,7 +24,7 @@ __device__ __forceinline__ float4 unit_vector(uint32_t w1, uint32_t w2) {
   return make_float4(rho * cs, rho * sn, z, 0.0f);
 }
 
-// The Metropolis step of one site (Sec. 5) from its spin si, the sum h of
+// The Metropolis step of one site (Sec. 4) from its spin si, the sum h of
 // its neighbours and its Philox call w: proposal n from words 0 and 1,
 // acceptance from word 2, dE = -(n - si) . h; returns whether n is taken.
 // kFast = false: the library's full-accuracy FP32 functions (sqrtf, sincospif,
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) heis_split_phase_kernel(float4 *__restric
   }
 }
 
-// Double checkerboard with multi-hit updates for the 2D model (Sec. 5 runs
+// Double checkerboard with multi-hit updates for the 2D model (Sec. 4 runs
 // its GPU code this way; tiles and hits as Sec. 3.2, 3.4): one launch takes
 // every T x T tile of one coarse colour into shared memory with a one-site
 // halo (from tiles of the other colour, unchanged by this launch) and gives

@@ -1,4 +1,4 @@
-// Heisenberg energy and magnetisation in FP64 (Sec. 5: double accumulation
+// Heisenberg energy and magnetisation in FP64 (Sec. 4: double accumulation
 // for continuous spins), shared by spin_measure and the allocation-free
 // reduction so that the two give bit-identical sums.
 //

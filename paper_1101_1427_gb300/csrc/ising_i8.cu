@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) ising2d_phase_kernel(int8_t *__restrict__
 // chunk update is ising2d_phase_kernel's (same chunks, same Philox
 // counters), so n sweeps give the lattice of 2n phase launches; lattices
 // (replicas) map to CTAs, as the paper's tempering code maps replicas to
-// thread blocks (Sec. 7).  Grid: one CTA per lattice; shared memory L^2
+// thread blocks (Sec. 6).  Grid: one CTA per lattice; shared memory L^2
 // bytes.  With E or M the kernel also measures after the sweeps s (0-based
 // in the launch) with s + 1 = first + j * every, j = 0, 1, ...: row j of E
 // and M (n_lat entries each) gets E = 2 anti - 2 N and M = N - 2 down of

@@ -1,6 +1,6 @@
-// Reductions (energy, magnetisation, overlap; Sec. 4 measurements by
-// parallel reduction, double accumulation for continuous spins, Sec. 5)
-// and the replica-exchange step (Eq. parallel_tempering, Sec. 7).
+// Reductions (energy, magnetisation, overlap; Sec. 3.5 measurements by
+// parallel reduction, double accumulation for continuous spins, Sec. 4)
+// and the replica-exchange step (Eq. parallel_tempering, Sec. 6).
 #include "bitslice.cuh"
 #include "ea_cs.cuh"
 #include "heis_reduce.cuh"

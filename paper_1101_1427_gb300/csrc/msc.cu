@@ -1,10 +1,10 @@
 // +-J Edwards-Anderson glass in 3D (and on the square lattice of the
-// paper's own Sec. 6 benchmark) with asynchronous multi-spin coding: bit b
+// paper's own Sec. 5 benchmark) with asynchronous multi-spin coding: bit b
 // of a 32-bit word is the spin of realisation 32 g + b at one site, bit set
 // <=> s = -1; word-lattices [n_sets][groups][n_temps], each stored
 // colour-split (ea_cs.cuh).  Coupling words [groups][dim][colour][N/2], bit
 // set <=> J = -1.  The 32 realisations of a word share one
-// uniform per site and sweep (the paper's footnote to Sec. 6), so one Philox
+// uniform per site and sweep (the paper's footnote to Sec. 5), so one Philox
 // call serves four word-sites.
 #include "ea_cs.cuh"
 #include "internal.h"
@@ -78,7 +78,7 @@ __host__ __device__ constexpr uint32_t ea_slots(bool row_quads) { return row_qua
 // When L % 8 == 0 those updates share the quad's geometry and coupling
 // words, read once (ea_cs.cuh); each word-lattice draws its own uniforms,
 // so the mapping of updates to threads does not change the result.
-// kPair (w = 64, Sec. 6: 64 spins per variable): groups 2q and 2q + 1 of
+// kPair (w = 64, Sec. 5: 64 spins per variable): groups 2q and 2q + 1 of
 // one (set, slot) share their uniforms, keyed by q.  kRowQuads: L % 8 == 0
 // (else every site takes its own neighbour indices).  ftb divides by the
 // number of slot blocks ceil(n_temps / kS).  Register bounds: two CTAs per

@@ -1,4 +1,4 @@
-// 2D Ising ferromagnet with synchronous multi-spin coding (Sec. 6: several
+// 2D Ising ferromagnet with synchronous multi-spin coding (Sec. 5: several
 // spins of one lattice per word).  Per lattice the spins are stored as
 // [2 colours][L rows][L/64 words]; in row y the colour-c sites are
 // x = 2k + ((c + y) & 1), k = 0 .. L/2-1, grouped in blocks of 128 k's with

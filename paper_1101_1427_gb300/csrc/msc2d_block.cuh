@@ -1,5 +1,5 @@
 // Bit-sliced Metropolis update of one block of the 2D coded ferromagnet
-// (Sec. 6, synchronous multi-spin coding): the four words 4B .. 4B+3 of row
+// (Sec. 5, synchronous multi-spin coding): the four words 4B .. 4B+3 of row
 // y of one colour, i.e. 128 sites, given the acceptance masks of those four
 // words for dE = 4 and dE = 8.  Shared by the per-phase kernel and the
 // batched kernel.  A lattice is stored as [2 colours][L rows][L/64 words];

@@ -4,7 +4,7 @@
 // (colour phases, fused pass, resident lattice, coded path); which one is
 // fastest depends on the lattice size, the number of lattices and the call
 // length.  The double-checkerboard order (Sec. 3.2) takes a tile edge T whose
-// best value the paper finds by measurement (Sec. 3.4: tiles against
+// best value the paper finds by measurement (Sec. 3.5, Fig. blocks: tiles against
 // occupancy and shared memory); a handle set up with tile 0 lets this tuner
 // choose it.  Trials run on the handle's own buffer after a backup copy, and
 // the spins and counters are restored afterwards.

@@ -1,5 +1,5 @@
 """Double-checkerboard multi-hit order (Sec. 3.2, 3.4; cubic tiles in 3D,
-Sec. 4) on the GPU: shared-memory tile kernels vs the oracle, bit for bit
+Sec. 3.6) on the GPU: shared-memory tile kernels vs the oracle, bit for bit
 (lattices and measurement series), across tile sizes, hit counts, both
 compound orders and both dimensions."""
 import numpy as np

@@ -1,5 +1,5 @@
 """The Heisenberg model on the square lattice, the paper's own study
-(Sec. 5): FP32 GPU kernels against the FP64 oracle with the tolerances of
+(Sec. 4): FP32 GPU kernels against the FP64 oracle with the tolerances of
 the 3D tests (one sweep from a common start within 1e-5 away from near-ties,
 |s| - 1 <= 1e-6 after renormalisation, reductions on a given state, and the
 long-run energy within 3 combined standard errors)."""

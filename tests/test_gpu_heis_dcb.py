@@ -1,5 +1,5 @@
 """The 2D Heisenberg model in the double-checkerboard multi-hit order
-(Sec. 5's GPU scheme) against the FP64 oracle: one compound move within
+(Sec. 4's GPU scheme) against the FP64 oracle: one compound move within
 1e-5 away from near-ties, the infinite-temperature equivalence, the
 renormalisation rule, a long run in equilibrium, and refused settings."""
 import math

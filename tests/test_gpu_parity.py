@@ -202,7 +202,7 @@ def _ea_oracle(L, seed, betas, n_real, n_sets, n_sweeps, pt_every=0, reals=None,
 
 @pytest.mark.parametrize("L,width", [(16, 32), (10, 32), (16, 64)])
 def test_ea2d_coded_bit_exact(L, width):
-    """The coded EA glass on the square lattice (the paper's Sec. 6 benchmark
+    """The coded EA glass on the square lattice (the paper's Sec. 5 benchmark
     is 2D): exchange and E, M, Q every sweep, vectorised (L % 8 == 0) and
     per-site (L = 10) paths, w = 32 and 64; sampled realisations equal the
     oracle (int8 per realisation, four bonds)."""
@@ -236,7 +236,7 @@ def test_ea2d_coded_bit_exact(L, width):
 
 @pytest.mark.parametrize("L,T", [(8, 4), (6, 4), (8, 6)])
 def test_ea_w64_shared_uniforms_bit_exact(L, T):
-    """w = 64 (Sec. 6): realisations r and r' with r >> 6 == r' >> 6 share
+    """w = 64 (Sec. 5): realisations r and r' with r >> 6 == r' >> 6 share
     every update uniform; plain per-handle path with exchange and
     measurement every sweep, sampled realisations of both words of a pair.
     T = 6 leaves the second block of four slots of a thread half empty."""

@@ -1,5 +1,5 @@
 """Physics-level checks of the GPU chains: the 2D Ising ferromagnet with
-replica exchange (the paper's tempering benchmark, Sec. 7) bit-exact with the
+replica exchange (the paper's tempering benchmark, Sec. 6) bit-exact with the
 oracle, and long runs of the coded 2D sweep reproducing the exact energy and
 specific heat of the 1024 x 1024 torus at beta = 0.4 (Tab. rng)."""
 import math
@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 @pytest.mark.parametrize("L,pt_every,me,n", [(16, 1, 1, 12), (32, 3, 1, 12), (6, 1, 1, 12), (16, 5, 3, 23),
                                              (8, 4200, 7, 4500)])
 def test_ising2d_parallel_tempering_bit_exact(L, pt_every, me, n):
-    """n = 20 replicas at equally spaced beta in [0.1, 0.15] (Sec. 7), int8
+    """n = 20 replicas at equally spaced beta in [0.1, 0.15] (Sec. 6), int8
     layout, E every `me` sweeps and one exchange per `pt_every`: lattices,
     energies and exchange counts equal the oracle's.  L % 8 == 0 runs the
     resident kernel, which measures itself; its first stretch of 4200 sweeps

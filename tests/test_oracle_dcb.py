@@ -119,7 +119,7 @@ def test_long_run_matches_enumeration(k, symmetric):
     assert_within(e_mc, e_err, bf["E"], what="<E>")
 
 
-# ------------------------------------------------------------------ 3D (Sec. 4: T x T x T tiles)
+# ------------------------------------------------------------------ 3D (Sec. 3.6: T x T x T tiles)
 def _nb3(L):
     n = L ** 3
     out = []
@@ -258,7 +258,7 @@ def test_3d_long_run_matches_plain_sweeps():
     assert abs(a - b) <= 4.5 * np.hypot(ea, eb), (a, ea, b, eb)
 
 
-# ------------------------------------------------------------------ Heisenberg (Sec. 5)
+# ------------------------------------------------------------------ Heisenberg (Sec. 4)
 @pytest.mark.parametrize("dim,L,T,k,symmetric,move", [(2, 16, 4, 3, True, 1), (2, 16, 8, 2, False, 0),
                                                       (3, 8, 2, 2, True, 3)])
 def test_heis_dcb_infinite_temperature_keeps_the_last_proposal(dim, L, T, k, symmetric, move):

@@ -141,7 +141,7 @@ def test_overlap_of_independent_replicas_at_infinite_temperature():
 
 
 def test_overlap_second_moment_matches_enumeration():
-    """Two independent replicas of one 4x4 +-J realisation (Sec. 6): the
+    """Two independent replicas of one 4x4 +-J realisation (Sec. 5): the
     overlap series of the oracle's two-set run has <q> = 0 (each replica is
     spin-flip symmetric) and <q^2> = sum_ij <s_i s_j>^2, the correlation
     matrix taken over all 2^16 states."""

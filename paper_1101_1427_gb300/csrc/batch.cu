@@ -351,6 +351,10 @@ __device__ __forceinline__ void cta_swap_bits(uint32_t *w0, uint32_t *w1, uint32
   }
 }
 
+struct NoCount {
+  __device__ void operator()(uint32_t, uint32_t, uint32_t) const {}
+};
+
 // ---------------------------------------------------------------- EA unit
 __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, const RoundKeys &rk,
                          Sync &sy, uint32_t s_abs, bool measure, bool pt, long long meas_row,
@@ -373,6 +377,29 @@ __device__ bool ea_sweep(const BatchUnit &U, const uint32_t *Jsrc, int part, con
     if (colour == 1 && need_e)
       for (int k = threadIdx.x; k < n_w * 32; k += kThreads) (&e_cnt[0][0])[k] = 0;
     if (colour == 1) __syncthreads();
+    if (!(colour == 1 && need_e) && (U.L & 7) == 0 && n_w >= 2) {
+      // phases that count nothing: a thread takes one quad in a block of up
+      // to four owned word-lattices, whose geometry and coupling words it
+      // reads once (the same group for all of them)
+      const uint32_t quads = N / 8;
+      const uint32_t nb = (uint32_t)(n_w + 3) / 4, items = quads * nb;
+      const uint32_t wctr = ctr_w(TAG_UPDATE, (uint32_t)colour, 0);
+      for (uint32_t it = threadIdx.x; it < items; it += kThreads) {
+        const uint32_t blk = it / quads, j4 = it - blk * quads;
+        const EaQuadGeom q = ea_quad_geom<3>(j4, colour, (uint32_t)U.L, U.fL);
+        const EaQuadJ c = ea_quad_couplings<3>(Jsrc, q, colour, N);
+        const int w0 = 4 * (int)blk, w1 = w0 + 4 < n_w ? w0 + 4 : n_w;
+#pragma unroll 1
+        for (int wi = w0; wi < w1; ++wi) {
+          const int g = g0 + wi, a = g % U.n_sets, t = g / U.n_sets;
+          const uint4 r = philox(make_uint4(j4, s_abs, lattice_id((uint32_t)a, (uint32_t)U.rgrp, (uint32_t)t), wctr), rk);
+          ea_quad_update<3, false>(words(a, t), q, c, colour, N, r, __ldg(U.thr + 4 * t + 1), __ldg(U.thr + 4 * t + 2),
+                                   __ldg(U.thr + 4 * t + 3), NoCount());
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     for (int wi = warp / wpw; wi < n_w; wi += kWarps / wpw) {
       const int g = g0 + wi, a = g % U.n_sets, t = g / U.n_sets;
       uint32_t *s = words(a, t);

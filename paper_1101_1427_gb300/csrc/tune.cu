@@ -21,12 +21,15 @@ bool dcb_supported(const spin_lattice *h, int tile);
 
 namespace {
 
-using Key = std::tuple<int, int, int, int, int64_t, int, int, int64_t>;
+// (model, layout, dim, L, lattices, order, hits, requested tile (0: open), call length)
+using Key = std::tuple<int, int, int, int, int64_t, int, int, int, int64_t>;
 std::mutex g_tune_mutex;
 std::map<Key, std::pair<int, int>> g_tuned;  // shape -> (variant, tile)
 
 Key key_of(const spin_lattice *h, int64_t n_sweeps) {
-  return Key(h->d.model, h->d.layout, h->d.dim, h->g.L, h->n_lat, h->order, h->order_hits, n_sweeps);
+  const bool dcb = h->order != SPIN_ORDER_CHECKERBOARD;
+  return Key(h->d.model, h->d.layout, h->d.dim, h->g.L, h->n_lat, h->order, dcb ? h->order_hits : 0,
+             dcb ? h->order_tile : 0, n_sweeps);
 }
 
 int64_t spin_bytes(const spin_lattice *h) {

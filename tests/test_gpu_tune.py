@@ -61,6 +61,21 @@ def test_tune_chooses_an_open_tile_edge(order):
     b.close()
 
 
+def test_tune_keeps_a_tile_set_by_hand():
+    """A handle whose tile edge was chosen by hand keeps it, even after a
+    handle of the same shape with an open edge was tuned."""
+    L, k, betas = 256, 2, [0.44]
+    a = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=5)
+    a.set_update_order(B.SPIN_ORDER_DCB, 0, k)
+    _, tuned = a.tune(betas, 2 * k)
+    fixed = 8 if tuned != 8 else 16
+    b = sp.Lattice(B.SPIN_ISING, 2, L, B.SPIN_I8, seed=5)
+    b.set_update_order(B.SPIN_ORDER_DCB, fixed, k)
+    assert b.tune(betas, 2 * k)[1] == fixed
+    a.close()
+    b.close()
+
+
 def test_tune_rejects_bad_arguments():
     a = sp.Lattice(B.SPIN_ISING, 2, 64, B.SPIN_I8, seed=2)
     with pytest.raises(B.SpinError):

@@ -32,7 +32,8 @@
  * (threshold tables, reduction partials, an error word), allocated by
  * spin_init, and one lattice-sized working buffer allocated by the first
  * sweep call that needs it (the fused 2D int8 pass, the coded path of int8
- * lattices, long fast-math Heisenberg calls); all are freed by spin_destroy.
+ * lattices, long Heisenberg calls), with, for the resident 3D Heisenberg
+ * sweeps, one counter per CTA; all are freed by spin_destroy.
  *
  * Errors: every entry point returns 0 (SPIN_OK) or a negative SPIN_E* code
  * and never throws.  Work is asynchronous on the handle's stream; kernel
@@ -218,7 +219,11 @@ int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
 /* Batch options taken from the first item's handle: bound on every barrier
  * wait in ns (0: 2 s), CTAs per SM (0: autotuned or 2), and a number of
  * barrier arrivals that never come (0 in normal use; > 0 makes every team
- * barrier wait out its bound, for tests of the timeout path). */
+ * barrier wait out its bound, for tests of the timeout path).  The bound
+ * and the missing arrivals also apply to the neighbour waits of the resident
+ * 3D Heisenberg sweeps (spin_set_variant); a wait that runs out ends the
+ * launch early (the lattices keep their contents from before the call) and
+ * spin_sync reports SPIN_ETIMEOUT. */
 int spin_set_batch_options(spin_lattice *lat, uint64_t timeout_ns, int32_t ctas_per_sm,
                            int32_t missing_arrivals);
 
@@ -336,7 +341,14 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * acceptance as u3 2^24 < 2^(24 - beta log2(e) dE) with the hardware exp2;
  * within the same tolerances of the FP64 reference.  Calls of at least 4
  * sweeps in variant 2 run on a colour-split copy of the lattices (same
- * results bit for bit). */
+ * results bit for bit).  In either variant, calls of at least 4 sweeps of 3D
+ * lattices with L = 64 or 128 that fit in the SMs' shared memory (one
+ * lattice of L = 128 on a GPU with at least 145 SMs of 227 KB; up to a few
+ * of L = 64) run resident: one cooperative launch per 100-sweep
+ * renormalisation interval, each CTA holding a pencil of rows of one lattice
+ * in shared memory for all its sweeps and exchanging the pencil's faces with
+ * its four neighbours through the handle's lattice-sized working buffer
+ * (same results bit for bit). */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
 /* Slab decomposition of one 2D int8 ferromagnet over several GPUs (the

@@ -139,7 +139,7 @@ int validate_desc(const spin_desc *d) {
 
 void free_workspaces(spin_lattice *h) {
   void *bufs[] = {h->d_thr,    h->d_pt_thr,      h->d_pt_off, h->d_pt_len,    h->d_pt_dbeta, h->d_energy,
-                  h->d_scratch64, h->d_err, h->d_pingpong, h->d_ctr, h->d_bar,  h->d_escr};
+                  h->d_scratch64, h->d_err, h->d_pingpong, h->d_ctr, h->d_bar,  h->d_escr, h->d_res_flags};
   for (void *b : bufs)
     if (b) cudaFree(b);
 }

@@ -2,59 +2,11 @@
 // in the paper's own study (Sec. 4), the square lattice, with FP32 unit
 // vectors stored as float4 (x, y, z, 0): hot start, checkerboard Metropolis
 // sweep with a uniformly drawn new direction (Sec. 4), renormalisation.
+#include "heis_step.cuh"
 #include "internal.h"
 
 namespace spin {
 namespace {
-
-// Uniform unit vector from two uniforms: z = 2 u1 - 1, phi = 2 pi u2.
-// sin/cos of 2 pi u2 are evaluated as sincospi(2 u2): 2 u2 is exact, so the
-// argument reduction is exact too.  kFast selects the hardware
-// approximations (the paper's "fast_math" mode, Sec. 4).
-template <bool kFast>
-__device__ __forceinline__ float4 unit_vector(uint32_t w1, uint32_t w2) {
-  const float z = 2.0f * uniform24(w1) - 1.0f;
-  const float rho = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-  float sn, cs;
-  if (kFast) {
-    __sincosf(6.28318530717958647692f * uniform24(w2), &sn, &cs);
-  } else {
-    sincospif(2.0f * uniform24(w2), &sn, &cs);
-  }
-  return make_float4(rho * cs, rho * sn, z, 0.0f);
-}
-
-// The Metropolis step of one site (Sec. 4) from its spin si, the sum h of
-// its neighbours and its Philox call w: proposal n from words 0 and 1,
-// acceptance from word 2, dE = -(n - si) . h; returns whether n is taken.
-// kFast = false: the library's full-accuracy FP32 functions (sqrtf, sincospif,
-// expf).  kFast = true, the paper's fast-math mode: rho = sqrt(1 - z^2) as
-// s2 rsqrt(s2), sin and cos of phi = 2 pi u2 from the hardware sin and cos of
-// phi - pi in [-pi, pi) (negated), and u3 < exp(-beta dE) tested as
-// (w2 >> 8) < 2^(24 - beta log2(e) dE) with the hardware exp2 (beta_l2e =
-// beta log2(e) from the host).  Every kernel of one variant calls this, so a
-// chain does not depend on which kernel or call length ran it.
-template <bool kFast>
-__device__ __forceinline__ bool heis_step(const float4 &si, float hx, float hy, float hz, const uint4 &w,
-                                          float beta, float beta_l2e, float4 &n) {
-  if (!kFast) {
-    n = unit_vector<false>(w.x, w.y);
-    const float u3 = uniform24(w.z);
-    const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
-    return dE <= 0.0f || u3 < expf(-beta * dE);
-  }
-  const float z = fmaf(__uint2float_rn(w.x >> 8), 1.1920928955078125e-7f, -1.0f);  // 2 u1 - 1
-  const float s2 = fmaf(-z, z, 1.0f);
-  const float rho = s2 * rsqrtf(fmaxf(s2, 1e-30f));
-  const float xa = fmaf(__uint2float_rn(w.y >> 8), 3.7450702663161573e-7f, -3.14159265358979f);
-  float sn, cs;
-  __sincosf(xa, &sn, &cs);
-  n = make_float4(-rho * cs, -rho * sn, z, 0.0f);
-  const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
-  float p;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(fmaf(-beta_l2e, dE, 24.0f)));
-  return dE <= 0.0f || __uint2float_rn(w.z >> 8) < p;
-}
 
 __global__ void heis_init_kernel(float4 *__restrict__ s, Geom g, int64_t n_lat, RoundKeys rk) {
   const int64_t total = n_lat * g.N;
@@ -368,9 +320,38 @@ cudaError_t sweeps_heis_split(spin_lattice *h, int64_t n_sweeps) {
   heis_from_split_kernel<<<capped_grid(total), 256, 0, h->stream>>>(S, (float4 *)h->spins, h->g, total);
   return cudaGetLastError();
 }
+
+
+// Calls of at least this many sweeps of a 3D lattice that fits run resident
+// in shared memory (heis_res.cu); the launch loads and stores the lattices
+// once, about a quarter of one sweep's time at L = 128.
+constexpr int64_t kResidentMinSweeps = 4;
+
+// The resident sweeps, split at the renormalisation sweeps (every 100th,
+// applied to the row-major lattices between two launches).
+cudaError_t sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan, int64_t n_sweeps) {
+  int64_t done = 0;
+  while (done < n_sweeps) {
+    const int64_t s0 = h->sweeps_done + done;
+    const int64_t to_renorm = 100 - s0 % 100;  // sweeps up to and including the next renormalised one
+    const int64_t n = n_sweeps - done < to_renorm ? n_sweeps - done : to_renorm;
+    cudaError_t e = launch_sweeps_heis_resident(h, plan, s0, n);
+    if (e != cudaSuccess) return e;
+    if (n == to_renorm) {
+      heis_renorm_kernel<<<capped_grid(h->n_lat * h->g.N), 256, 0, h->stream>>>((float4 *)h->spins,
+                                                                               h->n_lat * h->g.N);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    done += n;
+  }
+  return cudaSuccess;
+}
 }  // namespace
 
 cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
+  HeisResPlan plan;
+  if (n_sweeps >= kResidentMinSweeps && heis_resident_plan(h, &plan)) return sweeps_heis_resident(h, plan, n_sweeps);
   if (h->variant == 2 && n_sweeps >= kSplitMinSweeps && h->n_lat * h->g.N < ((int64_t)1 << 32))
     return sweeps_heis_split(h, n_sweeps);
   const RoundKeys rk = make_round_keys(h->d.seed);

@@ -58,6 +58,10 @@ struct spin_lattice {
   unsigned *d_bar;            // one team-barrier counter per work unit of this handle
   int *d_escr;                // EA: [group][n_sets][n_temps][32] energy scratch
   int64_t ctr_dev[2];         // what d_ctr holds once the enqueued work is done (-1: unknown)
+  // resident 3D Heisenberg sweeps (heis_res.cu), allocated on first use
+  unsigned *d_res_flags;      // one published-phase counter per CTA
+  int res_flags_n;
+  uint32_t res_base;          // phases the counters have advanced by in earlier launches
 };
 
 namespace spin {
@@ -77,6 +81,17 @@ cudaError_t launch_pack_msc(spin_lattice *h, const int8_t *in);
 // heis.cu
 cudaError_t launch_init_heis(spin_lattice *h);
 cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps);
+
+// heis_res.cu: 3D lattices resident in the SMs' shared memory for a whole
+// call, one pencil of rows per CTA (L = 64 or 128, where they fit)
+struct HeisResPlan {
+  int Py, Pz;   // pencils per lattice along y and z
+  int grid;     // CTAs: n_lat Py Pz, one per SM at most
+  size_t smem;  // dynamic shared memory per CTA
+};
+bool heis_resident_plan(const spin_lattice *h, HeisResPlan *plan);
+// sweeps sweep0 .. sweep0 + n_sweeps - 1 (no renormalisation inside)
+cudaError_t launch_sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan, int64_t sweep0, int64_t n_sweeps);
 
 // measure.cu
 cudaError_t launch_measure(spin_lattice *h, const void *J, int64_t *E, int64_t *M, int64_t *Q,

@@ -19,6 +19,15 @@ struct NvtxRange {
   NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+namespace spin {
+// Decomposition of the resident 3D Heisenberg sweeps (heis_res.cu).
+struct HeisResPlan {
+  int Py, Pz;   // pencils per lattice along y and z
+  int grid;     // CTAs: n_lat Py Pz, one per SM at most
+  size_t smem;  // dynamic shared memory per CTA
+};
+}  // namespace spin
+
 struct spin_lattice {
   spin_desc d;
   spin::Geom g;
@@ -62,6 +71,8 @@ struct spin_lattice {
   unsigned *d_res_flags;      // one published-phase counter per CTA
   int res_flags_n;
   uint32_t res_base;          // phases the counters have advanced by in earlier launches
+  spin::HeisResPlan res_plan[2];  // per variant (full accuracy, fast math)
+  int res_plan_state[2];          // 0: not made yet, 1: usable, -1: the lattices do not fit
 };
 
 namespace spin {
@@ -83,12 +94,8 @@ cudaError_t launch_init_heis(spin_lattice *h);
 cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps);
 
 // heis_res.cu: 3D lattices resident in the SMs' shared memory for a whole
-// call, one pencil of rows per CTA (L = 64 or 128, where they fit)
-struct HeisResPlan {
-  int Py, Pz;   // pencils per lattice along y and z
-  int grid;     // CTAs: n_lat Py Pz, one per SM at most
-  size_t smem;  // dynamic shared memory per CTA
-};
+// call, one pencil of rows per CTA (L = 64 or 128, where they fit); the
+// plan (HeisResPlan, above the handle) is made once per handle and variant
 bool heis_resident_plan(const spin_lattice *h, HeisResPlan *plan);
 // sweeps sweep0 .. sweep0 + n_sweeps - 1 (no renormalisation inside)
 cudaError_t launch_sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan, int64_t sweep0, int64_t n_sweeps);

@@ -141,6 +141,21 @@ def test_no_stray_writes(name, args, kw, variant, order):
     hd.close()
 
 
+@pytest.mark.parametrize("variant", [0, 2])
+def test_no_stray_writes_heis3d_resident(variant):
+    """3D Heisenberg L = 64 with two slots: calls of 6 sweeps and a run
+    measuring every 4 sweeps take the resident kernel (pencils of two
+    lattices in shared memory, faces through the handle's buffer)."""
+    hd = Handle(B.SPIN_HEISENBERG, 3, 64, B.SPIN_F32X4, n_temps=2, seed=9)
+    B.spin_set_variant(hd.h, variant)
+    betas = [0.5, 0.9]
+    B.spin_sweep(hd.h, None, betas, 6, hd.seed)
+    ser = hd.series(2)
+    B.spin_run(hd.h, None, betas, 8, 4, 0, None, None, None, ser["Ef"].t, ser["Mf"].t, None, None)
+    _run_all(hd, betas)
+    hd.close()
+
+
 def test_no_stray_writes_w64_and_batch():
     ea = Handle(B.SPIN_EA, 3, 8, B.SPIN_MSC1, n_real=128, n_temps=4, n_sets=2, seed=5)
     B.spin_set_msc_width(ea.h, 64)

@@ -118,8 +118,9 @@ __device__ bool team_barrier(Sync &sy) {
   sy.target += sy.size;
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(sy.ctr, 1u);
+    // release: the CTA's writes (ordered before this by the barrier above)
+    // become visible to every CTA that acquires the final count
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(sy.ctr) : "memory");
     const unsigned want = sy.target + (unsigned)sy.extra;
     const uint64_t t0 = globaltimer();
     while ((int)(ld_acquire(sy.ctr) - want) < 0) {
@@ -134,7 +135,6 @@ __device__ bool team_barrier(Sync &sy) {
       }
       __nanosleep(100);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -209,10 +209,13 @@ int spin_batch_run(const spin_batch_item *items, int n_items, int64_t n_sweeps,
 
 /* Autotuner for spin_batch_run: times n_sweeps-sweep trial launches (with
  * the given measurement and exchange schedule, into scratch series) for
- * 1..4 CTAs per SM and three weights of the Ising units in the split of
- * CTAs between work units, on copies of the spins (handles and counters are
- * left as they were), and caches the fastest pair for this batch shape;
- * best (optional, host) receives the CTAs per SM. */
+ * 1..4 CTAs per SM and the weights of the split of CTAs between work units
+ * (three weights of the Ising units when the batch mixes Ising and EA
+ * handles; three fixed costs per EA word-lattice, 0, 1024 and 4096 sites,
+ * when its EA lattices have several sizes), on copies of the spins (handles
+ * and counters are left as they were), and caches the fastest choice for
+ * this batch shape; best (optional, host) receives the CTAs per SM.  The
+ * choice changes only which CTAs do which work, never the results. */
 int spin_batch_tune(const spin_batch_item *items, int n_items, int64_t n_sweeps,
                     int32_t measure_every, int32_t pt_every, void *stream, int32_t *best);
 

@@ -766,15 +766,17 @@ __global__ void batch_epilogue_kernel(const BatchCtl c) {
 struct Tuned {
   int ctas_per_sm;
   double ising_scale;
+  double ea_n0;
 };
 static std::map<std::vector<long long>, Tuned> g_tuned;  // autotuner cache, by batch signature
 
 // Relative cost of one sweep of a unit, per CTA-time, with measurement and
 // exchange every sweep (calibrated on GB300: a coded EA word-site costs ~4x
 // an int8 Ising site and ~8x a coded Ising site); the autotuner rescales
-// the Ising share.
-static double unit_work(const BatchUnit &U, double ising_scale) {
-  if (U.kind == 0) return 48.0 * U.n_sets * U.n_T * (double)U.N;
+// the Ising share and adds ea_n0 sites of fixed cost per EA word-lattice
+// (barriers and set-up weigh more, per site, in small lattices).
+static double unit_work(const BatchUnit &U, double ising_scale, double ea_n0) {
+  if (U.kind == 0) return 48.0 * U.n_sets * U.n_T * ((double)U.N + ea_n0);
   if (U.kind == 1) return 12.0 * ising_scale * (double)U.N;
   return 6.0 * ising_scale * (double)U.N;
 }
@@ -784,7 +786,7 @@ static double unit_work(const BatchUnit &U, double ising_scale) {
 // one to the unit with the largest work per CTA, up to each unit's maximum
 // (EA: one word-lattice per CTA; Ising: 8 rows per CTA).  Returns the CTAs
 // used.
-static int assign_teams(BatchUnit *units, int n, int grid, double ising_scale) {
+static int assign_teams(BatchUnit *units, int n, int grid, double ising_scale, double ea_n0) {
   std::vector<int> P(n), cap(n);
   int used = 0;
   for (int u = 0; u < n; ++u) {
@@ -807,8 +809,8 @@ static int assign_teams(BatchUnit *units, int n, int grid, double ising_scale) {
     int best = -1;
     double bw = -1;
     for (int u = 0; u < n; ++u)
-      if (P[u] < cap[u] && unit_work(units[u], ising_scale) / P[u] > bw) {
-        bw = unit_work(units[u], ising_scale) / P[u];
+      if (P[u] < cap[u] && unit_work(units[u], ising_scale, ea_n0) / P[u] > bw) {
+        bw = unit_work(units[u], ising_scale, ea_n0) / P[u];
         best = u;
       }
     if (best < 0) break;
@@ -1085,12 +1087,14 @@ extern "C" int spin_batch_run(const spin_batch_item *items, int n_items, int64_t
   }
   int bps = std::min(per_sm, h0->batch_ctas_per_sm > 0 ? h0->batch_ctas_per_sm : 2);
   double scale = h0->batch_ising_scale > 0.0 ? h0->batch_ising_scale : 1.0;
+  double n0 = h0->batch_ea_n0 > 0.0 ? h0->batch_ea_n0 - 1.0 : 0.0;
   auto it = g_tuned.find(sig);
   if (it != g_tuned.end()) {
     if (h0->batch_ctas_per_sm <= 0) bps = std::min(per_sm, it->second.ctas_per_sm);
     if (h0->batch_ising_scale <= 0.0) scale = it->second.ising_scale;
+    if (h0->batch_ea_n0 <= 0.0) n0 = it->second.ea_n0;
   }
-  const int grid = assign_teams(prm.units, prm.n_units, sms * bps, scale);
+  const int grid = assign_teams(prm.units, prm.n_units, sms * bps, scale, n0);
   if (grid > sms * per_sm) return SPIN_EINVAL;
   batch_prologue_kernel<<<1, 256, 0, st>>>(ctl);
   if (cudaGetLastError() != cudaSuccess) return SPIN_ECUDA;
@@ -1157,18 +1161,40 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
   }
   spin_lattice *h0 = items[0].lat;
   const int saved_bps = h0->batch_ctas_per_sm;
-  const double saved_scale = h0->batch_ising_scale;
+  const double saved_scale = h0->batch_ising_scale, saved_n0 = h0->batch_ea_n0;
   float best_ms = 1e30f;
-  Tuned best{1, 1.0};
+  Tuned best{1, 1.0, 0.0};
+  // weights that can change the split: the Ising share only with Ising and
+  // EA units together, the EA overhead only with EA units of several sizes
+  bool has_ising = false, has_ea = false, ea_sizes = false;
+  {
+    BatchParams *p0 = new BatchParams;
+    batch_build(items, n_items, *p0);
+    uint32_t n_first = 0;
+    for (int u = 0; u < p0->n_units; ++u) {
+      if (p0->units[u].kind == 0) {
+        if (has_ea && p0->units[u].N != n_first) ea_sizes = true;
+        if (!has_ea) n_first = p0->units[u].N;
+        has_ea = true;
+      } else {
+        has_ising = true;
+      }
+    }
+    delete p0;
+  }
+  const std::vector<double> scales =
+      has_ising && has_ea ? std::vector<double>{0.5, 1.0, 2.0} : std::vector<double>{1.0};
+  const std::vector<double> n0s = ea_sizes ? std::vector<double>{0.0, 1024.0, 4096.0} : std::vector<double>{0.0};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   int rc = SPIN_OK;
-  const double scales[3] = {0.5, 1.0, 2.0};
   for (int c = 1; c <= std::min(per_sm, 4) && !rc; ++c)
-    for (double sc : scales) {
+    for (double sc : scales)
+    for (double e0 : n0s) {
       h0->batch_ctas_per_sm = c;
       h0->batch_ising_scale = sc;
+      h0->batch_ea_n0 = e0 + 1.0;  // held plus one: 0 means not set
       float ms = 1e30f;
       for (int rep = 0; rep < 2 && !rc; ++rep) {  // best of two
         cudaEventRecord(a, st);
@@ -1187,11 +1213,12 @@ extern "C" int spin_batch_tune(const spin_batch_item *items, int n_items, int64_
       if (rc) break;
       if (ms < best_ms) {
         best_ms = ms;
-        best = Tuned{c, sc};
+        best = Tuned{c, sc, e0};
       }
     }
   h0->batch_ctas_per_sm = saved_bps;
   h0->batch_ising_scale = saved_scale;
+  h0->batch_ea_n0 = saved_n0;
   for (int k = 0; k < n_items; ++k) {
     cudaMemcpyAsync(items[k].lat->spins, backup[k], bytes[k], cudaMemcpyDeviceToDevice, st);
     items[k].lat->sweeps_done = sw[k];

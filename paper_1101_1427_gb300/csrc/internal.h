@@ -61,6 +61,7 @@ struct spin_lattice {
   uint64_t batch_timeout_ns;  // bound on every team-barrier wait (0: 2 s)
   int batch_ctas_per_sm;      // 0: autotuned / default
   double batch_ising_scale;   // 0: autotuned / default; weight of Ising units in the CTA split
+  double batch_ea_n0;         // 0: autotuned / default; else 1 + fixed cost per EA word-lattice, in sites
   int batch_fault_extra;      // arrivals a barrier waits for that never come (tests)
   // batched-launch workspace, allocated by the first uncaptured batch call
   int64_t *d_ctr;             // [sweeps_done, pt_steps_done] as the batch kernel reads them

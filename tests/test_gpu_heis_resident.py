@@ -20,10 +20,11 @@ import paper_1101_1427_gb300 as sp  # noqa: E402
 from paper_1101_1427_gb300 import _binding as B  # noqa: E402
 
 
-def _pair(L, n_real, n_temps, variant, seed, start=94):
+def _pair(L, n_real, n_temps, variant, seed, start=94, n_sets=1):
     out = []
     for _ in range(2):
-        lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, n_real=n_real, n_temps=n_temps, seed=seed)
+        lat = sp.Lattice(B.SPIN_HEISENBERG, 3, L, B.SPIN_F32X4, n_real=n_real, n_temps=n_temps, n_sets=n_sets,
+                         seed=seed)
         lat.set_variant(variant)
         lat.set_counters(start, 0)  # the calls below cross the renormalisation after sweep 100
         out.append(lat)
@@ -31,10 +32,10 @@ def _pair(L, n_real, n_temps, variant, seed, start=94):
 
 
 @pytest.mark.parametrize("variant", [0, 2])
-@pytest.mark.parametrize("L,n_real,n_temps", [(128, 1, 1), (64, 1, 3), (64, 2, 2)])
-def test_resident_and_per_phase_kernels_give_one_chain(variant, L, n_real, n_temps):
+@pytest.mark.parametrize("L,n_real,n_temps,n_sets", [(128, 1, 1, 1), (64, 1, 3, 1), (64, 2, 2, 1), (64, 1, 2, 2)])
+def test_resident_and_per_phase_kernels_give_one_chain(variant, L, n_real, n_temps, n_sets):
     betas = list(np.linspace(0.5, 1.1, n_temps))
-    a, b = _pair(L, n_real, n_temps, variant, seed=43)
+    a, b = _pair(L, n_real, n_temps, variant, seed=43, n_sets=n_sets)
     for _ in range(12):
         a.sweep(betas, 1)  # one launch per colour phase
     b.sweep(betas, 12)  # resident: sweeps 94..99, renormalisation, 100..105

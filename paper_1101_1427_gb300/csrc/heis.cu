@@ -350,12 +350,18 @@ cudaError_t sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan, int64
 }  // namespace
 
 cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
-  if (n_sweeps >= kResidentMinSweeps) {
+  // Inside a stream capture only the per-phase kernels: they allocate
+  // nothing, and a replayed graph must not meet the resident kernel's
+  // published-phase counters already advanced by an earlier replay.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) return cudaGetLastError();
+  const bool capturing = cs != cudaStreamCaptureStatusNone;
+  if (!capturing && n_sweeps >= kResidentMinSweeps) {
     const int v = h->variant == 2 ? 1 : 0;
     if (h->res_plan_state[v] == 0) h->res_plan_state[v] = heis_resident_plan(h, &h->res_plan[v]) ? 1 : -1;
     if (h->res_plan_state[v] == 1) return sweeps_heis_resident(h, h->res_plan[v], n_sweeps);
   }
-  if (h->variant == 2 && n_sweeps >= kSplitMinSweeps && h->n_lat * h->g.N < ((int64_t)1 << 32))
+  if (!capturing && h->variant == 2 && n_sweeps >= kSplitMinSweeps && h->n_lat * h->g.N < ((int64_t)1 << 32))
     return sweeps_heis_split(h, n_sweeps);
   const RoundKeys rk = make_round_keys(h->d.seed);
   const uint32_t half = (uint32_t)(h->n_lat * (h->g.N / 2));

@@ -338,8 +338,17 @@ cudaError_t launch_sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan
   a.timeout_ns = h->batch_timeout_ns ? h->batch_timeout_ns : 2000000000ull;
   h->res_base += 2u * (uint32_t)n_sweeps + 1u;
   void *args[] = {&a};
-  return cudaLaunchCooperativeKernel(pick_kernel(h->variant, h->g.L), dim3(plan.grid), dim3(kResThreads), args,
-                                     plan.smem, h->stream);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)plan.grid);
+  cfg.blockDim = dim3(kResThreads);
+  cfg.dynamicSmemBytes = plan.smem;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once: the neighbour waits need it
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, pick_kernel(h->variant, h->g.L), args);
 }
 
 }  // namespace spin

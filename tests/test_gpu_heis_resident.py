@@ -106,3 +106,28 @@ def test_resident_wait_timeout_is_reported_and_context_survives():
     other.sync()
     lat.close()
     other.close()
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_captured_sweeps_take_the_per_phase_kernels(variant):
+    """Inside a stream capture the sweeps go through the per-phase kernels
+    (nothing allocated, no published-phase counters to be met again by a
+    later replay): one replay equals the same sweeps run resident."""
+    s = torch.cuda.Stream()
+    a = sp.Lattice(B.SPIN_HEISENBERG, 3, 64, B.SPIN_F32X4, seed=47, stream=s)
+    b = sp.Lattice(B.SPIN_HEISENBERG, 3, 64, B.SPIN_F32X4, seed=47)
+    for lat in (a, b):
+        lat.set_variant(variant)
+        lat.sweep([0.7], 1)  # uploads the thresholds outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        B.spin_sweep(a.h, None, [0.7], 6, a.seed)
+    g.replay()
+    torch.cuda.synchronize()
+    b.sweep([0.7], 6)  # resident
+    b.sync()
+    assert a.sweeps_done == b.sweeps_done == 7
+    assert torch.equal(a.spins, b.spins)
+    a.close()
+    b.close()

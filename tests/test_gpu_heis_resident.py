@@ -131,3 +131,18 @@ def test_captured_sweeps_take_the_per_phase_kernels(variant):
     assert torch.equal(a.spins, b.spins)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_lattices_that_do_not_fit_take_the_other_paths(variant):
+    """Two lattices of L = 128 (64 MiB) exceed the SMs' shared memory: long
+    calls take the colour-split copy (fast math) or the per-phase kernel,
+    with the same chain as calls of one sweep."""
+    a, b = _pair(128, 1, 2, variant, seed=48, start=0)
+    betas = [0.6, 0.9]
+    b.sweep(betas, 5)
+    for _ in range(5):
+        a.sweep(betas, 1)
+    assert torch.equal(a.spins, b.spins)
+    a.close()
+    b.close()

@@ -190,8 +190,12 @@ __global__ void __launch_bounds__(kResThreads, 1) heis_resident_kernel(ResArgs P
       const float4 *o = oth + idx;
       const float4 m = o[0], sh = o[p ? dxp : dxm];  // x +- 1: sh is x + 1 if p, else x - 1
       const float4 *gy = Xo + ri.z + kx, *gz = Xo + ri.w + kx;
-      const float4 cy = ld_cg((ext & 1) ? gy : o + kH), dy = ld_cg((ext & 2) ? gy : o - kH);
-      const float4 ez = ld_cg((ext & 4) ? gz : o + nyH), fz = ld_cg((ext & 8) ? gz : o - (int)nyH);
+      // (the face bits are the same for the whole warp: no divergence)
+      float4 cy, dy, ez, fz;
+      if (ext & 1) cy = ld_cg(gy); else cy = o[kH];
+      if (ext & 2) dy = ld_cg(gy); else dy = o[-kH];
+      if (ext & 4) ez = ld_cg(gz); else ez = o[nyH];
+      if (ext & 8) fz = ld_cg(gz); else fz = o[-(int)nyH];
       const float4 si = own[idx];
       const uint4 w = philox(make_uint4(ri.x + kx, sweep, lid, wctr), P.rk);
       // (x+1) + (x-1) first: the same sum in either order

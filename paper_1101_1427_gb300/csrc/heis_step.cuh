@@ -44,10 +44,16 @@ __device__ __forceinline__ bool heis_step(const float4 &si, float hx, float hy, 
   }
   const float z = fmaf(__uint2float_rn(w.x >> 8), 1.1920928955078125e-7f, -1.0f);  // 2 u1 - 1
   const float s2 = fmaf(-z, z, 1.0f);
-  const float rho = s2 * rsqrtf(fmaxf(s2, 1e-30f));
+  // the hardware approximations in their flush-to-zero forms: every input and
+  // output here is a normal number (s2 >= 1e-30; |xa|, |sin xa|, |cos xa| are
+  // 0 or >= ~3e-7), so they equal the non-flushing forms and skip their
+  // denormal handling
+  float rs, sn, cs;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(fmaxf(s2, 1e-30f)));
+  const float rho = s2 * rs;
   const float xa = fmaf(__uint2float_rn(w.y >> 8), 3.7450702663161573e-7f, -3.14159265358979f);
-  float sn, cs;
-  __sincosf(xa, &sn, &cs);
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(xa));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(xa));
   n = make_float4(-rho * cs, -rho * sn, z, 0.0f);
   const float dE = (si.x - n.x) * hx + (si.y - n.y) * hy + (si.z - n.z) * hz;
   float p;

@@ -45,9 +45,10 @@ __device__ __forceinline__ bool heis_step(const float4 &si, float hx, float hy, 
   const float z = fmaf(__uint2float_rn(w.x >> 8), 1.1920928955078125e-7f, -1.0f);  // 2 u1 - 1
   const float s2 = fmaf(-z, z, 1.0f);
   // the hardware approximations in their flush-to-zero forms: every input and
-  // output here is a normal number (s2 >= 1e-30; |xa|, |sin xa|, |cos xa| are
-  // 0 or >= ~3e-7), so they equal the non-flushing forms and skip their
-  // denormal handling
+  // output here is 0 or a normal number (s2 >= 1e-30; xa = (k - 2^23) c with
+  // c = fl(2 pi 2^-24), so |xa| is 0 or >= c, and the sine and cosine of such
+  // angles are 0 or above 1e-8), so they equal the non-flushing forms and
+  // skip their denormal handling
   float rs, sn, cs;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(fmaxf(s2, 1e-30f)));
   const float rho = s2 * rs;

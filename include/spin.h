@@ -351,8 +351,10 @@ int spin_set_counters(spin_lattice *lat, int64_t sweeps_done, int64_t pt_steps_d
  * renormalisation interval, each CTA holding a pencil of rows of one lattice
  * in shared memory for all its sweeps and exchanging the pencil's faces with
  * its four neighbours through the handle's lattice-sized working buffer
- * (same results bit for bit).  Inside a stream capture Heisenberg sweeps
- * always take the per-phase kernels (same results; nothing allocated). */
+ * (same results bit for bit; if the GPU refuses the cooperative launch, its
+ * SMs shared with other work, the handle takes the other paths from then
+ * on).  Inside a stream capture Heisenberg sweeps always take the per-phase
+ * kernels (same results; nothing allocated). */
 int spin_set_variant(spin_lattice *lat, int32_t variant);
 
 /* Slab decomposition of one 2D int8 ferromagnet over several GPUs (the

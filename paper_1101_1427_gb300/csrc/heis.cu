@@ -329,8 +329,8 @@ constexpr int64_t kResidentMinSweeps = 4;
 
 // The resident sweeps, split at the renormalisation sweeps (every 100th,
 // applied to the row-major lattices between two launches).
-cudaError_t sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan, int64_t n_sweeps) {
-  int64_t done = 0;
+cudaError_t sweeps_heis_resident(spin_lattice *h, const HeisResPlan &plan, int64_t n_sweeps, int64_t &done) {
+  done = 0;
   while (done < n_sweeps) {
     const int64_t s0 = h->sweeps_done + done;
     const int64_t to_renorm = 100 - s0 % 100;  // sweeps up to and including the next renormalised one
@@ -359,7 +359,20 @@ cudaError_t launch_sweeps_heis(spin_lattice *h, int64_t n_sweeps) {
   if (!capturing && n_sweeps >= kResidentMinSweeps) {
     const int v = h->variant == 2 ? 1 : 0;
     if (h->res_plan_state[v] == 0) h->res_plan_state[v] = heis_resident_plan(h, &h->res_plan[v]) ? 1 : -1;
-    if (h->res_plan_state[v] == 1) return sweeps_heis_resident(h, h->res_plan[v], n_sweeps);
+    if (h->res_plan_state[v] == 1) {
+      int64_t done = 0;
+      cudaError_t e = sweeps_heis_resident(h, h->res_plan[v], n_sweeps, done);
+      if (e != cudaErrorCooperativeLaunchTooLarge) return e;
+      // The GPU cannot hold every CTA at once (its SMs shared with other
+      // work): the refused launch ran nothing, and this handle takes the
+      // other paths from here on, from the first sweep not yet done.
+      cudaGetLastError();
+      h->res_plan_state[v] = -1;
+      h->sweeps_done += done;
+      e = launch_sweeps_heis(h, n_sweeps - done);
+      h->sweeps_done -= done;
+      return e;
+    }
   }
   if (!capturing && h->variant == 2 && n_sweeps >= kSplitMinSweeps && h->n_lat * h->g.N < ((int64_t)1 << 32))
     return sweeps_heis_split(h, n_sweeps);
